@@ -1,0 +1,220 @@
+/*
+ * pi2rh.h -- C ABI of the B300 (sm_103a) implementation of one receding-horizon
+ * path-integral (PI^2-RH) control update over a learned LWPR dynamics model
+ * ("GPU based Path Integral Control with Learned Dynamics", arXiv 1503.00330).
+ *
+ * One update (pi_update) computes, on the GPU:
+ *   1. K perturbed control sequences u_{k,t} = u_nom_t + eps_{k,t},
+ *      eps ~ N(0, diag(sigma_u)), drawn in-kernel from Philox4x32-10
+ *      (Sec. 3.1, "sample possible trajectories").
+ *   2. K rollouts of T Euler steps through the probabilistic LWPR model:
+ *      normalized Gaussian receptive-field weights, local linear mean, variance
+ *      (Sec. 2, Eq. 1), and a sampled next state x + dt (y + sigma n)
+ *      (Sec. 3.2; Euler integration as in Table 1). With M > 1 each rollout is
+ *      M sub-rollouts that share eps and average their cost (Sec. 3.2).
+ *   3. the running cost q(x_t, z_t) per step and the terminal cost phi(x_T)
+ *      (Sec. 5 obstacle-navigation cost; indicator or Gaussian-bump form).
+ *   4. the cost-to-go S_{k,i} = phi + dt sum_{j>=i} q_{k,j} (Sec. 3.1), in FP64.
+ *   5. per timestep i, the weights exp(-S_{k,i}/lambda) / sum_k and
+ *      u_out_i = u_nom_i + sum_k P_{k,i} eps_{k,i} (Sec. 3.1, Eq. 2), with the
+ *      normalization over k in FP64.
+ *
+ * Fixed dimensions: state NX = 12 (position, velocity, roll/pitch/yaw, body
+ * rates), control NU = 4 (thrust, roll, pitch, yaw-rate), LWPR input
+ * z = [x, u] (NZ = 16), LWPR outputs NY = 12 (the state derivatives).
+ *
+ * Conventions for every entry point:
+ *   - Return value 0 (PI_OK) or a PI_ERR_* code; pi_last_error() gives a
+ *     message for the calling thread.  No entry point aborts the process.
+ *   - "device" pointers are CUDA global-memory pointers on the context's
+ *     device; "host" pointers are ordinary CPU memory.  The caller owns every
+ *     buffer it passes; the library never frees or retains caller memory.
+ *   - Work is enqueued asynchronously on the context's stream (pi_set_stream,
+ *     default: the legacy default stream) unless stated otherwise.  Results are
+ *     valid once that stream is synchronized; pi_sync() does that and reports
+ *     device-side errors.
+ *   - Float inputs must be finite; non-finite inputs give unspecified (but
+ *     memory-safe) outputs.
+ */
+#ifndef PI2RH_H
+#define PI2RH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PI2RH_NX 12
+#define PI2RH_NU 4
+#define PI2RH_NZ 16
+#define PI2RH_NY 12
+#define PI2RH_MAX_OBS 256
+#define PI2RH_MAX_M 64
+
+enum {
+    PI_OK = 0,
+    PI_ERR_INVALID_ARG = 1, /* a size, pointer or parameter is out of range       */
+    PI_ERR_OOM = 2,         /* device allocation failed                           */
+    PI_ERR_CUDA = 3,        /* a CUDA runtime call or kernel launch failed         */
+    PI_ERR_TIMEOUT = 4,     /* a bounded device-side wait expired (see pi_sync)    */
+    PI_ERR_INTERNAL = 5,    /* a device-side consistency check failed              */
+    PI_ERR_UNSUPPORTED = 6  /* option not available in this build                  */
+};
+
+enum { PI_PRECISION_FP32 = 0 };
+enum { PI_NOISE_MEAN_ONLY = 0, PI_NOISE_SAMPLED = 1 };
+enum { PI_OBS_INDICATOR = 0, PI_OBS_GAUSSIAN = 1 };
+
+typedef struct pi_ctx pi_ctx;
+
+/* LWPR model (Sec. 2, Eq. 1).  All arrays host, float32, row-major, copied at
+ * pi_create.  n_in must be 16 and n_out 12; L >= 1 fields per output.
+ *   c     [n_out][L][n_in]        receptive-field centers c_j
+ *   D     [n_out][L][n_in][n_in]  distance metrics D_j (used through the
+ *                                 quadratic form, so only D + D^T matters)
+ *   beta  [n_out][L][n_in]        local slopes: y_j(z) = b_j + beta_j . (z - c_j)
+ *   b     [n_out][L]              local offsets (value at the center)
+ *   sigma [n_out][L]              per-field noise standard deviation sigma_j
+ *   dt                            Euler step (s), > 0                          */
+typedef struct {
+    int n_in;
+    int n_out;
+    int L;
+    float dt;
+    const float *c;
+    const float *D;
+    const float *beta;
+    const float *b;
+    const float *sigma;
+} pi_lwpr_params;
+
+/* Running cost (Sec. 5 form, generalized):
+ *   q(x, z) = sum_d Q_pos[d] (p_d - goal_d)^2 + Q_vel |v|^2 + Q_ang |angles|^2
+ *           + (obs_kind == PI_OBS_INDICATOR ? w_obs * C
+ *                                           : w_obs * sum_i exp(-obs_sharp d_i^2))
+ *           + w_crash * C + w_var * sum_o var_o(z)
+ *   C = 1 if (p_x, p_y) is strictly inside any vertical cylinder of the given
+ *   radius around obs_xy[i] (decided in FP32), else 0.
+ * Terminal cost phi(x_T) = w_T * sum_d Q_pos[d] (p_{T,d} - goal_d)^2.
+ * obs_xy: host [n_obs][2], 0 <= n_obs <= PI2RH_MAX_OBS, copied at pi_create. */
+typedef struct {
+    float goal[3];
+    float Q_pos[3];
+    float Q_vel;
+    float Q_ang;
+    float w_obs;
+    float obs_sharp;
+    float radius;
+    float w_crash;
+    float w_var;
+    float w_T;
+    int obs_kind;
+    int n_obs;
+    const float *obs_xy;
+} pi_cost_params;
+
+/* Options.  precision: PI_PRECISION_FP32.  model_noise: PI_NOISE_SAMPLED
+ * (draw x' = x + dt (y + sigma n)) or PI_NOISE_MEAN_ONLY (x' = x + dt y).
+ * M: sub-rollouts per rollout (Sec. 3.2), a power of two in [1, 64].
+ * device: CUDA device ordinal. */
+typedef struct {
+    int precision;
+    int model_noise;
+    int M;
+    int device;
+} pi_opts;
+
+/* Fills *opts with FP32, sampled noise, M = 1, device 0. */
+void pi_default_opts(pi_opts *opts);
+
+/* Creates a context: validates and packs the model into the kernel's record
+ * layout and copies model, obstacles and options to the device (synchronous).
+ * opts may be NULL (defaults).  On success *out owns device memory until
+ * pi_destroy.  Errors: INVALID_ARG (bad dims / NULL / ranges), OOM, CUDA. */
+int pi_create(const pi_lwpr_params *lwpr, const pi_cost_params *cost, const pi_opts *opts,
+              pi_ctx **out);
+
+/* Sets the cudaStream_t (passed as void*) used by later calls; NULL = legacy
+ * default stream.  The stream must belong to the context's device. */
+int pi_set_stream(pi_ctx *ctx, void *stream);
+
+/* Pre-allocates the per-update scratch for K rollouts and T steps so that later
+ * pi_update calls with K' <= K, T' <= T allocate nothing. */
+int pi_reserve(pi_ctx *ctx, int K, int T);
+
+/* One control update (Sec. 3.1 / Eq. 2 over the rollouts of Sec. 3.2).
+ *   x0        device [12]      initial state
+ *   u_nominal device [T][4]    nominal controls (may alias u_out)
+ *   K >= 1 rollouts, T >= 1 steps; lambda > 0 (temperature of Eq. 2)
+ *   sigma_u   host [4]         control-noise variances (>= 0), Sigma_u = diag
+ *   seed                       Philox key; noise of rollout k, step t, block b,
+ *                              sub-rollout m uses counter (k, t, b, m)
+ *   u_out     device [T][4]    u_nom + sum_k P_k eps_k per timestep
+ *   costs_out device [K]       S_{k,0}, the cost-to-go of each whole rollout
+ * Asynchronous on the context's stream.  Scratch (about K*T*20 bytes) is
+ * grown with stream-ordered allocation when needed.  Errors: INVALID_ARG,
+ * OOM, CUDA; device-side errors are reported by pi_sync. */
+int pi_update(pi_ctx *ctx, const float *x0, const float *u_nominal, int K, int T, float lambda,
+              const float *sigma_u, uint64_t seed, float *u_out, float *costs_out);
+
+/* Same update with HOST buffers (x0 [12], u_nominal [T][4], u_out [T][4],
+ * costs_out [K]): copies inputs to context-owned device buffers, runs
+ * pi_update, copies results back and synchronizes the stream before
+ * returning.  This is the end-to-end path (host<->device copies included). */
+int pi_update_host(pi_ctx *ctx, const float *x0, const float *u_nominal, int K, int T,
+                   float lambda, const float *sigma_u, uint64_t seed, float *u_out,
+                   float *costs_out);
+
+/* Synchronizes the context's stream and reports device-side errors raised by
+ * earlier work: PI_ERR_TIMEOUT if a bounded wait in a kernel expired (the
+ * kernel returned early and its outputs are invalid), PI_ERR_INTERNAL for a
+ * failed device-side check.  Clears the device error word. */
+int pi_sync(pi_ctx *ctx);
+
+/* Frees the context and its device memory (synchronizes its stream first).
+ * NULL is accepted. */
+void pi_destroy(pi_ctx *ctx);
+
+/* Message of the last error on the calling thread ("" if none). */
+const char *pi_last_error(void);
+
+/* Number of kernel launches enqueued through this context since creation. */
+uint64_t pi_launch_count(const pi_ctx *ctx);
+
+/* ---------------------------------------------------------------------------
+ * Staged entry points (same device code as pi_update, exposed for parity
+ * tests of each step).  All pointers are device pointers; asynchronous on the
+ * context's stream (pi_debug_noise / pi_debug_normals take a stream).
+ * ------------------------------------------------------------------------- */
+
+/* Raw Philox4x32-10 blocks: raw[k][t][blk][4] = Philox(counter (k, t, blk,
+ * blk == 0 ? 0 : m), key (seed lo, seed hi)), blk = 0..3. */
+int pi_debug_noise(uint64_t seed, int K, int T, int m, uint32_t *raw, void *stream);
+
+/* Standard normals from those blocks by Box-Muller on (u0,u1), (u2,u3) with
+ * u = (2 (r >> 9) + 1) 2^-24: ctrl[k][t][4] from block 0, model[k][t][12] from
+ * blocks 1..3. */
+int pi_debug_normals(uint64_t seed, int K, int T, int m, float *ctrl, float *model, void *stream);
+
+/* LWPR prediction (Eq. 1) of the context's model at n inputs:
+ * z [n][16] -> y [n][12], var [n][12]. */
+int pi_debug_lwpr(pi_ctx *ctx, const float *z, int n, float *y, float *var);
+
+/* Rollout stage only: writes cost [T][K] (running cost averaged over the
+ * sub-rollouts), eps [T][K][4] and phi [K] (terminal cost, averaged). */
+int pi_debug_rollout(pi_ctx *ctx, const float *x0, const float *u_nominal, int K, int T,
+                     const float *sigma_u, uint64_t seed, float *cost, float *eps, float *phi);
+
+/* Cost-to-go and weighted-average stage only, from given cost [T][K],
+ * phi [K], eps [T][K][4]: writes u_out [T][4] and costs_out [K]. */
+int pi_debug_reduce(pi_ctx *ctx, const float *cost, const float *phi, const float *eps,
+                    const float *u_nominal, int K, int T, float lambda, float *u_out,
+                    float *costs_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PI2RH_H */

@@ -1,0 +1,102 @@
+"""ctypes view of the C ABI declared in ``include/pi2rh.h`` (argument marshalling only).
+
+The shared library is built in-tree by ``paper_1503_00330_b300.build``.  If it is
+missing, loading raises: there is no CPU fallback for any entry point.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "lib", "libpi2rh.so")
+HEADER = os.path.join(os.path.dirname(PKG), "include", "pi2rh.h")
+
+PI_OK, PI_ERR_INVALID_ARG, PI_ERR_OOM, PI_ERR_CUDA, PI_ERR_TIMEOUT, PI_ERR_INTERNAL, PI_ERR_UNSUPPORTED = range(7)
+ERR_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "TIMEOUT", 5: "INTERNAL", 6: "UNSUPPORTED"}
+
+_fp = ctypes.POINTER(ctypes.c_float)
+_vp = ctypes.c_void_p
+
+
+class LwprParamsC(ctypes.Structure):
+    _fields_ = [("n_in", ctypes.c_int), ("n_out", ctypes.c_int), ("L", ctypes.c_int), ("dt", ctypes.c_float),
+                ("c", _vp), ("D", _vp), ("beta", _vp), ("b", _vp), ("sigma", _vp)]
+
+
+class CostParamsC(ctypes.Structure):
+    _fields_ = [("goal", ctypes.c_float * 3), ("Q_pos", ctypes.c_float * 3), ("Q_vel", ctypes.c_float),
+                ("Q_ang", ctypes.c_float), ("w_obs", ctypes.c_float), ("obs_sharp", ctypes.c_float),
+                ("radius", ctypes.c_float), ("w_crash", ctypes.c_float), ("w_var", ctypes.c_float),
+                ("w_T", ctypes.c_float), ("obs_kind", ctypes.c_int), ("n_obs", ctypes.c_int),
+                ("obs_xy", _vp)]
+
+
+class OptsC(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("model_noise", ctypes.c_int), ("M", ctypes.c_int),
+                ("device", ctypes.c_int)]
+
+
+class PiError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"pi2rh error {ERR_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+# name -> (restype, argtypes)
+_SIGS = {
+    "pi_default_opts": (None, [ctypes.POINTER(OptsC)]),
+    "pi_create": (ctypes.c_int, [ctypes.POINTER(LwprParamsC), ctypes.POINTER(CostParamsC),
+                                 ctypes.POINTER(OptsC), ctypes.POINTER(_vp)]),
+    "pi_set_stream": (ctypes.c_int, [_vp, _vp]),
+    "pi_reserve": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
+    "pi_update": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_float, _fp,
+                                 ctypes.c_uint64, _vp, _vp]),
+    "pi_update_host": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_float, _fp,
+                                      ctypes.c_uint64, _vp, _vp]),
+    "pi_sync": (ctypes.c_int, [_vp]),
+    "pi_destroy": (None, [_vp]),
+    "pi_last_error": (ctypes.c_char_p, []),
+    "pi_launch_count": (ctypes.c_uint64, [_vp]),
+    "pi_debug_noise": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp]),
+    "pi_debug_normals": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp,
+                                        _vp]),
+    "pi_debug_lwpr": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _vp, _vp]),
+    "pi_debug_rollout": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, _fp, ctypes.c_uint64,
+                                        _vp, _vp, _vp]),
+    "pi_debug_reduce": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_float,
+                                       _vp, _vp]),
+}
+
+
+def load():
+    """Loads the in-tree library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -m paper_1503_00330_b300.build`; there is no CPU fallback")
+        lib = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def check(rc: int) -> None:
+    if rc != PI_OK:
+        msg = load().pi_last_error()
+        raise PiError(rc, msg.decode() if msg else "")
+
+
+def declared_functions() -> list[str]:
+    """Names of the functions declared in include/pi2rh.h."""
+    with open(HEADER) as f:
+        src = f.read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(pi_[a-z_]+)\s*\(", src)))

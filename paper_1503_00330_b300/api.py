@@ -1,0 +1,174 @@
+"""Python front end of the PI^2-RH / LWPR library.
+
+Thin marshalling over the C ABI (``include/pi2rh.h``): every step of the
+update runs in the library's CUDA kernels.  PyTorch provides device memory
+and the current CUDA stream; nothing here computes any part of the method.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import PiError, check  # noqa: F401
+from .workloads import CostParams, LwprModel
+
+NX, NU, NZ, NY = 12, 4, 16, 12
+
+
+def _ptr(t: torch.Tensor):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _f32_dev(a, device) -> torch.Tensor:
+    if isinstance(a, torch.Tensor):
+        return a.to(device=device, dtype=torch.float32).contiguous()
+    return torch.as_tensor(np.ascontiguousarray(a, np.float32), device=device)
+
+
+def _sigma4(sigma_u):
+    s = np.ascontiguousarray(np.asarray(sigma_u, np.float32).reshape(4))
+    return s, s.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+class Controller:
+    """One LWPR model + cost on one GPU (a ``pi_ctx``)."""
+
+    def __init__(self, model: LwprModel, cost: CostParams, M: int = 1, model_noise: bool = True,
+                 device: int = 0):
+        lib = _lib.load()
+        self._lib = lib
+        self.device = torch.device("cuda", device)
+        self.model, self.cost, self.M = model, cost, M
+        arrs = [np.ascontiguousarray(a, np.float32) for a in (model.c, model.D, model.beta, model.b, model.sigma)]
+        lw = _lib.LwprParamsC(NZ, NY, int(model.L), float(model.dt), *[a.ctypes.data for a in arrs])
+        obs = np.ascontiguousarray(np.asarray(cost.obs_xy, np.float32).reshape(-1, 2))
+        cp = _lib.CostParamsC((ctypes.c_float * 3)(*cost.goal), (ctypes.c_float * 3)(*cost.Q_pos),
+                              cost.Q_vel, cost.Q_ang, cost.w_obs, cost.obs_sharp, cost.radius,
+                              cost.w_crash, cost.w_var, cost.w_T, int(cost.obs_kind), int(obs.shape[0]),
+                              obs.ctypes.data if obs.size else None)
+        opts = _lib.OptsC(0, 1 if model_noise else 0, int(M), int(device))
+        h = ctypes.c_void_p()
+        check(lib.pi_create(ctypes.byref(lw), ctypes.byref(cp), ctypes.byref(opts), ctypes.byref(h)))
+        self._h = h
+        self._stream = None
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.pi_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    def _use_current_stream(self):
+        s = torch.cuda.current_stream(self.device).cuda_stream
+        if s != self._stream:
+            check(self._lib.pi_set_stream(self._h, ctypes.c_void_p(s)))
+            self._stream = s
+
+    def launch_count(self) -> int:
+        return int(self._lib.pi_launch_count(self._h))
+
+    def reserve(self, K: int, T: int):
+        self._use_current_stream()
+        check(self._lib.pi_reserve(self._h, K, T))
+
+    def update(self, x0, u_nom, K: int, T: int, lam: float, sigma_u, seed: int,
+               u_out: torch.Tensor | None = None, costs_out: torch.Tensor | None = None):
+        """pi_update on device tensors; returns (u_out [T,4], costs_out [K]) (async)."""
+        self._use_current_stream()
+        x0 = _f32_dev(x0, self.device)
+        u_nom = _f32_dev(u_nom, self.device)
+        if u_out is None:
+            u_out = torch.empty((T, NU), dtype=torch.float32, device=self.device)
+        if costs_out is None:
+            costs_out = torch.empty((K,), dtype=torch.float32, device=self.device)
+        _, sp = _sigma4(sigma_u)
+        check(self._lib.pi_update(self._h, _ptr(x0), _ptr(u_nom), K, T, float(lam), sp,
+                                  ctypes.c_uint64(seed), _ptr(u_out), _ptr(costs_out)))
+        return u_out, costs_out
+
+    def update_host(self, x0, u_nom, K: int, T: int, lam: float, sigma_u, seed: int,
+                    u_out: np.ndarray | None = None, costs_out: np.ndarray | None = None):
+        """pi_update_host on host (numpy) buffers; synchronous."""
+        self._use_current_stream()
+        x0 = np.ascontiguousarray(x0, np.float32)
+        u_nom = np.ascontiguousarray(u_nom, np.float32)
+        if u_out is None:
+            u_out = np.empty((T, NU), np.float32)
+        if costs_out is None:
+            costs_out = np.empty(K, np.float32)
+        _, sp = _sigma4(sigma_u)
+        check(self._lib.pi_update_host(self._h, x0.ctypes.data, u_nom.ctypes.data, K, T, float(lam), sp,
+                                       ctypes.c_uint64(seed), u_out.ctypes.data, costs_out.ctypes.data))
+        return u_out, costs_out
+
+    def sync(self):
+        check(self._lib.pi_sync(self._h))
+
+    # ------------------------------------------------------------- staged
+    def debug_lwpr(self, z):
+        self._use_current_stream()
+        z = _f32_dev(z, self.device).reshape(-1, NZ)
+        n = z.shape[0]
+        y = torch.empty((n, NY), dtype=torch.float32, device=self.device)
+        v = torch.empty((n, NY), dtype=torch.float32, device=self.device)
+        check(self._lib.pi_debug_lwpr(self._h, _ptr(z), n, _ptr(y), _ptr(v)))
+        return y, v
+
+    def debug_rollout(self, x0, u_nom, K, T, sigma_u, seed):
+        """Returns (cost [T,K], eps [T,K,4], phi [K])."""
+        self._use_current_stream()
+        x0 = _f32_dev(x0, self.device)
+        u_nom = _f32_dev(u_nom, self.device)
+        cost = torch.empty((T, K), dtype=torch.float32, device=self.device)
+        eps = torch.empty((T, K, NU), dtype=torch.float32, device=self.device)
+        phi = torch.empty((K,), dtype=torch.float32, device=self.device)
+        _, sp = _sigma4(sigma_u)
+        check(self._lib.pi_debug_rollout(self._h, _ptr(x0), _ptr(u_nom), K, T, sp, ctypes.c_uint64(seed),
+                                          _ptr(cost), _ptr(eps), _ptr(phi)))
+        return cost, eps, phi
+
+    def debug_reduce(self, cost_tk, phi, eps_tk, u_nom, lam):
+        """From cost [T,K], phi [K], eps [T,K,4] -> (u_out [T,4], costs_out [K])."""
+        self._use_current_stream()
+        cost_tk = _f32_dev(cost_tk, self.device)
+        phi = _f32_dev(phi, self.device)
+        eps_tk = _f32_dev(eps_tk, self.device)
+        u_nom = _f32_dev(u_nom, self.device)
+        T, K = cost_tk.shape
+        u_out = torch.empty((T, NU), dtype=torch.float32, device=self.device)
+        costs = torch.empty((K,), dtype=torch.float32, device=self.device)
+        check(self._lib.pi_debug_reduce(self._h, _ptr(cost_tk), _ptr(phi), _ptr(eps_tk), _ptr(u_nom), K, T,
+                                         float(lam), _ptr(u_out), _ptr(costs)))
+        return u_out, costs
+
+
+def debug_noise(seed: int, K: int, T: int, m: int = 0, device: int = 0) -> torch.Tensor:
+    """Raw Philox blocks [K, T, 4, 4] (uint32 stored in int32)."""
+    lib = _lib.load()
+    raw = torch.empty((K, T, 4, 4), dtype=torch.int32, device=torch.device("cuda", device))
+    s = torch.cuda.current_stream(raw.device).cuda_stream
+    check(lib.pi_debug_noise(ctypes.c_uint64(seed), K, T, m, _ptr(raw), ctypes.c_void_p(s)))
+    return raw
+
+
+def debug_normals(seed: int, K: int, T: int, m: int = 0, device: int = 0):
+    """(ctrl [K, T, 4], model [K, T, 12]) standard normals."""
+    lib = _lib.load()
+    dev = torch.device("cuda", device)
+    ctrl = torch.empty((K, T, 4), dtype=torch.float32, device=dev)
+    model = torch.empty((K, T, 12), dtype=torch.float32, device=dev)
+    s = torch.cuda.current_stream(dev).cuda_stream
+    check(lib.pi_debug_normals(ctypes.c_uint64(seed), K, T, m, _ptr(ctrl), _ptr(model), ctypes.c_void_p(s)))
+    return ctrl, model

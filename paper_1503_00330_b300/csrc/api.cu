@@ -1,0 +1,487 @@
+// api.cu -- the extern "C" boundary of the library (declared in pi2rh.h):
+// context creation (model validation and packing), scratch management,
+// launches of the update pipeline, the host-buffer path, error reporting and
+// host-side fault injection (PI_FAULT=alloc|launch|timeout).
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "pi2rh.h"
+#include "pi2rh_kernels.h"
+
+using namespace pi2rh;
+
+struct pi_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    pi_opts opts{};
+    int L = 0, P = 0, spo = 0;
+    float dt = 0.f;
+    float2 *d_rec = nullptr;   // packed model [NY][P][REC_LEN]
+    float2 *d_obs = nullptr;
+    CostDev cost{};
+    int *d_err = nullptr;
+    // per-update scratch
+    float *d_cost = nullptr;   // [T][K]
+    float4 *d_eps = nullptr;   // [T][K]
+    float *d_phi = nullptr;    // [K]
+    double *d_part = nullptr;  // [nblk][T][6]
+    size_t cap_cost = 0, cap_eps = 0, cap_phi = 0, cap_part = 0;
+    // staging for the host-buffer path
+    float *d_x0 = nullptr, *d_unom = nullptr, *d_uout = nullptr, *d_costs = nullptr;
+    size_t cap_x0 = 0, cap_unom = 0, cap_uout = 0, cap_costs = 0;
+    uint64_t launches = 0;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what)
+{
+    if (e == cudaErrorMemoryAllocation)
+        return fail(PI_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
+    return fail(PI_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define PI_CUDA(call, what)                                    \
+    do {                                                       \
+        cudaError_t e_ = (call);                               \
+        if (e_ != cudaSuccess) return cuda_fail(e_, (what));   \
+    } while (0)
+
+#define PI_TRY(call)                 \
+    do {                             \
+        int rc_ = (call);            \
+        if (rc_ != PI_OK) return rc_; \
+    } while (0)
+
+// Restores the caller's current device on scope exit.
+struct DeviceGuard {
+    int prev = -1;
+    cudaError_t err = cudaSuccess;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) err = cudaSetDevice(dev);
+    }
+    ~DeviceGuard()
+    {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+// Host-side fault injection: PI_FAULT=alloc|launch|timeout makes the update
+// entry points return the matching error before touching the GPU.
+int injected_fault()
+{
+    const char *f = getenv("PI_FAULT");
+    if (!f || !*f) return PI_OK;
+    if (!strcmp(f, "alloc")) return fail(PI_ERR_OOM, "injected fault: allocation");
+    if (!strcmp(f, "launch")) return fail(PI_ERR_CUDA, "injected fault: launch");
+    if (!strcmp(f, "timeout")) return fail(PI_ERR_TIMEOUT, "injected fault: device wait timeout");
+    return PI_OK;
+}
+
+bool finite_all(const float *p, size_t n)
+{
+    for (size_t i = 0; i < n; ++i)
+        if (!std::isfinite(p[i])) return false;
+    return true;
+}
+
+template <class T>
+int grow(T **ptr, size_t *cap, size_t need, cudaStream_t s, const char *what)
+{
+    if (need <= *cap) return PI_OK;
+    size_t n = need < 2 * *cap ? 2 * *cap : need;
+    if (*ptr) PI_CUDA(cudaFreeAsync(*ptr, s), what);
+    *ptr = nullptr;
+    *cap = 0;
+    PI_CUDA(cudaMallocAsync((void **)ptr, n * sizeof(T), s), what);
+    *cap = n;
+    return PI_OK;
+}
+
+int ensure_scratch(pi_ctx *c, int K, int T)
+{
+    const size_t kt = (size_t)K * T;
+    PI_TRY(grow(&c->d_cost, &c->cap_cost, kt, c->stream, "scratch cost"));
+    PI_TRY(grow(&c->d_eps, &c->cap_eps, kt, c->stream, "scratch eps"));
+    PI_TRY(grow(&c->d_phi, &c->cap_phi, (size_t)K, c->stream, "scratch phi"));
+    PI_TRY(grow(&c->d_part, &c->cap_part, (size_t)scan_blocks(K) * T * 6, c->stream, "scratch partials"));
+    return PI_OK;
+}
+
+int check_sizes(int K, int T, int M)
+{
+    if (K < 1 || T < 1) return fail(PI_ERR_INVALID_ARG, "K and T must be >= 1 (K=%d, T=%d)", K, T);
+    if ((long long)K * M > (1LL << 31) - 1 || (long long)K * T > (1LL << 40))
+        return fail(PI_ERR_INVALID_ARG, "problem too large (K=%d, T=%d, M=%d)", K, T, M);
+    return PI_OK;
+}
+
+int check_update_args(const float *lambda_p, float lambda, const float *sigma_u)
+{
+    (void)lambda_p;
+    if (!(lambda > 0.0f) || !std::isfinite(lambda))
+        return fail(PI_ERR_INVALID_ARG, "lambda must be finite and > 0 (got %g)", (double)lambda);
+    if (!sigma_u) return fail(PI_ERR_INVALID_ARG, "sigma_u is NULL");
+    for (int i = 0; i < 4; ++i)
+        if (!std::isfinite(sigma_u[i]) || sigma_u[i] < 0.0f)
+            return fail(PI_ERR_INVALID_ARG, "sigma_u[%d] must be finite and >= 0", i);
+    return PI_OK;
+}
+
+RolloutArgs base_args(const pi_ctx *c)
+{
+    RolloutArgs a{};
+    a.rec = c->d_rec;
+    a.P = c->P;
+    a.stages_per_out = c->spo;
+    a.cost = c->cost;
+    a.dt = c->dt;
+    a.M = c->opts.M;
+    a.model_noise = c->opts.model_noise == PI_NOISE_SAMPLED ? 1 : 0;
+    a.err = c->d_err;
+    return a;
+}
+
+int launch_rollouts(pi_ctx *c, const float *x0, const float *u_nom, int K, int T,
+                    const float *sigma_u, uint64_t seed, float *cost, float4 *eps, float *phi)
+{
+    RolloutArgs a = base_args(c);
+    a.K = K;
+    a.T = T;
+    for (int i = 0; i < 4; ++i) a.sqrt_sigma_u[i] = sqrtf(sigma_u[i]);
+    a.seed = seed;
+    a.x0 = x0;
+    a.u_nom = u_nom;
+    a.cost_tk = cost;
+    a.eps_tk = eps;
+    a.phi = phi;
+    PI_CUDA(launch_rollout_fp32(a, c->stream), "rollout kernel launch");
+    c->launches++;
+    return PI_OK;
+}
+
+int launch_reduce(pi_ctx *c, const float *cost, const float *phi, const float4 *eps,
+                  const float *u_nom, int K, int T, float lambda, float *u_out, float *costs_out)
+{
+    const double inv_lam_log2e = 1.4426950408889634074 / (double)lambda;
+    PI_CUDA(launch_scan_lse(cost, phi, eps, K, T, c->dt, inv_lam_log2e, costs_out, c->d_part,
+                            c->stream),
+            "scan kernel launch");
+    c->launches++;
+    PI_CUDA(launch_lse_merge(c->d_part, scan_blocks(K), T, inv_lam_log2e, u_nom, u_out, c->stream),
+            "merge kernel launch");
+    c->launches++;
+    return PI_OK;
+}
+
+void free_ctx_memory(pi_ctx *c)
+{
+    void *ptrs[] = {c->d_rec, c->d_obs, c->d_err, c->d_cost, c->d_eps, c->d_phi, c->d_part,
+                    c->d_x0, c->d_unom, c->d_uout, c->d_costs};
+    for (void *p : ptrs)
+        if (p) cudaFreeAsync(p, c->stream);
+    cudaStreamSynchronize(c->stream);
+}
+
+}  // namespace
+
+extern "C" {
+
+void pi_default_opts(pi_opts *o)
+{
+    if (!o) return;
+    o->precision = PI_PRECISION_FP32;
+    o->model_noise = PI_NOISE_SAMPLED;
+    o->M = 1;
+    o->device = 0;
+}
+
+const char *pi_last_error(void) { return g_err.c_str(); }
+
+uint64_t pi_launch_count(const pi_ctx *c) { return c ? c->launches : 0; }
+
+int pi_create(const pi_lwpr_params *lw, const pi_cost_params *cp, const pi_opts *opts_in, pi_ctx **out)
+{
+    if (!out) return fail(PI_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!lw || !cp) return fail(PI_ERR_INVALID_ARG, "lwpr or cost params are NULL");
+    pi_opts opts;
+    pi_default_opts(&opts);
+    if (opts_in) opts = *opts_in;
+    if (lw->n_in != NZ || lw->n_out != NY)
+        return fail(PI_ERR_INVALID_ARG, "n_in must be %d and n_out %d (got %d, %d)", NZ, NY, lw->n_in,
+                    lw->n_out);
+    if (lw->L < 1 || lw->L > (1 << 20)) return fail(PI_ERR_INVALID_ARG, "L out of range (%d)", lw->L);
+    if (!(lw->dt > 0.0f) || !std::isfinite(lw->dt)) return fail(PI_ERR_INVALID_ARG, "dt must be > 0");
+    if (!lw->c || !lw->D || !lw->beta || !lw->b || !lw->sigma)
+        return fail(PI_ERR_INVALID_ARG, "an LWPR array is NULL");
+    if (opts.precision != PI_PRECISION_FP32)
+        return fail(PI_ERR_UNSUPPORTED, "precision %d is not available", opts.precision);
+    if (opts.model_noise != PI_NOISE_SAMPLED && opts.model_noise != PI_NOISE_MEAN_ONLY)
+        return fail(PI_ERR_INVALID_ARG, "model_noise must be 0 or 1");
+    if (opts.M < 1 || opts.M > PI2RH_MAX_M || (opts.M & (opts.M - 1)))
+        return fail(PI_ERR_INVALID_ARG, "M must be a power of two in [1, %d] (got %d)", PI2RH_MAX_M, opts.M);
+    if (cp->n_obs < 0 || cp->n_obs > PI2RH_MAX_OBS)
+        return fail(PI_ERR_INVALID_ARG, "n_obs must be in [0, %d]", PI2RH_MAX_OBS);
+    if (cp->n_obs > 0 && !cp->obs_xy) return fail(PI_ERR_INVALID_ARG, "obs_xy is NULL");
+    if (cp->obs_kind != PI_OBS_INDICATOR && cp->obs_kind != PI_OBS_GAUSSIAN)
+        return fail(PI_ERR_INVALID_ARG, "obs_kind must be 0 or 1");
+    const int L = lw->L;
+    const size_t nf = (size_t)NY * L;
+    if (!finite_all(lw->c, nf * NZ) || !finite_all(lw->D, nf * NZ * NZ) ||
+        !finite_all(lw->beta, nf * NZ) || !finite_all(lw->b, nf) || !finite_all(lw->sigma, nf))
+        return fail(PI_ERR_INVALID_ARG, "LWPR parameters must be finite");
+    const float scal[] = {cp->goal[0], cp->goal[1], cp->goal[2], cp->Q_pos[0], cp->Q_pos[1],
+                          cp->Q_pos[2], cp->Q_vel, cp->Q_ang, cp->w_obs, cp->obs_sharp,
+                          cp->radius, cp->w_crash, cp->w_var, cp->w_T};
+    if (!finite_all(scal, sizeof scal / sizeof scal[0]) ||
+        (cp->n_obs > 0 && !finite_all(cp->obs_xy, (size_t)2 * cp->n_obs)))
+        return fail(PI_ERR_INVALID_ARG, "cost parameters must be finite");
+
+    // Pack field pairs (see the record layout in pi2rh_device.cuh).
+    const int P = (L + 1) / 2;
+    std::vector<float2> rec((size_t)NY * P * REC_LEN, make_float2(0.f, 0.f));
+    const double kap = 0.72134752044448170368;   // log2(e) / 2
+    for (int o = 0; o < NY; ++o) {
+        for (int j = 0; j < L; ++j) {
+            float2 *r = &rec[((size_t)o * P + j / 2) * REC_LEN];
+            const int h = j & 1;
+            auto put = [&](int e, float v) {
+                if (h) r[e].y = v; else r[e].x = v;
+            };
+            const size_t f = (size_t)o * L + j;
+            const float *c = lw->c + f * NZ;
+            const float *D = lw->D + f * NZ * NZ;
+            for (int a = 0; a < NZ; ++a) put(REC_NEGC + a, -c[a]);
+            for (int i = 0; i < NZ; ++i)
+                for (int jj = i; jj < NZ; ++jj) {
+                    double v = (i == jj) ? -kap * (double)D[i * NZ + i]
+                                         : -kap * ((double)D[i * NZ + jj] + (double)D[jj * NZ + i]);
+                    put(REC_A + tri_index(i, jj), (float)v);
+                }
+            for (int a = 0; a < NZ; ++a) put(REC_BETA + a, lw->beta[f * NZ + a]);
+            put(REC_B, lw->b[f]);
+            const double s = (double)lw->sigma[f];
+            put(REC_VAR, (float)(s * s));
+            put(REC_BIAS, 0.0f);
+        }
+        if (L & 1) rec[((size_t)o * P + P - 1) * REC_LEN + REC_BIAS].y = -INFINITY;
+    }
+
+    pi_ctx *c = new pi_ctx();
+    c->device = opts.device;
+    c->opts = opts;
+    c->L = L;
+    c->P = P;
+    c->spo = (P + RF_PAIRS_PER_STAGE - 1) / RF_PAIRS_PER_STAGE;
+    c->dt = lw->dt;
+    DeviceGuard dg(opts.device);
+    if (dg.err != cudaSuccess) {
+        delete c;
+        return cuda_fail(dg.err, "cudaSetDevice");
+    }
+    auto bail = [&](cudaError_t e, const char *what) {
+        free_ctx_memory(c);
+        delete c;
+        return cuda_fail(e, what);
+    };
+    cudaError_t e;
+    if ((e = cudaMalloc(&c->d_rec, rec.size() * sizeof(float2))) != cudaSuccess) return bail(e, "model alloc");
+    if ((e = cudaMemcpy(c->d_rec, rec.data(), rec.size() * sizeof(float2), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return bail(e, "model copy");
+    const int nob = cp->n_obs > 0 ? cp->n_obs : 1;
+    if ((e = cudaMalloc(&c->d_obs, nob * sizeof(float2))) != cudaSuccess) return bail(e, "obstacle alloc");
+    if (cp->n_obs > 0 &&
+        (e = cudaMemcpy(c->d_obs, cp->obs_xy, cp->n_obs * sizeof(float2), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return bail(e, "obstacle copy");
+    if ((e = cudaMalloc(&c->d_err, sizeof(int))) != cudaSuccess) return bail(e, "error word alloc");
+    if ((e = cudaMemset(c->d_err, 0, sizeof(int))) != cudaSuccess) return bail(e, "error word clear");
+    CostDev &C = c->cost;
+    for (int d = 0; d < 3; ++d) {
+        C.goal[d] = cp->goal[d];
+        C.Q_pos[d] = cp->Q_pos[d];
+    }
+    C.Q_vel = cp->Q_vel;
+    C.Q_ang = cp->Q_ang;
+    C.w_obs = cp->w_obs;
+    C.obs_sharp = cp->obs_sharp;
+    C.radius = cp->radius;
+    C.w_crash = cp->w_crash;
+    C.w_var = cp->w_var;
+    C.w_T = cp->w_T;
+    C.obs_kind = cp->obs_kind;
+    C.n_obs = cp->n_obs;
+    C.obs = c->d_obs;
+    *out = c;
+    return PI_OK;
+}
+
+int pi_set_stream(pi_ctx *c, void *stream)
+{
+    if (!c) return fail(PI_ERR_INVALID_ARG, "ctx is NULL");
+    DeviceGuard dg(c->device);
+    PI_CUDA(dg.err, "cudaSetDevice");
+    // Scratch is stream-ordered: finish the old stream's work before switching.
+    PI_CUDA(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+    c->stream = (cudaStream_t)stream;
+    return PI_OK;
+}
+
+int pi_reserve(pi_ctx *c, int K, int T)
+{
+    if (!c) return fail(PI_ERR_INVALID_ARG, "ctx is NULL");
+    PI_TRY(check_sizes(K, T, c->opts.M));
+    DeviceGuard dg(c->device);
+    PI_CUDA(dg.err, "cudaSetDevice");
+    return ensure_scratch(c, K, T);
+}
+
+int pi_update(pi_ctx *c, const float *x0, const float *u_nom, int K, int T, float lambda,
+              const float *sigma_u, uint64_t seed, float *u_out, float *costs_out)
+{
+    if (!c) return fail(PI_ERR_INVALID_ARG, "ctx is NULL");
+    if (!x0 || !u_nom || !u_out || !costs_out) return fail(PI_ERR_INVALID_ARG, "a buffer is NULL");
+    PI_TRY(check_sizes(K, T, c->opts.M));
+    PI_TRY(check_update_args(nullptr, lambda, sigma_u));
+    PI_TRY(injected_fault());
+    DeviceGuard dg(c->device);
+    PI_CUDA(dg.err, "cudaSetDevice");
+    PI_TRY(ensure_scratch(c, K, T));
+    PI_TRY(launch_rollouts(c, x0, u_nom, K, T, sigma_u, seed, c->d_cost, c->d_eps, c->d_phi));
+    return launch_reduce(c, c->d_cost, c->d_phi, c->d_eps, u_nom, K, T, lambda, u_out, costs_out);
+}
+
+int pi_sync(pi_ctx *c)
+{
+    if (!c) return fail(PI_ERR_INVALID_ARG, "ctx is NULL");
+    DeviceGuard dg(c->device);
+    PI_CUDA(dg.err, "cudaSetDevice");
+    PI_CUDA(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+    int err = 0;
+    PI_CUDA(cudaMemcpy(&err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost), "error word read");
+    if (err) {
+        PI_CUDA(cudaMemset(c->d_err, 0, sizeof(int)), "error word clear");
+        if (err & (DEVERR_TIMEOUT_FULL | DEVERR_TIMEOUT_EMPTY | DEVERR_TIMEOUT_DRAIN))
+            return fail(PI_ERR_TIMEOUT, "a bounded device-side wait expired (flags 0x%x)", err);
+        return fail(PI_ERR_INTERNAL, "device-side check failed (flags 0x%x)", err);
+    }
+    return PI_OK;
+}
+
+int pi_update_host(pi_ctx *c, const float *x0, const float *u_nom, int K, int T, float lambda,
+                   const float *sigma_u, uint64_t seed, float *u_out, float *costs_out)
+{
+    if (!c) return fail(PI_ERR_INVALID_ARG, "ctx is NULL");
+    if (!x0 || !u_nom || !u_out || !costs_out) return fail(PI_ERR_INVALID_ARG, "a buffer is NULL");
+    PI_TRY(check_sizes(K, T, c->opts.M));
+    PI_TRY(check_update_args(nullptr, lambda, sigma_u));
+    PI_TRY(injected_fault());
+    DeviceGuard dg(c->device);
+    PI_CUDA(dg.err, "cudaSetDevice");
+    PI_TRY(grow(&c->d_x0, &c->cap_x0, (size_t)NX, c->stream, "staging x0"));
+    PI_TRY(grow(&c->d_unom, &c->cap_unom, (size_t)T * NU, c->stream, "staging u_nom"));
+    PI_TRY(grow(&c->d_uout, &c->cap_uout, (size_t)T * NU, c->stream, "staging u_out"));
+    PI_TRY(grow(&c->d_costs, &c->cap_costs, (size_t)K, c->stream, "staging costs"));
+    PI_CUDA(cudaMemcpyAsync(c->d_x0, x0, NX * sizeof(float), cudaMemcpyHostToDevice, c->stream), "copy x0");
+    PI_CUDA(cudaMemcpyAsync(c->d_unom, u_nom, (size_t)T * NU * sizeof(float), cudaMemcpyHostToDevice, c->stream),
+            "copy u_nom");
+    PI_TRY(pi_update(c, c->d_x0, c->d_unom, K, T, lambda, sigma_u, seed, c->d_uout, c->d_costs));
+    PI_CUDA(cudaMemcpyAsync(u_out, c->d_uout, (size_t)T * NU * sizeof(float), cudaMemcpyDeviceToHost, c->stream),
+            "copy u_out");
+    PI_CUDA(cudaMemcpyAsync(costs_out, c->d_costs, (size_t)K * sizeof(float), cudaMemcpyDeviceToHost, c->stream),
+            "copy costs");
+    return pi_sync(c);
+}
+
+void pi_destroy(pi_ctx *c)
+{
+    if (!c) return;
+    DeviceGuard dg(c->device);
+    cudaStreamSynchronize(c->stream);
+    free_ctx_memory(c);
+    delete c;
+}
+
+int pi_debug_noise(uint64_t seed, int K, int T, int m, uint32_t *raw, void *stream)
+{
+    PI_TRY(check_sizes(K, T, 1));
+    if (!raw || m < 0) return fail(PI_ERR_INVALID_ARG, "bad argument");
+    PI_CUDA(launch_noise_raw(seed, K, T, m, raw, (cudaStream_t)stream), "noise kernel launch");
+    return PI_OK;
+}
+
+int pi_debug_normals(uint64_t seed, int K, int T, int m, float *ctrl, float *model, void *stream)
+{
+    PI_TRY(check_sizes(K, T, 1));
+    if (!ctrl || !model || m < 0) return fail(PI_ERR_INVALID_ARG, "bad argument");
+    PI_CUDA(launch_noise_normals(seed, K, T, m, ctrl, model, (cudaStream_t)stream), "normals kernel launch");
+    return PI_OK;
+}
+
+int pi_debug_lwpr(pi_ctx *c, const float *z, int n, float *y, float *var)
+{
+    if (!c) return fail(PI_ERR_INVALID_ARG, "ctx is NULL");
+    if (n < 1 || !z || !y || !var) return fail(PI_ERR_INVALID_ARG, "bad argument");
+    DeviceGuard dg(c->device);
+    PI_CUDA(dg.err, "cudaSetDevice");
+    RolloutArgs a = base_args(c);
+    a.M = 1;
+    a.z_in = z;
+    a.y_out = y;
+    a.var_out = var;
+    a.n_pred = n;
+    PI_CUDA(launch_predict_fp32(a, c->stream), "predict kernel launch");
+    c->launches++;
+    return PI_OK;
+}
+
+int pi_debug_rollout(pi_ctx *c, const float *x0, const float *u_nom, int K, int T,
+                     const float *sigma_u, uint64_t seed, float *cost, float *eps, float *phi)
+{
+    if (!c) return fail(PI_ERR_INVALID_ARG, "ctx is NULL");
+    if (!x0 || !u_nom || !cost || !eps || !phi) return fail(PI_ERR_INVALID_ARG, "a buffer is NULL");
+    PI_TRY(check_sizes(K, T, c->opts.M));
+    PI_TRY(check_update_args(nullptr, 1.0f, sigma_u));
+    DeviceGuard dg(c->device);
+    PI_CUDA(dg.err, "cudaSetDevice");
+    return launch_rollouts(c, x0, u_nom, K, T, sigma_u, seed, cost, reinterpret_cast<float4 *>(eps), phi);
+}
+
+int pi_debug_reduce(pi_ctx *c, const float *cost, const float *phi, const float *eps,
+                    const float *u_nom, int K, int T, float lambda, float *u_out, float *costs_out)
+{
+    if (!c) return fail(PI_ERR_INVALID_ARG, "ctx is NULL");
+    if (!cost || !phi || !eps || !u_nom || !u_out || !costs_out)
+        return fail(PI_ERR_INVALID_ARG, "a buffer is NULL");
+    PI_TRY(check_sizes(K, T, 1));
+    const float zero4[4] = {0.f, 0.f, 0.f, 0.f};
+    PI_TRY(check_update_args(nullptr, lambda, zero4));
+    DeviceGuard dg(c->device);
+    PI_CUDA(dg.err, "cudaSetDevice");
+    PI_TRY(grow(&c->d_part, &c->cap_part, (size_t)scan_blocks(K) * T * 6, c->stream, "scratch partials"));
+    return launch_reduce(c, cost, phi, reinterpret_cast<const float4 *>(eps), u_nom, K, T, lambda, u_out,
+                         costs_out);
+}
+
+}  // extern "C"

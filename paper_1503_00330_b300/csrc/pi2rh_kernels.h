@@ -1,0 +1,55 @@
+// pi2rh_kernels.h -- host-side launch interface of the kernels (internal).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "pi2rh_device.cuh"
+
+namespace pi2rh {
+
+// Arguments of the fused rollout kernel (also used in prediction-only mode).
+struct RolloutArgs {
+    const float2 *rec;       // packed model [NY][P][REC_LEN]
+    int P;                   // field pairs per output
+    int stages_per_out;      // ceil(P / pairs per stage)
+    CostDev cost;
+    float dt;
+    int K, T, M;             // rollouts, steps, sub-rollouts per rollout
+    int model_noise;         // 1 = sampled next state, 0 = mean only
+    float sqrt_sigma_u[4];   // control-noise standard deviations
+    uint64_t seed;
+    const float *x0;         // [NX]
+    const float *u_nom;      // [T][NU]
+    float *cost_tk;          // [T][K] running cost (mean over sub-rollouts)
+    float4 *eps_tk;          // [T][K] control perturbations
+    float *phi;              // [K] terminal cost (mean over sub-rollouts)
+    const float *z_in;       // prediction mode: [n_pred][NZ]
+    float *y_out, *var_out;  // prediction mode: [n_pred][NY]
+    int n_pred;
+    int *err;                // device error word
+};
+
+// Rollout slots (rollout x sub-rollout) per CTA of the FP32 rollout kernel.
+constexpr int RF_SLOTS = 64;
+constexpr int RF_CONSUMER_WARPS = 8;
+constexpr int RF_PAIRS_PER_STAGE = RF_CONSUMER_WARPS;
+
+cudaError_t launch_rollout_fp32(const RolloutArgs &a, cudaStream_t s);
+cudaError_t launch_predict_fp32(const RolloutArgs &a, cudaStream_t s);
+
+// Cost-to-go scan + per-CTA log-sum-exp partials, then the merge over CTAs.
+constexpr int RS_KC = 64;   // rollouts per CTA of the scan kernel
+int scan_blocks(int K);
+cudaError_t launch_scan_lse(const float *cost_tk, const float *phi, const float4 *eps_tk, int K,
+                            int T, float dt, double inv_lam_log2e, float *costs_out, double *part,
+                            cudaStream_t s);
+cudaError_t launch_lse_merge(const double *part, int nblk, int T, double inv_lam_log2e,
+                             const float *u_nom, float *u_out, cudaStream_t s);
+
+// Staged noise kernels.
+cudaError_t launch_noise_raw(uint64_t seed, int K, int T, int m, uint32_t *raw, cudaStream_t s);
+cudaError_t launch_noise_normals(uint64_t seed, int K, int T, int m, float *ctrl, float *model,
+                                 cudaStream_t s);
+
+}  // namespace pi2rh

@@ -1,0 +1,181 @@
+// reduce.cu -- cost-to-go scan and the per-timestep weighted average (Eq. 2).
+//
+// scan_lse_kernel: one CTA per RS_KC = 64 rollouts.  The timesteps are walked
+// from T-1 down to 0 in chunks of TC: one thread per rollout extends its
+// suffix sum S_{k,i} = phi_k + dt sum_{j>=i} q_{k,j} in FP64 (Sec. 3.1) and
+// parks the chunk in shared memory; then each warp takes whole timesteps of
+// the chunk and forms, over the CTA's 64 rollouts, the log-sum-exp partial
+//     m_c = min_k S,  Z_c = sum_k 2^((m_c - S) log2(e)/lambda),
+//     V_c = sum_k 2^(...) eps_k
+// (exponent in FP64, exponential and the 2-term lane sums in FP32, warp sums
+// in FP64).  cost and eps are read once, coalesced and vectorised ([T][K]
+// layout, eps as float4).  costs_out[k] = S_{k,0}.
+//
+// lse_merge_kernel: one warp per timestep merges the per-CTA partials in a
+// fixed order (deterministic) in FP64 and writes u_out = u_nom + V / Z.
+#include "pi2rh_kernels.h"
+
+namespace pi2rh {
+
+namespace {
+
+constexpr int KC = RS_KC;
+constexpr int TC = 32;
+constexpr int NT = 256;
+
+__device__ __forceinline__ double warp_min_d(double v)
+{
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, off));
+    return v;
+}
+
+__device__ __forceinline__ double warp_sum_d(double v)
+{
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
+}
+
+__global__ void __launch_bounds__(NT) scan_lse_kernel(const float *__restrict__ cost_tk,
+                                                      const float *__restrict__ phi,
+                                                      const float4 *__restrict__ eps_tk, int K, int T,
+                                                      double dt, double inv_lam_log2e,
+                                                      float *__restrict__ costs_out,
+                                                      double *__restrict__ part)
+{
+    __shared__ double S_s[TC][KC];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int k0 = blockIdx.x * KC;
+    const int k = k0 + tid;
+    double acc = 0.0;
+    if (tid < KC && k < K) acc = (double)phi[k];
+
+    for (int hi = T; hi > 0; hi -= TC) {
+        const int lo = hi > TC ? hi - TC : 0;
+        if (tid < KC) {
+            for (int i = hi - 1; i >= lo; --i) {
+                double s = INFINITY;
+                if (k < K) {
+                    acc += (double)cost_tk[(size_t)i * K + k] * dt;
+                    s = acc;
+                }
+                S_s[i - lo][tid] = s;
+            }
+            if (lo == 0 && k < K) costs_out[k] = (float)acc;
+        }
+        __syncthreads();
+        for (int r = warp; r < hi - lo; r += NT / 32) {
+            const int i = lo + r;
+            const double sa = S_s[r][lane], sb = S_s[r][lane + 32];
+            const double mn = warp_min_d(fmin(sa, sb));
+            const float wa = exp2f((float)((mn - sa) * inv_lam_log2e));
+            const float wb = exp2f((float)((mn - sb) * inv_lam_log2e));
+            const int ka = k0 + lane, kb = k0 + lane + 32;
+            const float4 ea = ka < K ? eps_tk[(size_t)i * K + ka] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 eb = kb < K ? eps_tk[(size_t)i * K + kb] : make_float4(0.f, 0.f, 0.f, 0.f);
+            double z = warp_sum_d((double)(wa + wb));
+            double v0 = warp_sum_d((double)fmaf(wa, ea.x, wb * eb.x));
+            double v1 = warp_sum_d((double)fmaf(wa, ea.y, wb * eb.y));
+            double v2 = warp_sum_d((double)fmaf(wa, ea.z, wb * eb.z));
+            double v3 = warp_sum_d((double)fmaf(wa, ea.w, wb * eb.w));
+            if (lane == 0) {
+                double *p = part + ((size_t)blockIdx.x * T + i) * 6;
+                p[0] = mn;
+                p[1] = z;
+                p[2] = v0;
+                p[3] = v1;
+                p[4] = v2;
+                p[5] = v3;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(256) lse_merge_kernel(const double *__restrict__ part, int nblk, int T,
+                                                        double inv_lam_log2e,
+                                                        const float *u_nom, float *u_out)
+{
+    const int lane = threadIdx.x & 31;
+    const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (i >= T) return;
+    double mn = INFINITY;
+    for (int c = lane; c < nblk; c += 32) mn = fmin(mn, part[((size_t)c * T + i) * 6]);
+    mn = warp_min_d(mn);
+    double z = 0.0, v[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int c = lane; c < nblk; c += 32) {
+        const double *p = part + ((size_t)c * T + i) * 6;
+        const double sc = exp2((mn - p[0]) * inv_lam_log2e);
+        z = fma(p[1], sc, z);
+#pragma unroll
+        for (int a = 0; a < 4; ++a) v[a] = fma(p[2 + a], sc, v[a]);
+    }
+    z = warp_sum_d(z);
+#pragma unroll
+    for (int a = 0; a < 4; ++a) v[a] = warp_sum_d(v[a]);
+    if (lane < 4) {
+        const double va = lane == 0 ? v[0] : lane == 1 ? v[1] : lane == 2 ? v[2] : v[3];
+        u_out[(size_t)i * 4 + lane] = (float)((double)u_nom[(size_t)i * 4 + lane] + va / z);
+    }
+}
+
+__global__ void noise_raw_kernel(uint64_t seed, int K, int T, int m, uint4 *raw)
+{
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)K * T) return;
+    const int k = (int)(idx / T), t = (int)(idx % T);
+    for (int blk = 0; blk < 4; ++blk)
+        raw[idx * 4 + blk] = noise_block(seed, (uint32_t)k, (uint32_t)t, (uint32_t)blk,
+                                         blk == 0 ? 0u : (uint32_t)m);
+}
+
+__global__ void noise_normals_kernel(uint64_t seed, int K, int T, int m, float4 *ctrl, float4 *model)
+{
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)K * T) return;
+    const int k = (int)(idx / T), t = (int)(idx % T);
+    ctrl[idx] = box_muller4(noise_block(seed, (uint32_t)k, (uint32_t)t, 0u, 0u));
+    for (int blk = 1; blk < 4; ++blk)
+        model[idx * 3 + blk - 1] =
+            box_muller4(noise_block(seed, (uint32_t)k, (uint32_t)t, (uint32_t)blk, (uint32_t)m));
+}
+
+}  // namespace
+
+int scan_blocks(int K) { return (K + KC - 1) / KC; }
+
+cudaError_t launch_scan_lse(const float *cost_tk, const float *phi, const float4 *eps_tk, int K,
+                            int T, float dt, double inv_lam_log2e, float *costs_out, double *part,
+                            cudaStream_t s)
+{
+    scan_lse_kernel<<<scan_blocks(K), NT, 0, s>>>(cost_tk, phi, eps_tk, K, T, (double)dt,
+                                                  inv_lam_log2e, costs_out, part);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lse_merge(const double *part, int nblk, int T, double inv_lam_log2e,
+                             const float *u_nom, float *u_out, cudaStream_t s)
+{
+    lse_merge_kernel<<<(T + 7) / 8, 256, 0, s>>>(part, nblk, T, inv_lam_log2e, u_nom, u_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_noise_raw(uint64_t seed, int K, int T, int m, uint32_t *raw, cudaStream_t s)
+{
+    const long long n = (long long)K * T;
+    noise_raw_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(seed, K, T, m,
+                                                                 reinterpret_cast<uint4 *>(raw));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_noise_normals(uint64_t seed, int K, int T, int m, float *ctrl, float *model,
+                                 cudaStream_t s)
+{
+    const long long n = (long long)K * T;
+    noise_normals_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
+        seed, K, T, m, reinterpret_cast<float4 *>(ctrl), reinterpret_cast<float4 *>(model));
+    return cudaGetLastError();
+}
+
+}  // namespace pi2rh

@@ -1,0 +1,431 @@
+// rollout_fp32.cu -- fused FP32 rollout kernel of one PI^2-RH update.
+//
+// One CTA owns RF_SLOTS = 64 rollout slots (rollout k, sub-rollout m) for all
+// T steps.  Per step and per output o it evaluates every receptive field of
+// the LWPR model (Sec. 2, Eq. 1) for its 64 slots:
+//     d = z - c_j,  s_j = -(1/2) log2(e) d^T D_j d,  e_j = b_j + beta_j . d - y_ref
+// and folds them into an online (max-shifted) base-2 softmax that carries
+//     sum w, sum w e, sum w e^2, sum w sigma_j^2
+// so that the mean y = y_ref + S1/S0 and the variance
+//     sum_j w_j ((y - y_j)^2 + sigma_j^2) = S2/S0 - (S1/S0)^2 + S3/S0
+// come out of one pass (y_ref is the slot's previous mean of that output, so
+// the spread term does not cancel).  Then the slot's running cost, the sampled
+// Euler step x + dt (y + sigma n) (Sec. 3.2) and the next control perturbation
+// are computed, with Philox noise generated in the kernel.
+//
+// Data movement: the model is far larger than shared memory (12 L records of
+// 1376 bytes per field pair), so it is streamed through a ring of NSTAGE
+// shared-memory stages by one producer warp issuing 1-D bulk asynchronous
+// copies (TMA) that complete on mbarriers; eight consumer warps each take one
+// field-pair record per stage.  All 32 lanes of a consumer warp read the same
+// record (shared-memory broadcast), and each lane evaluates it for two slots,
+// so every parameter load feeds four field-slot evaluations on the packed
+// FP32x2 FMA datapath.  Every wait is bounded; on expiry the kernel records a
+// flag in the device error word, drains its copies and returns.
+#include "pi2rh_kernels.h"
+
+namespace pi2rh {
+
+namespace {
+
+constexpr int NSTAGE = 4;
+constexpr int CW = RF_CONSUMER_WARPS;          // consumer warps
+constexpr int NTHREADS = (CW + 1) * 32;        // + one producer warp
+constexpr int NCONS = CW * 32;                 // consumer threads
+constexpr int SLOTS = RF_SLOTS;                // 2 per consumer lane
+constexpr int STAGE_BYTES = RF_PAIRS_PER_STAGE * REC_BYTES;
+constexpr int MAX_OBS = 256;
+
+// Shared-memory layout (bytes from the dynamic base).
+constexpr int OFF_STAGE = 0;
+constexpr int OFF_PART = OFF_STAGE + NSTAGE * STAGE_BYTES;          // [2][CW][5][SLOTS] f32
+constexpr int PART_BUF = CW * 5 * SLOTS;                            // floats per buffer
+constexpr int OFF_Z = OFF_PART + 2 * PART_BUF * 4;                  // [NZ][SLOTS]
+constexpr int OFF_X = OFF_Z + NZ * SLOTS * 4;                       // [NX][SLOTS]
+constexpr int OFF_Y = OFF_X + NX * SLOTS * 4;                       // [NY][SLOTS]
+constexpr int OFF_V = OFF_Y + NY * SLOTS * 4;                       // [NY][SLOTS]
+constexpr int OFF_YREF = OFF_V + NY * SLOTS * 4;                    // [NY][SLOTS]
+constexpr int OFF_Q = OFF_YREF + NY * SLOTS * 4;                    // [SLOTS]
+constexpr int OFF_OBS = OFF_Q + SLOTS * 4;                          // [MAX_OBS] float2
+constexpr int OFF_BAR = OFF_OBS + MAX_OBS * 8;                      // full[NSTAGE], empty[NSTAGE]
+constexpr int OFF_ABORT = OFF_BAR + 2 * NSTAGE * 8;
+constexpr int SMEM_BYTES = OFF_ABORT + 16;
+static_assert(OFF_PART % 16 == 0 && OFF_BAR % 8 == 0, "alignment");
+
+struct Soft {
+    float m, s0, s1, s2, s3;
+};
+
+__device__ __forceinline__ void soft_init(Soft &st)
+{
+    st.m = -INFINITY;
+    st.s0 = st.s1 = st.s2 = st.s3 = 0.0f;
+}
+
+// Adds two fields (packed exponent s, centered prediction e, variance v).
+__device__ __forceinline__ void soft_add2(Soft &st, float2 s, float2 e, float2 v)
+{
+    float mn = fmaxf(st.m, fmaxf(s.x, s.y));
+    float sc = ex2(st.m - mn);
+    float wa = ex2(s.x - mn), wb = ex2(s.y - mn);
+    float wea = wa * e.x, web = wb * e.y;
+    st.s0 = fmaf(st.s0, sc, wa + wb);
+    st.s1 = fmaf(st.s1, sc, wea + web);
+    st.s2 = fmaf(st.s2, sc, fmaf(wea, e.x, web * e.y));
+    st.s3 = fmaf(st.s3, sc, fmaf(wa, v.x, wb * v.y));
+    st.m = mn;
+}
+
+__device__ __forceinline__ float2 f2(float4 v, int hi)
+{
+    return hi ? make_float2(v.z, v.w) : make_float2(v.x, v.y);
+}
+
+// Row I of the symmetric quadratic form: s += d_I (sum_{j>=I} A_Ij d_j), for
+// both slots; rows are expanded at compile time so every index is constant.
+template <int I>
+__device__ __forceinline__ void quad_rows(const float4 *__restrict__ r4, const float2 (&dA)[NZ],
+                                          const float2 (&dB)[NZ], float2 &sA, float2 &sB)
+{
+    if constexpr (I < NZ) {
+        constexpr int base = REC_A + tri_index(I, I);   // first entry of row I
+        const float2 a0 = f2(r4[base >> 1], base & 1);
+        float2 tA = __fmul2_rn(a0, dA[I]);
+        float2 tB = __fmul2_rn(a0, dB[I]);
+#pragma unroll
+        for (int j = I + 1; j < NZ; ++j) {
+            const int e = base + (j - I);
+            const float2 aij = f2(r4[e >> 1], e & 1);
+            tA = __ffma2_rn(aij, dA[j], tA);
+            tB = __ffma2_rn(aij, dB[j], tB);
+        }
+        sA = __ffma2_rn(dA[I], tA, sA);
+        sB = __ffma2_rn(dB[I], tB, sB);
+        quad_rows<I + 1>(r4, dA, dB, sA, sB);
+    }
+}
+
+// Evaluates one field-pair record for two slots A and B.
+__device__ __forceinline__ void process_pair(const float4 *__restrict__ r4, const float2 (&zA)[NZ],
+                                             const float2 (&zB)[NZ], float2 yrA, float2 yrB,
+                                             Soft &stA, Soft &stB)
+{
+    float2 dA[NZ], dB[NZ];
+#pragma unroll
+    for (int a = 0; a < NZ; a += 2) {
+        float4 nc = r4[(REC_NEGC + a) >> 1];
+        dA[a] = __fadd2_rn(zA[a], f2(nc, 0));
+        dA[a + 1] = __fadd2_rn(zA[a + 1], f2(nc, 1));
+        dB[a] = __fadd2_rn(zB[a], f2(nc, 0));
+        dB[a + 1] = __fadd2_rn(zB[a + 1], f2(nc, 1));
+    }
+    float4 tail = r4[REC_B >> 1];        // {b.x, b.y, var.x, var.y}
+    float4 tail2 = r4[REC_BIAS >> 1];    // {bias.x, bias.y, 0, 0}
+    float2 sA = f2(tail2, 0), sB = sA;
+    quad_rows<0>(r4, dA, dB, sA, sB);
+    float2 b = f2(tail, 0);
+    float2 eA = __fadd2_rn(b, yrA), eB = __fadd2_rn(b, yrB);   // yr holds -y_ref
+#pragma unroll
+    for (int a = 0; a < NZ; a += 2) {
+        float4 be = r4[(REC_BETA + a) >> 1];
+        eA = __ffma2_rn(f2(be, 0), dA[a], eA);
+        eA = __ffma2_rn(f2(be, 1), dA[a + 1], eA);
+        eB = __ffma2_rn(f2(be, 0), dB[a], eB);
+        eB = __ffma2_rn(f2(be, 1), dB[a + 1], eB);
+    }
+    float2 v = f2(tail, 1);
+    soft_add2(stA, sA, eA, v);
+    soft_add2(stB, sB, eB, v);
+}
+
+// Merges the CW per-warp partials of one output for one slot.
+__device__ __forceinline__ void merge_partials(const float *pb, int slot, float yref, float &y,
+                                               float &var)
+{
+    float M = -INFINITY;
+#pragma unroll
+    for (int w = 0; w < CW; ++w) M = fmaxf(M, pb[(w * 5 + 0) * SLOTS + slot]);
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+#pragma unroll
+    for (int w = 0; w < CW; ++w) {
+        float sc = ex2(pb[(w * 5 + 0) * SLOTS + slot] - M);
+        s0 = fmaf(pb[(w * 5 + 1) * SLOTS + slot], sc, s0);
+        s1 = fmaf(pb[(w * 5 + 2) * SLOTS + slot], sc, s1);
+        s2 = fmaf(pb[(w * 5 + 3) * SLOTS + slot], sc, s2);
+        s3 = fmaf(pb[(w * 5 + 4) * SLOTS + slot], sc, s3);
+    }
+    float inv = 1.0f / s0;
+    float mean_e = s1 * inv;
+    y = yref + mean_e;
+    var = fmaxf(fmaf(-mean_e, mean_e, s2 * inv), 0.0f) + s3 * inv;
+}
+
+template <bool PREDICT>
+__global__ void __launch_bounds__(NTHREADS, 1) rollout_fp32_kernel(const __grid_constant__ RolloutArgs a)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    unsigned char *stage_base = smem + OFF_STAGE;
+    float *part = reinterpret_cast<float *>(smem + OFF_PART);
+    float *zbuf = reinterpret_cast<float *>(smem + OFF_Z);
+    float *xbuf = reinterpret_cast<float *>(smem + OFF_X);
+    float *ybuf = reinterpret_cast<float *>(smem + OFF_Y);
+    float *vbuf = reinterpret_cast<float *>(smem + OFF_V);
+    float *yrbuf = reinterpret_cast<float *>(smem + OFF_YREF);
+    float *qbuf = reinterpret_cast<float *>(smem + OFF_Q);
+    float2 *obs_s = reinterpret_cast<float2 *>(smem + OFF_OBS);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + OFF_BAR);
+    uint64_t *empty = full + NSTAGE;
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + OFF_ABORT);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int P = a.P, spo = a.stages_per_out;
+    const int G = NY * spo;                       // stages per step
+    const int nsteps = PREDICT ? 1 : a.T;
+    const long long total = (long long)G * nsteps;
+    const int M = PREDICT ? 1 : a.M;
+
+    if (tid == 0) {
+        for (int s = 0; s < NSTAGE; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], CW);
+        }
+        *abort_flag = 0;
+        fence_mbar_init();
+    }
+    for (int i = tid; i < a.cost.n_obs; i += NTHREADS) obs_s[i] = a.cost.obs[i];
+    __syncthreads();
+
+    // ------------------------------------------------------------------ producer
+    if (warp == CW) {
+        if (lane != 0) return;
+        long long issued = 0;
+        for (long long g = 0; g < total; ++g) {
+            const int slot = (int)(g % NSTAGE);
+            if (g >= NSTAGE) {
+                const uint32_t par = (uint32_t)(((g / NSTAGE) - 1) & 1);
+                if (!mbar_wait_bounded(&empty[slot], par, abort_flag)) {
+                    if (!*abort_flag) atomicOr(a.err, DEVERR_TIMEOUT_EMPTY);
+                    *abort_flag = 1;
+                    break;
+                }
+            }
+            const int gs = (int)(g % G);
+            const int o = gs / spo, s = gs % spo;
+            const int p0 = s * RF_PAIRS_PER_STAGE;
+            const int np = min(RF_PAIRS_PER_STAGE, P - p0);
+            const uint32_t bytes = (uint32_t)np * REC_BYTES;
+            const float2 *src = a.rec + ((size_t)o * P + p0) * REC_LEN;
+            mbar_arrive_expect_tx(&full[slot], bytes);
+            bulk_g2s(stage_base + (size_t)slot * STAGE_BYTES, src, bytes, &full[slot]);
+            issued = g + 1;
+        }
+        // Keep the CTA alive until every copy issued has landed.
+        for (long long g = (issued > NSTAGE ? issued - NSTAGE : 0); g < issued; ++g) {
+            const int slot = (int)(g % NSTAGE);
+            if (!mbar_wait_drain(&full[slot], (uint32_t)((g / NSTAGE) & 1)))
+                atomicOr(a.err, DEVERR_TIMEOUT_DRAIN);
+        }
+        return;
+    }
+
+    // ------------------------------------------------------------------ consumers
+    const int slotA = lane, slotB = lane + 32;
+    const long long slot_base = (long long)blockIdx.x * SLOTS;
+
+    // Step-thread state: thread tid < SLOTS owns slot tid.
+    const bool stepper = tid < SLOTS;
+    const long long gslot = slot_base + tid;
+    const int k = (int)(gslot / M), m = (int)(gslot % M);
+    const bool writer = stepper && !PREDICT && k < a.K && m == 0;
+
+    if (stepper) {
+        if (PREDICT) {
+            const bool ok = gslot < a.n_pred;
+#pragma unroll
+            for (int c = 0; c < NZ; ++c)
+                zbuf[c * SLOTS + tid] = ok ? a.z_in[(size_t)gslot * NZ + c] : 0.0f;
+#pragma unroll
+            for (int o = 0; o < NY; ++o) yrbuf[o * SLOTS + tid] = 0.0f;
+        } else {
+            float4 n = box_muller4(noise_block(a.seed, (uint32_t)k, 0u, 0u, 0u));
+            float eps[4] = {a.sqrt_sigma_u[0] * n.x, a.sqrt_sigma_u[1] * n.y,
+                            a.sqrt_sigma_u[2] * n.z, a.sqrt_sigma_u[3] * n.w};
+#pragma unroll
+            for (int c = 0; c < NX; ++c) {
+                float xc = a.x0[c];
+                xbuf[c * SLOTS + tid] = xc;
+                zbuf[c * SLOTS + tid] = xc;
+            }
+#pragma unroll
+            for (int c = 0; c < NU; ++c) zbuf[(NX + c) * SLOTS + tid] = a.u_nom[c] + eps[c];
+#pragma unroll
+            for (int o = 0; o < NY; ++o) yrbuf[o * SLOTS + tid] = 0.0f;
+            if (writer) a.eps_tk[k] = make_float4(eps[0], eps[1], eps[2], eps[3]);
+        }
+    }
+    named_bar_sync(1, NCONS);
+
+    long long g = 0;
+    bool aborted = false;
+    for (int t = 0; t < nsteps; ++t) {
+        float2 zA[NZ], zB[NZ];
+#pragma unroll
+        for (int c = 0; c < NZ; ++c) {
+            float va = zbuf[c * SLOTS + slotA], vb = zbuf[c * SLOTS + slotB];
+            zA[c] = make_float2(va, va);
+            zB[c] = make_float2(vb, vb);
+        }
+        for (int o = 0; o < NY; ++o) {
+            const float ya = -yrbuf[o * SLOTS + slotA], yb = -yrbuf[o * SLOTS + slotB];
+            const float2 yrA = make_float2(ya, ya), yrB = make_float2(yb, yb);
+            Soft stA, stB;
+            soft_init(stA);
+            soft_init(stB);
+            for (int s = 0; s < spo; ++s, ++g) {
+                const int slot = (int)(g % NSTAGE);
+                if (!aborted &&
+                    !mbar_wait_bounded(&full[slot], (uint32_t)((g / NSTAGE) & 1), abort_flag)) {
+                    if (lane == 0) {
+                        if (!*abort_flag) atomicOr(a.err, DEVERR_TIMEOUT_FULL);
+                        *abort_flag = 1;
+                    }
+                    aborted = true;
+                }
+                const int pair = s * RF_PAIRS_PER_STAGE + warp;
+                if (!aborted && pair < P) {
+                    const float4 *r4 = reinterpret_cast<const float4 *>(
+                        stage_base + (size_t)slot * STAGE_BYTES + (size_t)warp * REC_BYTES);
+                    process_pair(r4, zA, zB, yrA, yrB, stA, stB);
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[slot]);
+            }
+            float *pb = part + (o & 1) * PART_BUF;
+            pb[(warp * 5 + 0) * SLOTS + slotA] = stA.m;
+            pb[(warp * 5 + 1) * SLOTS + slotA] = stA.s0;
+            pb[(warp * 5 + 2) * SLOTS + slotA] = stA.s1;
+            pb[(warp * 5 + 3) * SLOTS + slotA] = stA.s2;
+            pb[(warp * 5 + 4) * SLOTS + slotA] = stA.s3;
+            pb[(warp * 5 + 0) * SLOTS + slotB] = stB.m;
+            pb[(warp * 5 + 1) * SLOTS + slotB] = stB.s0;
+            pb[(warp * 5 + 2) * SLOTS + slotB] = stB.s1;
+            pb[(warp * 5 + 3) * SLOTS + slotB] = stB.s2;
+            pb[(warp * 5 + 4) * SLOTS + slotB] = stB.s3;
+            named_bar_sync(1, NCONS);
+            if (stepper) {
+                float y, var;
+                merge_partials(pb, tid, yrbuf[o * SLOTS + tid], y, var);
+                ybuf[o * SLOTS + tid] = y;
+                vbuf[o * SLOTS + tid] = var;
+            }
+        }
+
+        if (stepper) {
+            float y[NY], var[NY];
+#pragma unroll
+            for (int o = 0; o < NY; ++o) {
+                y[o] = ybuf[o * SLOTS + tid];
+                var[o] = vbuf[o * SLOTS + tid];
+            }
+            if (PREDICT) {
+                if (gslot < a.n_pred) {
+#pragma unroll
+                    for (int o = 0; o < NY; ++o) {
+                        a.y_out[(size_t)gslot * NY + o] = y[o];
+                        a.var_out[(size_t)gslot * NY + o] = var[o];
+                    }
+                }
+            } else {
+                float x[NX];
+#pragma unroll
+                for (int c = 0; c < NX; ++c) x[c] = xbuf[c * SLOTS + tid];
+                // running cost at (x_t, z_t), averaged over the sub-rollouts of k
+                qbuf[tid] = running_cost(a.cost, obs_s, x, var);
+                // sampled Euler step (Sec. 3.2)
+                float n[NY];
+                if (a.model_noise) {
+#pragma unroll
+                    for (int b = 0; b < 3; ++b) {
+                        float4 nb = box_muller4(noise_block(a.seed, (uint32_t)k, (uint32_t)t,
+                                                            (uint32_t)(b + 1), (uint32_t)m));
+                        n[4 * b] = nb.x;
+                        n[4 * b + 1] = nb.y;
+                        n[4 * b + 2] = nb.z;
+                        n[4 * b + 3] = nb.w;
+                    }
+                } else {
+#pragma unroll
+                    for (int o = 0; o < NY; ++o) n[o] = 0.0f;
+                }
+#pragma unroll
+                for (int c = 0; c < NX; ++c) {
+                    float xdot = fmaf(sqrtf(var[c]), n[c], y[c]);
+                    x[c] = fmaf(a.dt, xdot, x[c]);
+                    xbuf[c * SLOTS + tid] = x[c];
+                    zbuf[c * SLOTS + tid] = x[c];
+                    yrbuf[c * SLOTS + tid] = y[c];
+                }
+                named_bar_sync(2, SLOTS);
+                if (writer) {
+                    float qs = 0.0f;
+                    for (int i = 0; i < M; ++i) qs += qbuf[tid + i];
+                    a.cost_tk[(size_t)t * a.K + k] = qs / (float)M;
+                }
+                if (t + 1 < a.T) {
+                    float4 nn = box_muller4(noise_block(a.seed, (uint32_t)k, (uint32_t)(t + 1), 0u, 0u));
+                    float eps[4] = {a.sqrt_sigma_u[0] * nn.x, a.sqrt_sigma_u[1] * nn.y,
+                                    a.sqrt_sigma_u[2] * nn.z, a.sqrt_sigma_u[3] * nn.w};
+#pragma unroll
+                    for (int c = 0; c < NU; ++c)
+                        zbuf[(NX + c) * SLOTS + tid] = a.u_nom[(size_t)(t + 1) * NU + c] + eps[c];
+                    if (writer)
+                        a.eps_tk[(size_t)(t + 1) * a.K + k] = make_float4(eps[0], eps[1], eps[2], eps[3]);
+                } else {
+                    named_bar_sync(2, SLOTS);           // qbuf reads done before reuse
+                    qbuf[tid] = terminal_cost(a.cost, x);
+                    named_bar_sync(2, SLOTS);
+                    if (writer) {
+                        float ps = 0.0f;
+                        for (int i = 0; i < M; ++i) ps += qbuf[tid + i];
+                        a.phi[k] = ps / (float)M;
+                    }
+                }
+            }
+        }
+        const bool any_abort = bar_sync_or(3, NCONS, aborted || *abort_flag != 0);
+        if (any_abort) break;
+    }
+}
+
+bool g_attr_set[2] = {false, false};
+
+template <bool PREDICT>
+cudaError_t launch_impl(const RolloutArgs &a, cudaStream_t s, long long slots)
+{
+    if (a.cost.n_obs > MAX_OBS || a.P <= 0 || a.stages_per_out <= 0) return cudaErrorInvalidValue;
+    if (!g_attr_set[PREDICT]) {
+        cudaError_t e = cudaFuncSetAttribute(rollout_fp32_kernel<PREDICT>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+        if (e != cudaSuccess) return e;
+        g_attr_set[PREDICT] = true;
+    }
+    const long long blocks = (slots + SLOTS - 1) / SLOTS;
+    if (blocks <= 0 || blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+    rollout_fp32_kernel<PREDICT><<<(unsigned)blocks, NTHREADS, SMEM_BYTES, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_rollout_fp32(const RolloutArgs &a, cudaStream_t s)
+{
+    if (a.M < 1 || a.M > SLOTS || (a.M & (a.M - 1)) != 0) return cudaErrorInvalidValue;
+    return launch_impl<false>(a, s, (long long)a.K * a.M);
+}
+
+cudaError_t launch_predict_fp32(const RolloutArgs &a, cudaStream_t s)
+{
+    return launch_impl<true>(a, s, (long long)a.n_pred);
+}
+
+}  // namespace pi2rh
