@@ -1,0 +1,335 @@
+#!/usr/bin/env python3
+"""Benchmark of the PI^2-RH / LWPR update on one B300.
+
+Workload (default ``realtime``): K=8192 rollouts, T=100 steps, L=512 receptive
+fields per output (12 outputs over a 16-dim input), 16 cylinder obstacles; a
+receding-horizon loop of ``--steps`` iterations (20 by default), each one
+``pi_update`` (seed = seed + iteration) followed by ``pi_rh_advance`` (plant
+step with the first control, warm-start shift of the plan).  Synthetic inputs
+from the seeded generator; everything is resident in HBM before timing.
+
+Prints ONE JSON line (rank 0).  ``value`` = rollout-steps/s (K*T*M per update)
+over the timed iterations, device-timed with CUDA events on the launching
+stream; ``e2e`` is the same metric through ``pi_update_host`` (host buffers,
+copies inside the timed region); ``roofline`` is the rollout kernel's FP32
+rate from per-launch event times; ``cpu_baseline`` is the FP64 oracle timed on
+a bounded sample of the same workload.
+
+``--impl reference`` times the oracle itself (there is no reference
+implementation of the paper's method other than the oracle written from it).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "LWPR rollout-steps/s (ms per PI^2 update alongside)"
+UNIT = "rollout-steps/s"
+FLOPS_PER_FIELD = 360          # 16 sub + 136 FMA + 16 FMA + 16 FMA + 4 FMA (x2 flops per FMA)
+FP32_LANES_PER_SM = 128
+L2_BYTES = 126 * 2**20
+CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def profile_traffic(name: str):
+    """Per-launch DRAM bytes recorded in a committed ncu summary, or None."""
+    path = os.path.join(ROOT, "profiles", name)
+    try:
+        with open(path) as f:
+            m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", f.read())
+        return float(m.group(1)) if m else None
+    except OSError:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.device}", f"--query-gpu={CLOCK_FIELDS}", "--format=csv,noheader",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            with open(self.path) as f:
+                for line in f:
+                    parts = [p.strip() for p in line.split(",")]
+                    if len(parts) < 9:
+                        continue
+                    try:
+                        rows.append((float(parts[1].split()[0]), float(parts[2].split()[0]),
+                                     float(parts[3].split()[0]) if parts[3][0].isdigit() else 0.0,
+                                     parts[5], parts[6], parts[7], parts[8]))
+                    except (ValueError, IndexError):
+                        continue
+        finally:
+            if self.path and os.path.exists(self.path):
+                os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        power = [r[2] for r in rows]
+        pmax = max(power)
+        loaded = [r for r in rows if r[2] >= 0.5 * pmax] or rows
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({n for r in loaded for n, v in zip(names, r[3:]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in loaded), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(loaded), "power_w_max": pmax}
+
+
+def workload(name: str, seed: int):
+    from paper_1503_00330_b300 import workloads as W
+    if name == "realtime":
+        return W.realtime(seed), "realtime: K=8192 rollouts, T=100 steps, L=512 fields x 12 outputs, " \
+                                 "16 cylinder obstacles, receding-horizon loop with warm-start shift"
+    if name == "realtime_short":
+        p = W.realtime(seed)
+        p.T = 10
+        p.u_nom = p.u_nom[:10].copy()
+        return p, "realtime_short (profiling case): K=8192, T=10, L=512 x 12 outputs, 16 obstacles"
+    if name == "small":
+        return W.small(seed), "small: K=256, T=50, L=64 x 12 outputs, 4 obstacles"
+    if name == "precision":
+        return W.precision(seed), "precision: K=65536, T=100, L=2048 x 12 outputs, cond(D) logU[1,1e3]"
+    raise SystemExit(f"unknown workload {name}")
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws == 1:
+        return 0, 1, 0, None
+    import torch.distributed as dist
+    rank, local = int(os.environ["RANK"]), int(os.environ.get("LOCAL_RANK", "0"))
+    backend = "nccl" if os.environ.get("BENCH_BACKEND", "nccl") == "nccl" else "gloo"
+    dist.init_process_group(backend)
+    return rank, ws, local, dist
+
+
+def reduce_max(dist, v: float, device):
+    if dist is None:
+        return v
+    import torch
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_baseline(p, k_sample: int):
+    """FP64 oracle on the first k_sample rollouts of one update of the workload."""
+    from oracle import oracle as O
+    O.build()
+    t0 = time.perf_counter()
+    O.pi_update(p.model, p.cost, p.x0, p.u_nom, k_sample, p.T, p.lam, p.sigma_u, p.seed, M=p.M,
+                model_noise=p.model_noise)
+    el = time.perf_counter() - t0
+    return {"value": k_sample * p.T * p.M / el, "unit": UNIT, "cores": O.max_threads(), "kind": "oracle",
+            "sample": f"one update of {k_sample} of the {p.K} rollouts (T={p.T}, L={p.model.L}, M={p.M}), "
+                      f"{el:.2f} s"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    p, desc = workload(args.workload, 0)
+    O.build()
+    k_s = args.ref_sample
+    u_nom = p.u_nom.astype(np.float64)
+    times = []
+    for it in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        u, _ = O.pi_update(p.model, p.cost, p.x0, u_nom, k_s, p.T, p.lam, p.sigma_u, p.seed + it, M=p.M,
+                           model_noise=p.model_noise)
+        el = time.perf_counter() - t0
+        u_nom = np.concatenate([u[1:], u[-1:]], 0)
+        if it >= args.warmup:
+            times.append(el)
+    total = sum(times)
+    value = k_s * p.T * p.M * args.steps / total
+    cores = O.max_threads()
+    sample = f"each step: one update of {k_s} of the {p.K} rollouts (T={p.T}, L={p.model.L})"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": desc, "K": p.K, "T": p.T, "L": p.model.L, "M": p.M,
+                                            "sample_K": k_s},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    from paper_1503_00330_b300 import build
+    from paper_1503_00330_b300.api import Controller
+
+    rank, ws, local, dist = dist_setup()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    build.build()
+    p, desc = workload(args.workload, rank)          # replicas: rank-dependent seed
+    K, T, M, L = p.K, p.T, p.M, p.model.L
+
+    ctl = Controller(p.model, p.cost, M=M, model_noise=p.model_noise, device=local)
+    ctl.set_timing(True)
+    ctl.reserve(K, T)
+    x0 = torch.as_tensor(p.x0, device=dev).clone()
+    ua = torch.as_tensor(p.u_nom, device=dev).clone()
+    ub = torch.empty_like(ua)
+    costs = torch.empty(K, dtype=torch.float32, device=dev)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def rh_step(it):
+        ctl.update(x0, ua, K, T, p.lam, p.sigma_u, p.seed + it, u_out=ub, costs_out=costs)
+        ctl.rh_advance(x0, ub, ua)                   # next warm start back into ua
+
+    for it in range(args.warmup):
+        rh_step(it)
+    ctl.sync()
+
+    # ---- device-timed region -------------------------------------------------
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    rollout_ms, step_ms = [], []
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = ctl.launch_count()
+    with ClockSampler(local) as clocks:
+        for i in range(args.steps):
+            flush.zero_()                               # L2 flush, outside the event window
+            ev[i][0].record(stream)
+            rh_step(args.warmup + i)
+            ev[i][1].record(stream)
+            rollout_ms.append(ctl.stage_times()[0])     # waits for this update
+        torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    launches = ctl.launch_count() - launches0
+    ctl.sync()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_s = reduce_max(dist, sum(step_ms) / 1e3, dev)
+    value = ws * K * T * M * args.steps / total_s
+
+    # ---- end to end through the host-buffer entry point ----------------------
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float32)).pin_memory().numpy()
+    hx0, hu = pin(p.x0), pin(p.u_nom)
+    hout, hcost = pin(np.empty((T, 4), np.float32)), pin(np.empty(K, np.float32))
+    e2e_times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        ctl.update_host(hx0, hu, K, T, p.lam, p.sigma_u, p.seed + i, u_out=hout, costs_out=hcost)
+        el = time.perf_counter() - t0
+        hu[:-1] = hout[1:]
+        hu[-1] = hout[-1]
+        if i >= args.warmup:
+            e2e_times.append(el)
+    e2e_total = reduce_max(dist, sum(e2e_times), dev)
+    e2e_value = ws * K * T * M * args.steps / e2e_total
+
+    if rank != 0:
+        dist.destroy_process_group()
+        return
+
+    peaks = measured_peaks()
+    props = torch.cuda.get_device_properties(dev)
+    sm_max_mhz = float(peaks.get("sm_max_mhz", 2032.0))
+    peak_tflops = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12
+    flops_per_launch = float(K) * T * M * 12 * L * FLOPS_PER_FIELD
+    avg_rollout_s = statistics.mean(rollout_ms) / 1e3
+    achieved = flops_per_launch / avg_rollout_s / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                "frac": achieved / peak_tflops,
+                "traffic": profile_traffic(f"rollout_fp32_{args.workload}.md"),
+                "kernel": "rollout_fp32_kernel",
+                "peak_basis": f"FP32 FMA pipe: {props.multi_processor_count} SMs x {FP32_LANES_PER_SM} lanes x 2 flop "
+                              f"x {sm_max_mhz:.0f} MHz (max SM clock)",
+                "rollout_ms_per_launch": statistics.mean(rollout_ms),
+                "rollout_share_of_step": sum(rollout_ms) / sum(step_ms)}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded generator; quadrotor-shaped LWPR model and obstacle field)",
+            "config": {"workload": desc, "K": K, "T": T, "L": L, "M": M, "precision": "fp32",
+                       "parallelism": "replicas" if ws > 1 else "single",
+                       "l2": "flushed between timed steps (256 MiB write outside the event window); "
+                             "per-update working set ~21 MB"},
+            "ms_per_update": 1e3 * total_s / args.steps,
+            "gpu_launches": launches,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": (12 + T * 4) * 4,
+                    "d2h_bytes_per_step": (T * 4 + K) * 4},
+            "roofline": roofline,
+            "clocks": clocks.summary()}
+    if ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(p, args.cpu_sample)
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["realtime", "realtime_short", "small", "precision"], default="realtime")
+    ap.add_argument("--cpu-sample", type=int, default=256, help="rollouts in the CPU-baseline sample")
+    ap.add_argument("--ref-sample", type=int, default=64, help="rollouts per reference-arm step")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

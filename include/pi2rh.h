@@ -167,6 +167,22 @@ int pi_update_host(pi_ctx *ctx, const float *x0, const float *u_nominal, int K, 
                    float lambda, const float *sigma_u, uint64_t seed, float *u_out,
                    float *costs_out);
 
+/* Receding-horizon advance (Sec. 3.1: execute one step of the plan, then
+ * warm-start the next update with the unexecuted remainder).  On the context's
+ * stream, with device buffers:
+ *   x0        [12] in/out   x0 <- x0 + dt * y(z), y the LWPR mean (Eq. 1) at
+ *                           z = [x0, u_out[0]] (the synthetic plant)
+ *   u_out     [T][4] in     plan returned by pi_update
+ *   u_nom_next[T][4] out    u_out shifted left by one step, last step repeated;
+ *                           must not overlap u_out */
+int pi_rh_advance(pi_ctx *ctx, float *x0, const float *u_out, int T, float *u_nom_next);
+
+/* Per-kernel timing of pi_update with CUDA events on the context's stream
+ * (off by default).  pi_stage_times waits for the last timed update and writes
+ * ms[0] = rollout kernel, ms[1] = cost-to-go/LSE kernel, ms[2] = merge kernel. */
+int pi_set_timing(pi_ctx *ctx, int enable);
+int pi_stage_times(pi_ctx *ctx, float *ms);
+
 /* Synchronizes the context's stream and reports device-side errors raised by
  * earlier work: PI_ERR_TIMEOUT if a bounded wait in a kernel expired (the
  * kernel returned early and its outputs are invalid), PI_ERR_INTERNAL for a

@@ -87,6 +87,9 @@ def _load():
         lib.orc_rollouts.argtypes = [ctypes.POINTER(_Lwpr), ctypes.POINTER(_Cost), _dp, _dp,
                                      ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp,
                                      ctypes.c_uint64, ctypes.c_int, _dp, _dp, _dp, _dp]
+        lib.orc_rollouts_from.argtypes = [ctypes.POINTER(_Lwpr), ctypes.POINTER(_Cost), _dp, _dp,
+                                          ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp,
+                                          ctypes.c_uint64, ctypes.c_int, _dp, _dp, _dp, _dp]
         lib.orc_cost_to_go.argtypes = [_dp, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_double, _dp]
         lib.orc_weighted_update.argtypes = [_dp, _dp, _dp, ctypes.c_int, ctypes.c_int,
                                             ctypes.c_double, _dp]
@@ -214,8 +217,9 @@ def terminal_cost(cost_params, x) -> float:
 # rollouts, cost-to-go, weighted update
 # ---------------------------------------------------------------------------
 def rollouts(model, cost_params, x0, u_nom, K, T, sigma_u, seed, M=1, model_noise=True,
-             want_traj=False):
-    """Returns dict(eps [K,T,4], cost [K,T], phi [K], traj [K,M,T+1,12] or None)."""
+             want_traj=False, k0=0):
+    """Rollouts k0 .. k0+K-1 -> dict(eps [K,T,4], cost [K,T], phi [K],
+    traj [K,M,T+1,12] or None)."""
     lib = _load()
     hl, hc = _lwpr_struct(model), _cost_struct(cost_params)
     x0a, un, su = _f64(x0), _f64(u_nom).reshape(T, NU), _f64(sigma_u)
@@ -223,9 +227,9 @@ def rollouts(model, cost_params, x0, u_nom, K, T, sigma_u, seed, M=1, model_nois
     cost = np.zeros((K, T))
     phi = np.zeros(K)
     traj = np.zeros((K, M, T + 1, NX)) if want_traj else None
-    lib.orc_rollouts(ctypes.byref(hl.lwpr), ctypes.byref(hc.cost), _ptr(x0a), _ptr(un), K, T, M,
-                     _ptr(su), int(seed), int(bool(model_noise)), _ptr(eps), _ptr(cost), _ptr(phi),
-                     _ptr(traj) if want_traj else None)
+    lib.orc_rollouts_from(ctypes.byref(hl.lwpr), ctypes.byref(hc.cost), _ptr(x0a), _ptr(un), int(k0), K, T,
+                          M, _ptr(su), int(seed), int(bool(model_noise)), _ptr(eps), _ptr(cost), _ptr(phi),
+                          _ptr(traj) if want_traj else None)
     return {"eps": eps, "cost": cost, "phi": phi, "traj": traj}
 
 

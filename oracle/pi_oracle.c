@@ -267,12 +267,20 @@ double orc_terminal_cost(const orc_cost *C, const double *x)
 /*   xtraj[K][M][T+1][NX] (optional, may be NULL) visited states            */
 /* model_noise: 1 = sampled draw, 0 = mean prediction only.                 */
 /* ------------------------------------------------------------------------ */
-void orc_rollouts(const orc_lwpr *P, const orc_cost *C, const double *x0, const double *u_nom,
-                  int K, int T, int M, const double *sigma_u, uint64_t seed, int model_noise,
-                  double *eps, double *cost, double *phi, double *xtraj)
+/* Rollouts k0 .. k0+K-1 of an update (row r of the outputs is rollout k0 + r);
+ * rollout k only depends on its own noise counters, so any subset can be run. */
+void orc_rollouts_from(const orc_lwpr *P, const orc_cost *C, const double *x0, const double *u_nom,
+                       int k0, int K, int T, int M, const double *sigma_u, uint64_t seed,
+                       int model_noise, double *eps_out, double *cost_out, double *phi_out,
+                       double *xtraj_out)
 {
     #pragma omp parallel for schedule(dynamic, 1)
-    for (int k = 0; k < K; ++k) {
+    for (int r = 0; r < K; ++r) {
+        const int k = k0 + r;
+        double *eps = eps_out - (size_t)k0 * T * ORC_NU;
+        double *cost = cost_out - (size_t)k0 * T;
+        double *phi = phi_out - k0;
+        double *xtraj = xtraj_out ? xtraj_out - (size_t)k0 * M * (T + 1) * ORC_NX : NULL;
         for (int t = 0; t < T; ++t) cost[(size_t)k * T + t] = 0.0;
         phi[k] = 0.0;
         for (int m = 0; m < M; ++m) {
@@ -302,6 +310,13 @@ void orc_rollouts(const orc_lwpr *P, const orc_cost *C, const double *x0, const 
             phi[k] += orc_terminal_cost(C, x) / (double)M;
         }
     }
+}
+
+void orc_rollouts(const orc_lwpr *P, const orc_cost *C, const double *x0, const double *u_nom,
+                  int K, int T, int M, const double *sigma_u, uint64_t seed, int model_noise,
+                  double *eps, double *cost, double *phi, double *xtraj)
+{
+    orc_rollouts_from(P, C, x0, u_nom, 0, K, T, M, sigma_u, seed, model_noise, eps, cost, phi, xtraj);
 }
 
 /* Cost-to-go S(tau_i) = phi + sum_{j=i}^{T-1} q_j dt, accumulated from the end. */

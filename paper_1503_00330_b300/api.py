@@ -113,6 +113,21 @@ class Controller:
                                        ctypes.c_uint64(seed), u_out.ctypes.data, costs_out.ctypes.data))
         return u_out, costs_out
 
+    def rh_advance(self, x0: torch.Tensor, u_out: torch.Tensor, u_nom_next: torch.Tensor):
+        """In place: x0 <- plant step with u_out[0]; u_nom_next <- shifted plan."""
+        self._use_current_stream()
+        T = u_out.shape[0]
+        check(self._lib.pi_rh_advance(self._h, _ptr(x0), _ptr(u_out), T, _ptr(u_nom_next)))
+
+    def set_timing(self, enable: bool = True):
+        check(self._lib.pi_set_timing(self._h, 1 if enable else 0))
+
+    def stage_times(self):
+        """(rollout_ms, scan_ms, merge_ms) of the last timed update."""
+        ms = (ctypes.c_float * 3)()
+        check(self._lib.pi_stage_times(self._h, ms))
+        return tuple(float(v) for v in ms)
+
     def sync(self):
         check(self._lib.pi_sync(self._h))
 

@@ -34,6 +34,11 @@ struct pi_ctx {
     // staging for the host-buffer path
     float *d_x0 = nullptr, *d_unom = nullptr, *d_uout = nullptr, *d_costs = nullptr;
     size_t cap_x0 = 0, cap_unom = 0, cap_uout = 0, cap_costs = 0;
+    // receding-horizon advance scratch: z [16], y [12], var [12]
+    float *d_rh = nullptr;
+    // per-kernel timing
+    bool timing = false;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     uint64_t launches = 0;
 };
 
@@ -189,6 +194,7 @@ int launch_reduce(pi_ctx *c, const float *cost, const float *phi, const float4 *
                             c->stream),
             "scan kernel launch");
     c->launches++;
+    if (c->timing) PI_CUDA(cudaEventRecord(c->ev[2], c->stream), "event record");
     PI_CUDA(launch_lse_merge(c->d_part, scan_blocks(K), T, inv_lam_log2e, u_nom, u_out, c->stream),
             "merge kernel launch");
     c->launches++;
@@ -198,10 +204,12 @@ int launch_reduce(pi_ctx *c, const float *cost, const float *phi, const float4 *
 void free_ctx_memory(pi_ctx *c)
 {
     void *ptrs[] = {c->d_rec, c->d_obs, c->d_err, c->d_cost, c->d_eps, c->d_phi, c->d_part,
-                    c->d_x0, c->d_unom, c->d_uout, c->d_costs};
+                    c->d_x0, c->d_unom, c->d_uout, c->d_costs, c->d_rh};
     for (void *p : ptrs)
         if (p) cudaFreeAsync(p, c->stream);
     cudaStreamSynchronize(c->stream);
+    for (cudaEvent_t &e : c->ev)
+        if (e) cudaEventDestroy(e);
 }
 
 }  // namespace
@@ -368,8 +376,58 @@ int pi_update(pi_ctx *c, const float *x0, const float *u_nom, int K, int T, floa
     DeviceGuard dg(c->device);
     PI_CUDA(dg.err, "cudaSetDevice");
     PI_TRY(ensure_scratch(c, K, T));
+    if (c->timing) PI_CUDA(cudaEventRecord(c->ev[0], c->stream), "event record");
     PI_TRY(launch_rollouts(c, x0, u_nom, K, T, sigma_u, seed, c->d_cost, c->d_eps, c->d_phi));
-    return launch_reduce(c, c->d_cost, c->d_phi, c->d_eps, u_nom, K, T, lambda, u_out, costs_out);
+    if (c->timing) PI_CUDA(cudaEventRecord(c->ev[1], c->stream), "event record");
+    PI_TRY(launch_reduce(c, c->d_cost, c->d_phi, c->d_eps, u_nom, K, T, lambda, u_out, costs_out));
+    if (c->timing) PI_CUDA(cudaEventRecord(c->ev[3], c->stream), "event record");
+    return PI_OK;
+}
+
+int pi_rh_advance(pi_ctx *c, float *x0, const float *u_out, int T, float *u_next)
+{
+    if (!c) return fail(PI_ERR_INVALID_ARG, "ctx is NULL");
+    if (!x0 || !u_out || !u_next || T < 1) return fail(PI_ERR_INVALID_ARG, "bad argument");
+    if (u_next < u_out + (size_t)T * NU && u_out < u_next + (size_t)T * NU)
+        return fail(PI_ERR_INVALID_ARG, "u_nom_next must not overlap u_out");
+    DeviceGuard dg(c->device);
+    PI_CUDA(dg.err, "cudaSetDevice");
+    if (!c->d_rh) PI_CUDA(cudaMallocAsync((void **)&c->d_rh, 40 * sizeof(float), c->stream), "rh scratch");
+    PI_CUDA(launch_rh_build_z(x0, u_out, c->d_rh, c->stream), "rh kernel launch");
+    RolloutArgs a = base_args(c);
+    a.M = 1;
+    a.z_in = c->d_rh;
+    a.y_out = c->d_rh + 16;
+    a.var_out = c->d_rh + 28;
+    a.n_pred = 1;
+    PI_CUDA(launch_predict_fp32(a, c->stream), "predict kernel launch");
+    PI_CUDA(launch_rh_apply(x0, c->d_rh + 16, c->dt, u_out, T, u_next, c->stream), "rh kernel launch");
+    c->launches += 3;
+    return PI_OK;
+}
+
+int pi_set_timing(pi_ctx *c, int enable)
+{
+    if (!c) return fail(PI_ERR_INVALID_ARG, "ctx is NULL");
+    DeviceGuard dg(c->device);
+    PI_CUDA(dg.err, "cudaSetDevice");
+    if (enable && !c->ev[0])
+        for (cudaEvent_t &e : c->ev) PI_CUDA(cudaEventCreate(&e), "cudaEventCreate");
+    c->timing = enable != 0;
+    return PI_OK;
+}
+
+int pi_stage_times(pi_ctx *c, float *ms)
+{
+    if (!c || !ms) return fail(PI_ERR_INVALID_ARG, "bad argument");
+    if (!c->ev[0]) return fail(PI_ERR_INVALID_ARG, "timing is not enabled");
+    DeviceGuard dg(c->device);
+    PI_CUDA(dg.err, "cudaSetDevice");
+    PI_CUDA(cudaEventSynchronize(c->ev[3]), "cudaEventSynchronize");
+    PI_CUDA(cudaEventElapsedTime(&ms[0], c->ev[0], c->ev[1]), "cudaEventElapsedTime");
+    PI_CUDA(cudaEventElapsedTime(&ms[1], c->ev[1], c->ev[2]), "cudaEventElapsedTime");
+    PI_CUDA(cudaEventElapsedTime(&ms[2], c->ev[2], c->ev[3]), "cudaEventElapsedTime");
+    return PI_OK;
 }
 
 int pi_sync(pi_ctx *c)

@@ -47,6 +47,11 @@ cudaError_t launch_scan_lse(const float *cost_tk, const float *phi, const float4
 cudaError_t launch_lse_merge(const double *part, int nblk, int T, double inv_lam_log2e,
                              const float *u_nom, float *u_out, cudaStream_t s);
 
+// Receding-horizon advance.
+cudaError_t launch_rh_build_z(const float *x0, const float *u_out, float *z, cudaStream_t s);
+cudaError_t launch_rh_apply(float *x0, const float *y, float dt, const float *u_out, int T, float *u_next,
+                            cudaStream_t s);
+
 // Staged noise kernels.
 cudaError_t launch_noise_raw(uint64_t seed, int K, int T, int m, uint32_t *raw, cudaStream_t s);
 cudaError_t launch_noise_normals(uint64_t seed, int K, int T, int m, float *ctrl, float *model,
