@@ -180,7 +180,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) rollout_fp32_kernel(const __grid_
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int P = a.P, spo = a.stages_per_out;
     const int G = NY * spo;                       // stages per step
-    const int nsteps = PREDICT ? 1 : a.T;
+    // Prediction mode runs the field loop twice: the second pass centers the
+    // local predictions on the first pass's mean, so the spread term of the
+    // variance does not cancel.
+    const int nsteps = PREDICT ? 2 : a.T;
     const long long total = (long long)G * nsteps;
     const int M = PREDICT ? 1 : a.M;
 
@@ -328,7 +331,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) rollout_fp32_kernel(const __grid_
                 var[o] = vbuf[o * SLOTS + tid];
             }
             if (PREDICT) {
-                if (gslot < a.n_pred) {
+                if (t == 0) {
+#pragma unroll
+                    for (int o = 0; o < NY; ++o) yrbuf[o * SLOTS + tid] = y[o];
+                } else if (gslot < a.n_pred) {
 #pragma unroll
                     for (int o = 0; o < NY; ++o) {
                         a.y_out[(size_t)gslot * NY + o] = y[o];

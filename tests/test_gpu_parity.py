@@ -8,8 +8,10 @@ Tolerances (FP32 kernels vs FP64 oracle):
     rounding of the exponent s_j = -q_j/2 is about 1e-7 |q_j| with q_j up to ~100,
     i.e. ~1e-5 absolute in a weight's log, which moves y by ~1e-5 of the spread
     of the local predictions (O(1)).
-  * u_out (end to end): max_{t,c} |du| / max_t |u_ref[., c]| <= 1e-5 per channel,
-    the FP32 target of the method's accuracy contract.
+  * u_out (end to end): max_{t,c} |du| / scale_c <= 1e-5 per channel, the FP32
+    target of the method's accuracy contract, with scale_c = max_t |u_ref[., c]|
+    floored at sqrt(Sigma_u,c / K), the standard error of the mean perturbation
+    (with T = 1 a single |u_ref| can sit arbitrarily close to 0).
   * costs_out: max_k |dS_k| / S_k <= 1e-5.
 """
 import numpy as np
@@ -37,11 +39,13 @@ def _ctrl(p, **kw):
     return Controller(p.model, p.cost, M=p.M, model_noise=p.model_noise, **kw)
 
 
-def _u_err(u, ref):
+def _u_err(u, ref, sigma_u=None, K=None):
     u = np.asarray(u, np.float64)
     ref = np.asarray(ref, np.float64)
-    scale = np.maximum(np.abs(ref).max(axis=0), 1e-30)
-    return (np.abs(u - ref).max(axis=0) / scale)
+    scale = np.abs(ref).max(axis=0)
+    if sigma_u is not None:
+        scale = np.maximum(scale, np.sqrt(np.asarray(sigma_u, np.float64) / K))
+    return np.abs(u - ref).max(axis=0) / np.maximum(scale, 1e-30)
 
 
 def _oracle_update(oracle, p):
@@ -179,7 +183,7 @@ def test_end_to_end_ragged(oracle, K, T, L, M, noise, kind):
     u, c = ctl.update(p.x0, p.u_nom, p.K, p.T, p.lam, p.sigma_u, p.seed)
     ctl.sync()
     uref, cref = _oracle_update(oracle, p)
-    eu = _u_err(u.cpu().numpy(), uref)
+    eu = _u_err(u.cpu().numpy(), uref, p.sigma_u, p.K)
     ec = np.max(np.abs(c.cpu().numpy() - cref) / np.maximum(cref, 1e-3))
     print(f"K={K} T={T} L={L} M={M}: u err {eu} cost err {ec:.3g}")
     assert np.all(eu <= U_TOL)
