@@ -159,6 +159,34 @@ int pi_reserve(pi_ctx *ctx, int K, int T);
 int pi_update(pi_ctx *ctx, const float *x0, const float *u_nominal, int K, int T, float lambda,
               const float *sigma_u, uint64_t seed, float *u_out, float *costs_out);
 
+/* Limits of pi_update_noalloc's fixed scratch. */
+#define PI2RH_NOALLOC_MAX_K 65536
+#define PI2RH_NOALLOC_MAX_T 4096
+#define PI2RH_NOALLOC_MAX_KT 1048576
+
+/* pi_update for callers that cannot allocate device memory once they are
+ * running: a real-time control loop that must not call cudaMalloc after
+ * start-up (allocation can block, synchronize the device or fail at any
+ * moment), or a host program that owns all GPU memory through its own pool.
+ * There is no counterpart in the paper; it is a deployment variant.
+ *
+ * Same arguments, results and stream semantics as pi_update, but it calls no
+ * allocating routine: the per-update scratch lives in one fixed device array
+ * of about 21 MiB inside the library, held by every GPU that loads the library
+ * until the process exits.  Limits: K <= PI2RH_NOALLOC_MAX_K,
+ * T <= PI2RH_NOALLOC_MAX_T, K*T <= PI2RH_NOALLOC_MAX_KT; larger sizes return
+ * PI_ERR_INVALID_ARG with a message and launch nothing.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) and caches it; make that first call before any
+ * stream capture.  All calls on a device share the one array: calls whose
+ * work overlaps on the GPU (different streams or contexts without ordering
+ * between them) race and corrupt each other's results; order them on one
+ * stream or synchronize between them.  Every scratch element a call reads is
+ * written earlier in the same call, so no clearing is needed between calls. */
+int pi_update_noalloc(pi_ctx *ctx, const float *x0, const float *u_nominal, int K, int T,
+                      float lambda, const float *sigma_u, uint64_t seed, float *u_out,
+                      float *costs_out);
+
 /* Same update with HOST buffers (x0 [12], u_nominal [T][4], u_out [T][4],
  * costs_out [K]): copies inputs to context-owned device buffers, runs
  * pi_update, copies results back and synchronizes the stream before

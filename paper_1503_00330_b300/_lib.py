@@ -55,6 +55,8 @@ _SIGS = {
     "pi_reserve": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
     "pi_update": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_float, _fp,
                                  ctypes.c_uint64, _vp, _vp]),
+    "pi_update_noalloc": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_float, _fp,
+                                         ctypes.c_uint64, _vp, _vp]),
     "pi_update_host": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_float, _fp,
                                       ctypes.c_uint64, _vp, _vp]),
     "pi_sync": (ctypes.c_int, [_vp]),

@@ -11,36 +11,11 @@
 #include <vector>
 
 #include "pi2rh.h"
+#include "pi2rh_ctx.h"
 #include "pi2rh_kernels.h"
 
 using namespace pi2rh;
 
-struct pi_ctx {
-    int device = 0;
-    cudaStream_t stream = nullptr;
-    pi_opts opts{};
-    int L = 0, P = 0, spo = 0;
-    float dt = 0.f;
-    float2 *d_rec = nullptr;   // packed model [NY][P][REC_LEN]
-    float2 *d_obs = nullptr;
-    CostDev cost{};
-    int *d_err = nullptr;
-    // per-update scratch
-    float *d_cost = nullptr;   // [T][K]
-    float4 *d_eps = nullptr;   // [T][K]
-    float *d_phi = nullptr;    // [K]
-    double *d_part = nullptr;  // [nblk][T][6]
-    size_t cap_cost = 0, cap_eps = 0, cap_phi = 0, cap_part = 0;
-    // staging for the host-buffer path
-    float *d_x0 = nullptr, *d_unom = nullptr, *d_uout = nullptr, *d_costs = nullptr;
-    size_t cap_x0 = 0, cap_unom = 0, cap_uout = 0, cap_costs = 0;
-    // receding-horizon advance scratch: z [16], y [12], var [12]
-    float *d_rh = nullptr;
-    // per-kernel timing
-    bool timing = false;
-    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
-    uint64_t launches = 0;
-};
 
 namespace {
 
@@ -213,6 +188,11 @@ void free_ctx_memory(pi_ctx *c)
 }
 
 }  // namespace
+
+int pi2rh_fail(int code, const char *msg)
+{
+    return fail(code, "%s", msg);
+}
 
 extern "C" {
 
