@@ -257,6 +257,13 @@ int pi_debug_reduce(pi_ctx *ctx, const float *cost, const float *phi, const floa
                     const float *u_nominal, int K, int T, float lambda, float *u_out,
                     float *costs_out);
 
+/* Tensor-core GEMM core of the tensor-core form, checked on its own:
+ * D [128][64] f32 = A [128][K] x B [64][K]^T with A, B fp16 (IEEE binary16,
+ * row-major, device), K a multiple of 16 in [16, 160].  One CTA; operands are
+ * staged in shared memory in the K-major core-matrix layout and multiplied by
+ * tcgen05.mma into tensor memory.  Device errors are reported by pi_sync. */
+int pi_debug_tc_gemm(pi_ctx *ctx, const void *A, const void *B, int K, float *D);
+
 #ifdef __cplusplus
 }
 #endif

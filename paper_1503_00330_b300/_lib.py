@@ -66,6 +66,7 @@ _SIGS = {
     "pi_rh_advance": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _vp]),
     "pi_set_timing": (ctypes.c_int, [_vp, ctypes.c_int]),
     "pi_stage_times": (ctypes.c_int, [_vp, _fp]),
+    "pi_debug_tc_gemm": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _vp]),
     "pi_debug_noise": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp]),
     "pi_debug_normals": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp,
                                         _vp]),

@@ -522,4 +522,15 @@ int pi_debug_reduce(pi_ctx *c, const float *cost, const float *phi, const float 
                          costs_out);
 }
 
+int pi_debug_tc_gemm(pi_ctx *c, const void *A, const void *B, int K, float *D)
+{
+    if (!c) return fail(PI_ERR_INVALID_ARG, "ctx is NULL");
+    if (!A || !B || !D || K < 16 || K > 160 || K % 16) return fail(PI_ERR_INVALID_ARG, "bad argument");
+    DeviceGuard dg(c->device);
+    PI_CUDA(dg.err, "cudaSetDevice");
+    PI_CUDA(launch_tc_gemm_check(A, B, K, D, c->d_err, c->stream), "tc gemm launch");
+    c->launches++;
+    return PI_OK;
+}
+
 }  // extern "C"

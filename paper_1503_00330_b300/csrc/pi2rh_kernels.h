@@ -52,6 +52,9 @@ cudaError_t launch_rh_build_z(const float *x0, const float *u_out, float *z, cud
 cudaError_t launch_rh_apply(float *x0, const float *y, float dt, const float *u_out, int T, float *u_next,
                             cudaStream_t s);
 
+// Staged check of the tensor-core GEMM core: D[128x64] = A[128xK] B[64xK]^T, fp16 in, fp32 out.
+cudaError_t launch_tc_gemm_check(const void *A, const void *B, int K, float *D, int *err, cudaStream_t s);
+
 // Staged noise kernels.
 cudaError_t launch_noise_raw(uint64_t seed, int K, int T, int m, uint32_t *raw, cudaStream_t s);
 cudaError_t launch_noise_normals(uint64_t seed, int K, int T, int m, float *ctrl, float *model,
