@@ -63,7 +63,11 @@ enum {
     PI_ERR_UNSUPPORTED = 6  /* option not available in this build                  */
 };
 
-enum { PI_PRECISION_FP32 = 0 };
+/* PI_PRECISION_FP32: receptive fields evaluated on the FP32 FMA pipe.
+ * PI_PRECISION_TC_FP16X3: quadratic forms and local predictions as tensor-core
+ * GEMMs (tcgen05, fp16 hi/lo split, three products per term, fp32 accumulate);
+ * requires every LWPR input |z_a| < 255 so the fp16 features stay finite. */
+enum { PI_PRECISION_FP32 = 0, PI_PRECISION_TC_FP16X3 = 1 };
 enum { PI_NOISE_MEAN_ONLY = 0, PI_NOISE_SAMPLED = 1 };
 enum { PI_OBS_INDICATOR = 0, PI_OBS_GAUSSIAN = 1 };
 
@@ -115,7 +119,7 @@ typedef struct {
     const float *obs_xy;
 } pi_cost_params;
 
-/* Options.  precision: PI_PRECISION_FP32.  model_noise: PI_NOISE_SAMPLED
+/* Options.  precision: PI_PRECISION_FP32 or PI_PRECISION_TC_FP16X3.  model_noise: PI_NOISE_SAMPLED
  * (draw x' = x + dt (y + sigma n)) or PI_NOISE_MEAN_ONLY (x' = x + dt y).
  * M: sub-rollouts per rollout (Sec. 3.2), a power of two in [1, 64].
  * device: CUDA device ordinal. */

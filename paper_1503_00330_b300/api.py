@@ -36,8 +36,10 @@ def _sigma4(sigma_u):
 class Controller:
     """One LWPR model + cost on one GPU (a ``pi_ctx``)."""
 
+    PRECISIONS = {"fp32": 0, "tc": 1}
+
     def __init__(self, model: LwprModel, cost: CostParams, M: int = 1, model_noise: bool = True,
-                 device: int = 0):
+                 device: int = 0, precision: str = "fp32"):
         lib = _lib.load()
         self._lib = lib
         self.device = torch.device("cuda", device)
@@ -49,7 +51,8 @@ class Controller:
                               cost.Q_vel, cost.Q_ang, cost.w_obs, cost.obs_sharp, cost.radius,
                               cost.w_crash, cost.w_var, cost.w_T, int(cost.obs_kind), int(obs.shape[0]),
                               obs.ctypes.data if obs.size else None)
-        opts = _lib.OptsC(0, 1 if model_noise else 0, int(M), int(device))
+        self.precision = precision
+        opts = _lib.OptsC(self.PRECISIONS[precision], 1 if model_noise else 0, int(M), int(device))
         h = ctypes.c_void_p()
         check(lib.pi_create(ctypes.byref(lw), ctypes.byref(cp), ctypes.byref(opts), ctypes.byref(h)))
         self._h = h

@@ -10,9 +10,12 @@
 #include <string>
 #include <vector>
 
+#include <cuda_fp16.h>
+
 #include "pi2rh.h"
 #include "pi2rh_ctx.h"
 #include "pi2rh_kernels.h"
+#include "tc_ptx.cuh"
 
 using namespace pi2rh;
 
@@ -143,9 +146,44 @@ RolloutArgs base_args(const pi_ctx *c)
     return a;
 }
 
+TcArgs tc_args(const pi_ctx *c)
+{
+    TcArgs t{};
+    t.wtiles = c->d_wtiles;
+    t.wconst = c->d_wconst;
+    t.tiles_per_out = c->tiles_per_out;
+    t.cost = c->cost;
+    t.dt = c->dt;
+    t.M = c->opts.M;
+    t.model_noise = c->opts.model_noise == PI_NOISE_SAMPLED ? 1 : 0;
+    t.err = c->d_err;
+    return t;
+}
+
 int launch_rollouts(pi_ctx *c, const float *x0, const float *u_nom, int K, int T,
                     const float *sigma_u, uint64_t seed, float *cost, float4 *eps, float *phi)
 {
+    if (c->opts.precision == PI_PRECISION_TC_FP16X3) {
+        TcArgs t = tc_args(c);
+        t.K = K;
+        t.T = T;
+        for (int i = 0; i < 4; ++i) t.sqrt_sigma_u[i] = sqrtf(sigma_u[i]);
+        t.seed = seed;
+        t.x0 = x0;
+        t.u_nom = u_nom;
+        t.cost_tk = cost;
+        t.eps_tk = eps;
+        t.phi = phi;
+        {
+            cudaError_t e = launch_rollout_tc(t, c->stream);
+            if (e != cudaSuccess) {
+                std::string w = std::string("tensor-core rollout kernel launch (") + tc_launch_diag() + ")";
+                return cuda_fail(e, w.c_str());
+            }
+        }
+        c->launches++;
+        return PI_OK;
+    }
     RolloutArgs a = base_args(c);
     a.K = K;
     a.T = T;
@@ -179,12 +217,75 @@ int launch_reduce(pi_ctx *c, const float *cost, const float *phi, const float4 *
 void free_ctx_memory(pi_ctx *c)
 {
     void *ptrs[] = {c->d_rec, c->d_obs, c->d_err, c->d_cost, c->d_eps, c->d_phi, c->d_part,
-                    c->d_x0, c->d_unom, c->d_uout, c->d_costs, c->d_rh};
+                    c->d_x0, c->d_unom, c->d_uout, c->d_costs, c->d_rh, c->d_wtiles, c->d_wconst};
     for (void *p : ptrs)
         if (p) cudaFreeAsync(p, c->stream);
     cudaStreamSynchronize(c->stream);
     for (cudaEvent_t &e : c->ev)
         if (e) cudaEventDestroy(e);
+}
+
+}  // namespace
+
+namespace {
+
+// Packs the model for the tensor-core form: per output and tile of 64 fields,
+// the fp16 hi/lo coefficient tiles in the K-major core-matrix layout the MMAs
+// read, and the fp32 per-field constants (see rollout_tc.cu for the algebra).
+void pack_tc(const pi_lwpr_params *lw, int tiles, std::vector<unsigned char> &wt, std::vector<float> &wc)
+{
+    const int L = lw->L, TF = TC_TILE_FIELDS;
+    const double kap = 0.72134752044448170368;   // log2(e) / 2
+    wt.assign((size_t)NY * tiles * TC_TILE_BYTES, 0);
+    wc.assign((size_t)NY * tiles * 3 * TF, 0.0f);
+    auto put = [&](unsigned char *tile, int off, int row, int k, int kdim, double v) {
+        const __half hi = __float2half_rn((float)v);
+        const __half lo = __float2half_rn((float)(v - (double)__half2float(hi)));
+        const uint32_t o = kmajor_offset(row, k, kdim);
+        *reinterpret_cast<__half *>(tile + off + o) = hi;
+        *reinterpret_cast<__half *>(tile + off + (off == TC_OFF_SHI ? TC_OFF_SLO - TC_OFF_SHI : TC_OFF_YLO - TC_OFF_YHI) + o) = lo;
+    };
+    for (int o = 0; o < NY; ++o)
+        for (int tt = 0; tt < tiles; ++tt) {
+            unsigned char *tile = wt.data() + ((size_t)o * tiles + tt) * TC_TILE_BYTES;
+            float *cst = wc.data() + ((size_t)o * tiles + tt) * 3 * TF;
+            for (int i = 0; i < TF; ++i) {
+                const int j = tt * TF + i;
+                if (j >= L) {
+                    cst[i] = -INFINITY;          // padding field: zero weight
+                    continue;
+                }
+                const size_t f = (size_t)o * L + j;
+                const float *c = lw->c + f * NZ;
+                const float *D = lw->D + f * NZ * NZ;
+                const float *beta = lw->beta + f * NZ;
+                double Dsc[NZ], cDc = 0.0, bc = 0.0;
+                for (int a2 = 0; a2 < NZ; ++a2) {
+                    double acc = 0.0;
+                    for (int b2 = 0; b2 < NZ; ++b2)
+                        acc += 0.5 * ((double)D[a2 * NZ + b2] + (double)D[b2 * NZ + a2]) * (double)c[b2];
+                    Dsc[a2] = acc;
+                    cDc += (double)c[a2] * acc;
+                    bc += (double)beta[a2] * (double)c[a2];
+                }
+                for (int k = 0; k < TC_KF; ++k) {
+                    double v = 0.0;
+                    if (k < 16) {
+                        v = 2.0 * kap * Dsc[k];
+                    } else if (k < 152) {
+                        const int ra = tc_feat_row(k), cb = tc_feat_col(k);
+                        v = ra == cb ? -kap * (double)D[ra * NZ + ra]
+                                     : -kap * ((double)D[ra * NZ + cb] + (double)D[cb * NZ + ra]);
+                    }
+                    put(tile, TC_OFF_SHI, i, k, TC_KF, v);
+                }
+                for (int k = 0; k < 16; ++k) put(tile, TC_OFF_YHI, i, k, 16, (double)beta[k]);
+                cst[i] = (float)(-kap * cDc);
+                cst[TF + i] = (float)((double)lw->b[f] - bc);
+                const double sg = (double)lw->sigma[f];
+                cst[2 * TF + i] = (float)(sg * sg);
+            }
+        }
 }
 
 }  // namespace
@@ -224,7 +325,7 @@ int pi_create(const pi_lwpr_params *lw, const pi_cost_params *cp, const pi_opts 
     if (!(lw->dt > 0.0f) || !std::isfinite(lw->dt)) return fail(PI_ERR_INVALID_ARG, "dt must be > 0");
     if (!lw->c || !lw->D || !lw->beta || !lw->b || !lw->sigma)
         return fail(PI_ERR_INVALID_ARG, "an LWPR array is NULL");
-    if (opts.precision != PI_PRECISION_FP32)
+    if (opts.precision != PI_PRECISION_FP32 && opts.precision != PI_PRECISION_TC_FP16X3)
         return fail(PI_ERR_UNSUPPORTED, "precision %d is not available", opts.precision);
     if (opts.model_noise != PI_NOISE_SAMPLED && opts.model_noise != PI_NOISE_MEAN_ONLY)
         return fail(PI_ERR_INVALID_ARG, "model_noise must be 0 or 1");
@@ -305,6 +406,18 @@ int pi_create(const pi_lwpr_params *lw, const pi_cost_params *cp, const pi_opts 
         return bail(e, "obstacle copy");
     if ((e = cudaMalloc(&c->d_err, sizeof(int))) != cudaSuccess) return bail(e, "error word alloc");
     if ((e = cudaMemset(c->d_err, 0, sizeof(int))) != cudaSuccess) return bail(e, "error word clear");
+    if (opts.precision == PI_PRECISION_TC_FP16X3) {
+        std::vector<unsigned char> wt;
+        std::vector<float> wc;
+        c->tiles_per_out = (L + TC_TILE_FIELDS - 1) / TC_TILE_FIELDS;
+        pack_tc(lw, c->tiles_per_out, wt, wc);
+        if ((e = cudaMalloc(&c->d_wtiles, wt.size())) != cudaSuccess) return bail(e, "tile alloc");
+        if ((e = cudaMemcpy(c->d_wtiles, wt.data(), wt.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
+            return bail(e, "tile copy");
+        if ((e = cudaMalloc(&c->d_wconst, wc.size() * sizeof(float))) != cudaSuccess) return bail(e, "const alloc");
+        if ((e = cudaMemcpy(c->d_wconst, wc.data(), wc.size() * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess)
+            return bail(e, "const copy");
+    }
     CostDev &C = c->cost;
     for (int d = 0; d < 3; ++d) {
         C.goal[d] = cp->goal[d];
@@ -483,6 +596,23 @@ int pi_debug_lwpr(pi_ctx *c, const float *z, int n, float *y, float *var)
     if (n < 1 || !z || !y || !var) return fail(PI_ERR_INVALID_ARG, "bad argument");
     DeviceGuard dg(c->device);
     PI_CUDA(dg.err, "cudaSetDevice");
+    if (c->opts.precision == PI_PRECISION_TC_FP16X3) {
+        TcArgs t = tc_args(c);
+        t.M = 1;
+        t.z_in = z;
+        t.y_out = y;
+        t.var_out = var;
+        t.n_pred = n;
+        {
+            cudaError_t e = launch_predict_tc(t, c->stream);
+            if (e != cudaSuccess) {
+                std::string w = std::string("tensor-core predict kernel launch (") + tc_launch_diag() + ")";
+                return cuda_fail(e, w.c_str());
+            }
+        }
+        c->launches++;
+        return PI_OK;
+    }
     RolloutArgs a = base_args(c);
     a.M = 1;
     a.z_in = z;

@@ -15,6 +15,9 @@ struct pi_ctx {
     int L = 0, P = 0, spo = 0;
     float dt = 0.f;
     float2 *d_rec = nullptr;   // packed model [NY][P][REC_LEN]
+    unsigned char *d_wtiles = nullptr;   // tensor-core coefficient tiles (precision TC)
+    unsigned char *d_wconst = nullptr;   // tensor-core per-field constants
+    int tiles_per_out = 0;
     float2 *d_obs = nullptr;
     pi2rh::CostDev cost{};
     int *d_err = nullptr;

@@ -38,6 +38,62 @@ constexpr int RF_PAIRS_PER_STAGE = RF_CONSUMER_WARPS;
 cudaError_t launch_rollout_fp32(const RolloutArgs &a, cudaStream_t s);
 cudaError_t launch_predict_fp32(const RolloutArgs &a, cudaStream_t s);
 
+// ---------------------------------------------------------------------------
+// Tensor-core form.  Coefficient tiles of 64 fields are pre-packed at context
+// creation in the exact shared-memory image the MMAs read (fp16, K-major
+// core-matrix layout): S hi, S lo ([64][160]), Y hi, Y lo ([64][16]); the
+// per-field constants (cs, cy, sigma^2; 3 x 64 floats) are packed separately.
+// ---------------------------------------------------------------------------
+constexpr int TC_SLOTS = 128;           // rollout slots per CTA (MMA M)
+constexpr int TC_TILE_FIELDS = 64;      // fields per tile (MMA N)
+constexpr int TC_KF = 160;              // feature columns: z (16), z_a z_b (136), 0 (8)
+constexpr int TC_OFF_SHI = 0;
+constexpr int TC_OFF_SLO = TC_OFF_SHI + TC_TILE_FIELDS * TC_KF * 2;
+constexpr int TC_OFF_YHI = TC_OFF_SLO + TC_TILE_FIELDS * TC_KF * 2;
+constexpr int TC_OFF_YLO = TC_OFF_YHI + TC_TILE_FIELDS * 16 * 2;
+constexpr int TC_TILE_BYTES = TC_OFF_YLO + TC_TILE_FIELDS * 16 * 2;   // 45,056
+constexpr int TC_CONST_BYTES = 3 * TC_TILE_FIELDS * 4;                // 768
+
+// Quadratic feature k (16 <= k < 152) is z_a z_b with (a, b) the (k-16)-th
+// entry of the row-major upper triangle; features k < 16 are z_k.
+__host__ __device__ constexpr int tc_feat_row(int k)
+{
+    int t = k - 16, a = 0;
+    while (a < 16 && t >= 16 - a) { t -= 16 - a; ++a; }
+    return a;
+}
+__host__ __device__ constexpr int tc_feat_col(int k)
+{
+    int t = k - 16, a = 0;
+    while (a < 16 && t >= 16 - a) { t -= 16 - a; ++a; }
+    return a + t;
+}
+
+struct TcArgs {
+    const unsigned char *wtiles;   // [NY][tiles_per_out][TC_TILE_BYTES]
+    const unsigned char *wconst;   // [NY][tiles_per_out][TC_CONST_BYTES]
+    int tiles_per_out;
+    CostDev cost;
+    float dt;
+    int K, T, M;
+    int model_noise;
+    float sqrt_sigma_u[4];
+    uint64_t seed;
+    const float *x0;
+    const float *u_nom;
+    float *cost_tk;
+    float4 *eps_tk;
+    float *phi;
+    const float *z_in;
+    float *y_out, *var_out;
+    int n_pred;
+    int *err;
+};
+
+cudaError_t launch_rollout_tc(const TcArgs &a, cudaStream_t s);
+cudaError_t launch_predict_tc(const TcArgs &a, cudaStream_t s);
+const char *tc_launch_diag();   // resources of the tensor-core kernel (for error messages)
+
 // Cost-to-go scan + per-CTA log-sum-exp partials, then the merge over CTAs.
 constexpr int RS_KC = 64;   // rollouts per CTA of the scan kernel
 int scan_blocks(int K);

@@ -1,5 +1,12 @@
-"""Tensor-core GEMM core (tcgen05.mma kind::f16, fp32 accumulate in TMEM)
-against a float64 product of the same fp16 operands."""
+"""Tensor-core form: the tcgen05 GEMM core against a float64 product of the
+same fp16 operands, and the tensor-core rollout path (fp16 hi/lo split,
+three products per term) against the FP64 oracle.
+
+The split keeps each product to ~2^-22 relative, so the tensor-core form is
+held to the same tolerances as the FP32 form: LWPR mean |dy| <= 2e-5 (1 + |y|),
+variance |dvar| <= 2e-5 var + 1e-6, u_out 1e-5 per channel (scale as in the
+parity tests), costs 1e-5 relative.  The method's stated bound for this form
+(2e-3) is looser; the tests use the FP32 one."""
 import ctypes
 
 import numpy as np
@@ -42,3 +49,62 @@ def test_tc_gemm_core(ctl, K):
     print(f"K={K}: max err {err.max():.3g}, worst ratio {np.max(err / bound):.3g}")
     assert np.all(np.isfinite(d))
     assert np.all(err <= bound)
+
+
+def _tc(p):
+    from paper_1503_00330_b300.api import Controller
+    return Controller(p.model, p.cost, M=p.M, model_noise=p.model_noise, precision="tc")
+
+
+def _u_err(u, ref, sigma_u, K):
+    u, ref = np.asarray(u, np.float64), np.asarray(ref, np.float64)
+    scale = np.maximum(np.abs(ref).max(0), np.sqrt(np.asarray(sigma_u, np.float64) / K))
+    return np.abs(u - ref).max(0) / scale
+
+
+@pytest.mark.parametrize("L,n,cond", [(1, 5, False), (3, 70, False), (64, 200, False), (100, 130, True),
+                                      (257, 129, False)])
+def test_tc_lwpr_predict(ctl, oracle, L, n, cond):
+    p = W.problem(8, 4, L, seed=L, conditioned=cond)
+    tc = _tc(p)
+    g = np.random.default_rng(L)
+    z = np.concatenate([g.normal(0, 0.5, (n, 12)), g.normal(0, 0.3, (n, 4))], 1).astype(np.float32)
+    y, v = tc.debug_lwpr(z)
+    tc.sync()
+    y, v = y.cpu().numpy().astype(np.float64), v.cpu().numpy().astype(np.float64)
+    yr, vr = oracle.lwpr_predict(p.model, z)
+    ey = np.max(np.abs(y - yr) / (1 + np.abs(yr)))
+    print(f"TC L={L} n={n}: y err {ey:.3g}, var worst {np.max(np.abs(v - vr) / (2e-5 * vr + 1e-6)):.3g} of bound")
+    assert ey <= 2e-5
+    assert np.all(np.abs(v - vr) <= 2e-5 * vr + 1e-6)
+
+
+@pytest.mark.parametrize("K,T,L,M,noise", [(256, 50, 64, 1, True), (65, 3, 2, 1, True), (130, 17, 70, 2, True),
+                                           (200, 12, 33, 1, False)])
+def test_tc_end_to_end(ctl, oracle, K, T, L, M, noise):
+    p = W.problem(K, T, L, seed=7 + K, n_obs=4, M=M, model_noise=noise)
+    tc = _tc(p)
+    u, c = tc.update(p.x0, p.u_nom, p.K, p.T, p.lam, p.sigma_u, p.seed)
+    tc.sync()
+    uref, cref = oracle.pi_update(p.model, p.cost, p.x0, p.u_nom, p.K, p.T, p.lam, p.sigma_u, p.seed, M=p.M,
+                                  model_noise=p.model_noise)
+    eu = _u_err(u.cpu().numpy(), uref, p.sigma_u, p.K)
+    ec = np.max(np.abs(c.cpu().numpy() - cref) / cref)
+    print(f"TC K={K} T={T} L={L} M={M}: u err {eu}, cost err {ec:.3g}")
+    assert np.all(eu <= 1e-5)
+    assert ec <= 1e-5
+
+
+def test_tc_precision_workload_sampled(ctl, oracle):
+    """K=65536, T=100, L=2048, cond(D) in [1, 1e3]: sampled rollouts' S_{k,0}."""
+    p = W.precision()
+    tc = _tc(p)
+    u, c = tc.update(p.x0, p.u_nom, p.K, p.T, p.lam, p.sigma_u, p.seed)
+    tc.sync()
+    c = c.cpu().numpy().astype(np.float64)
+    for k in (0, 30001, 65535):
+        r = oracle.rollouts(p.model, p.cost, p.x0, p.u_nom, 1, p.T, p.sigma_u, p.seed, k0=k)
+        S0 = oracle.cost_to_go(r["cost"], r["phi"], float(p.model.dt))[0, 0]
+        print(f"TC precision rollout {k}: rel err {abs(c[k] - S0) / S0:.3g}")
+        assert abs(c[k] - S0) / S0 <= 1e-5
+    assert np.all(np.isfinite(u.cpu().numpy()))
