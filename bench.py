@@ -131,6 +131,11 @@ def workload(name: str, seed: int):
         p.T = 10
         p.u_nom = p.u_nom[:10].copy()
         return p, "realtime_short (profiling case): K=8192, T=10, L=512 x 12 outputs, 16 obstacles"
+    if name == "precision_short":
+        p = W.precision(seed)
+        p.T = 5
+        p.u_nom = p.u_nom[:5].copy()
+        return p, "precision_short (profiling case): K=65536, T=5, L=2048 x 12 outputs, cond(D) logU[1,1e3]"
     if name == "small":
         return W.small(seed), "small: K=256, T=50, L=64 x 12 outputs, 4 obstacles"
     if name == "precision":
@@ -203,6 +208,73 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+TC_FIELDS_PER_TILE = 64
+TC_MMA_FLOPS_PER_FIELD = 3 * 2 * (160 + 16)   # hi*hi + hi*lo + lo*hi over K=160 (S) and K=16 (Y)
+
+
+def form_roofline(precision, rollout_ms, K, T, M, L, dev, peaks, workload):
+    """Roofline of the rollout kernel from its per-launch CUDA-event times."""
+    import torch
+    props = torch.cuda.get_device_properties(dev)
+    avg_s = statistics.mean(rollout_ms) / 1e3
+    useful = float(K) * T * M * 12 * L * FLOPS_PER_FIELD
+    if precision == "fp32":
+        sm_max_mhz = float(peaks.get("sm_max_mhz", 2032.0))
+        peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12
+        achieved = useful / avg_s / 1e12
+        return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": profile_traffic(f"rollout_fp32_{workload}.md"), "kernel": "rollout_fp32_kernel",
+                "peak_basis": f"FP32 FMA pipe: {props.multi_processor_count} SMs x {FP32_LANES_PER_SM} lanes x 2 flop "
+                              f"x {sm_max_mhz:.0f} MHz (max SM clock)",
+                "rollout_ms_per_launch": statistics.mean(rollout_ms)}
+    L_pad = -(-L // TC_FIELDS_PER_TILE) * TC_FIELDS_PER_TILE
+    issued = float(K) * T * M * 12 * L_pad * TC_MMA_FLOPS_PER_FIELD
+    peak = float(peaks.get("bf16_tflops_sustained", 1366.3))
+    achieved = issued / avg_s / 1e12
+    return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": profile_traffic(f"rollout_tc_{workload}.md"), "kernel": "rollout_tc_kernel",
+            "peak_basis": "measured dense bf16 sustained (fp16 has the same nominal rate); achieved counts the "
+                          "issued fp16 MMA flops (3 split products x 2 x 176 per field)",
+            "useful_tflops": useful / avg_s / 1e12,
+            "rollout_ms_per_launch": statistics.mean(rollout_ms)}
+
+
+def time_form(precision, p, args, dev):
+    """The receding-horizon loop of `p` timed the same way with the other form."""
+    import torch
+    from paper_1503_00330_b300.api import Controller
+    K, T, M, L = p.K, p.T, p.M, p.model.L
+    ctl = Controller(p.model, p.cost, M=M, model_noise=p.model_noise, device=dev.index, precision=precision)
+    ctl.set_timing(True)
+    ctl.reserve(K, T)
+    x0 = torch.as_tensor(p.x0, device=dev).clone()
+    ua = torch.as_tensor(p.u_nom, device=dev).clone()
+    ub = torch.empty_like(ua)
+    costs = torch.empty(K, dtype=torch.float32, device=dev)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    rollout_ms, step_ms = [], []
+    for i in range(args.warmup + args.steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ctl.update(x0, ua, K, T, p.lam, p.sigma_u, p.seed + i, u_out=ub, costs_out=costs)
+        ctl.rh_advance(x0, ub, ua)
+        b.record(stream)
+        r = ctl.stage_times()[0]
+        b.synchronize()
+        if i >= args.warmup:
+            rollout_ms.append(r)
+            step_ms.append(a.elapsed_time(b))
+    ctl.sync()
+    ctl.close()
+    total_s = sum(step_ms) / 1e3
+    roof = form_roofline(precision, rollout_ms, K, T, M, L, dev, measured_peaks(), args.workload)
+    roof["rollout_share_of_step"] = sum(rollout_ms) / sum(step_ms)
+    return {"value": K * T * M * args.steps / total_s, "ms_per_update": 1e3 * total_s / args.steps,
+            "roofline": roof}
+
+
 def run_ours(args):
     import torch
     from paper_1503_00330_b300 import build
@@ -215,7 +287,7 @@ def run_ours(args):
     p, desc = workload(args.workload, rank)          # replicas: rank-dependent seed
     K, T, M, L = p.K, p.T, p.M, p.model.L
 
-    ctl = Controller(p.model, p.cost, M=M, model_noise=p.model_noise, device=local)
+    ctl = Controller(p.model, p.cost, M=M, model_noise=p.model_noise, device=local, precision=args.precision)
     ctl.set_timing(True)
     ctl.reserve(K, T)
     x0 = torch.as_tensor(p.x0, device=dev).clone()
@@ -277,25 +349,18 @@ def run_ours(args):
         return
 
     peaks = measured_peaks()
-    props = torch.cuda.get_device_properties(dev)
-    sm_max_mhz = float(peaks.get("sm_max_mhz", 2032.0))
-    peak_tflops = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12
-    flops_per_launch = float(K) * T * M * 12 * L * FLOPS_PER_FIELD
-    avg_rollout_s = statistics.mean(rollout_ms) / 1e3
-    achieved = flops_per_launch / avg_rollout_s / 1e12
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                "frac": achieved / peak_tflops,
-                "traffic": profile_traffic(f"rollout_fp32_{args.workload}.md"),
-                "kernel": "rollout_fp32_kernel",
-                "peak_basis": f"FP32 FMA pipe: {props.multi_processor_count} SMs x {FP32_LANES_PER_SM} lanes x 2 flop "
-                              f"x {sm_max_mhz:.0f} MHz (max SM clock)",
-                "rollout_ms_per_launch": statistics.mean(rollout_ms),
-                "rollout_share_of_step": sum(rollout_ms) / sum(step_ms)}
+    roofline = form_roofline(args.precision, rollout_ms, K, T, M, L, dev, peaks, args.workload)
+    roofline["rollout_share_of_step"] = sum(rollout_ms) / sum(step_ms)
+    forms = {args.precision: {"value": value, "ms_per_update": 1e3 * total_s / args.steps,
+                              "roofline": roofline}}
+    if not args.no_compare:
+        other = "tc" if args.precision == "fp32" else "fp32"
+        forms[other] = time_form(other, p, args, dev)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded generator; quadrotor-shaped LWPR model and obstacle field)",
-            "config": {"workload": desc, "K": K, "T": T, "L": L, "M": M, "precision": "fp32",
+            "config": {"workload": desc, "K": K, "T": T, "L": L, "M": M, "precision": args.precision,
                        "parallelism": "replicas" if ws > 1 else "single",
                        "l2": "flushed between timed steps (256 MiB write outside the event window); "
                              "per-update working set ~21 MB"},
@@ -304,6 +369,7 @@ def run_ours(args):
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": (12 + T * 4) * 4,
                     "d2h_bytes_per_step": (T * 4 + K) * 4},
             "roofline": roofline,
+            "forms": forms,
             "clocks": clocks.summary()}
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(p, args.cpu_sample)
@@ -318,10 +384,13 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["realtime", "realtime_short", "small", "precision"], default="realtime")
+    ap.add_argument("--workload", choices=["realtime", "realtime_short", "small", "precision", "precision_short"], default="realtime")
     ap.add_argument("--cpu-sample", type=int, default=256, help="rollouts in the CPU-baseline sample")
     ap.add_argument("--ref-sample", type=int, default=64, help="rollouts per reference-arm step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", choices=["fp32", "tc"], default="fp32",
+                    help="form of the headline line (the other form is timed too and reported under 'forms')")
+    ap.add_argument("--no-compare", action="store_true", help="skip timing the other form")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
