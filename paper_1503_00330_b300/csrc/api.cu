@@ -229,21 +229,24 @@ void free_ctx_memory(pi_ctx *c)
 
 namespace {
 
-// Packs the model for the tensor-core form: per output and tile of 64 fields,
-// the fp16 hi/lo coefficient tiles in the K-major core-matrix layout the MMAs
-// read, and the fp32 per-field constants (see rollout_tc.cu for the algebra).
+// Packs the model for the tensor-core form: per output and tile of 128
+// fields, 11 chunks of [hi | lo] fp16 coefficient blocks in the K-major
+// core-matrix layout the MMAs read (chunk j < 10: the S coefficients of K step
+// j; chunk 10: the Y coefficients), and the fp32 per-field constants (see
+// rollout_tc.cu for the algebra).
 void pack_tc(const pi_lwpr_params *lw, int tiles, std::vector<unsigned char> &wt, std::vector<float> &wc)
 {
     const int L = lw->L, TF = TC_TILE_FIELDS;
     const double kap = 0.72134752044448170368;   // log2(e) / 2
     wt.assign((size_t)NY * tiles * TC_TILE_BYTES, 0);
     wc.assign((size_t)NY * tiles * 3 * TF, 0.0f);
-    auto put = [&](unsigned char *tile, int off, int row, int k, int kdim, double v) {
+    auto put = [&](unsigned char *tile, int chunk, int row, int kin, double v) {
         const __half hi = __float2half_rn((float)v);
         const __half lo = __float2half_rn((float)(v - (double)__half2float(hi)));
-        const uint32_t o = kmajor_offset(row, k, kdim);
-        *reinterpret_cast<__half *>(tile + off + o) = hi;
-        *reinterpret_cast<__half *>(tile + off + (off == TC_OFF_SHI ? TC_OFF_SLO - TC_OFF_SHI : TC_OFF_YLO - TC_OFF_YHI) + o) = lo;
+        unsigned char *base = tile + (size_t)chunk * TC_CHUNK_BYTES;
+        const uint32_t o = kmajor_offset(row, kin, 16);
+        *reinterpret_cast<__half *>(base + o) = hi;
+        *reinterpret_cast<__half *>(base + TC_HALF_CHUNK + o) = lo;
     };
     for (int o = 0; o < NY; ++o)
         for (int tt = 0; tt < tiles; ++tt) {
@@ -277,9 +280,9 @@ void pack_tc(const pi_lwpr_params *lw, int tiles, std::vector<unsigned char> &wt
                         v = ra == cb ? -kap * (double)D[ra * NZ + ra]
                                      : -kap * ((double)D[ra * NZ + cb] + (double)D[cb * NZ + ra]);
                     }
-                    put(tile, TC_OFF_SHI, i, k, TC_KF, v);
+                    put(tile, k / 16, i, k % 16, v);
                 }
-                for (int k = 0; k < 16; ++k) put(tile, TC_OFF_YHI, i, k, 16, (double)beta[k]);
+                for (int k = 0; k < 16; ++k) put(tile, TC_KF / 16, i, k, (double)beta[k]);
                 cst[i] = (float)(-kap * cDc);
                 cst[TF + i] = (float)((double)lw->b[f] - bc);
                 const double sg = (double)lw->sigma[f];

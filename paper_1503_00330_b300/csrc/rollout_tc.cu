@@ -17,10 +17,13 @@
 //
 // Roles (one CTA per SM, 128 slots, 320 threads):
 //   warp 0 lane 0: producer -- 1-D bulk copies (TMA) of the pre-packed
-//                  coefficient tiles (64 fields, 45,056 B) into a 2-stage ring,
-//                  and of the per-field constants (cs, cy, sigma^2) into a
-//                  4-deep constant ring;
-//   warp 1 lane 0: MMA issuer -- 33 MMAs per tile (S: 10 K steps x 3, Y: 1 x 3)
+//                  coefficient chunks (8 KB: the hi and lo coefficient blocks
+//                  of one K step for 128 fields) into a ring of NSLOT chunk
+//                  slots, and of the per-field constants (cs, cy, sigma^2)
+//                  into a 4-deep constant ring;
+//   warp 1 lane 0: MMA issuer -- per tile of 128 fields, 33 MMAs (M=128,
+//                  N=128, K=16; S: 10 K steps x 3 split products, Y: 1 x 3),
+//                  releasing each chunk slot as soon as its MMAs complete,
 //                  into one of two TMEM accumulator buffers;
 //   warps 2-9:     epilogue -- tcgen05.ld of S and Y, online base-2 softmax
 //                  per output (chunks of 16 fields, one rescale per chunk),
@@ -43,19 +46,20 @@ namespace {
 constexpr int BM = TC_SLOTS;            // rollout slots per CTA (MMA M)
 constexpr int TNF = TC_TILE_FIELDS;     // fields per tile (MMA N)
 constexpr int KF = TC_KF;               // feature columns of phi (S GEMM K)
-constexpr int KY = 16;                  // Y GEMM K (z only)
-constexpr int NSTAGE = 2;
+constexpr int NCH = TC_CHUNKS_PER_TILE; // chunks per tile
+constexpr int NSLOT = 12;               // chunk slots in the ring
 constexpr int NCONST = 4;
 constexpr int NEPI = 8;                 // epilogue warps
 constexpr int NTHREADS = (2 + NEPI) * 32;
 constexpr int NE = NEPI * 32;
 constexpr int MAX_OBS = 256;
+constexpr int HALF = TNF / 2;           // columns per epilogue warp
 
 constexpr int PHI_BYTES = BM * KF * 2;                 // one fp16 feature tile
 constexpr int OFF_PHI_HI = 0;
 constexpr int OFF_PHI_LO = OFF_PHI_HI + PHI_BYTES;
-constexpr int OFF_STAGE = OFF_PHI_LO + PHI_BYTES;
-constexpr int OFF_CONST = OFF_STAGE + NSTAGE * TC_TILE_BYTES;
+constexpr int OFF_RING = OFF_PHI_LO + PHI_BYTES;
+constexpr int OFF_CONST = OFF_RING + NSLOT * TC_CHUNK_BYTES;
 constexpr int OFF_PART = OFF_CONST + NCONST * TC_CONST_BYTES;   // [2][5][BM]
 constexpr int OFF_Z = OFF_PART + 2 * 5 * BM * 4;                // [NZ][BM]
 constexpr int OFF_X = OFF_Z + NZ * BM * 4;                      // [NX][BM]
@@ -65,16 +69,16 @@ constexpr int OFF_YREF = OFF_V + NY * BM * 4;
 constexpr int OFF_Q = OFF_YREF + NY * BM * 4;                   // [BM]
 constexpr int OFF_OBS = OFF_Q + BM * 4;
 constexpr int OFF_BAR = OFF_OBS + MAX_OBS * 8;
-// barriers: stage_full[2], stage_empty[2], acc_full[2], acc_empty[2],
+// barriers: full[NSLOT], empty[NSLOT], acc_full[2], acc_empty[2],
 //           const_full[4], const_empty[4], phi_ready
-constexpr int NBARS = 2 * NSTAGE + 4 + 2 * NCONST + 1;
+constexpr int NBARS = 2 * NSLOT + 4 + 2 * NCONST + 1;
 constexpr int OFF_TSLOT = OFF_BAR + NBARS * 8;
 constexpr int OFF_ABORT = OFF_TSLOT + 8;
 constexpr int SMEM_BYTES = OFF_ABORT + 16;
-static_assert(OFF_STAGE % 128 == 0 && OFF_CONST % 16 == 0 && OFF_BAR % 8 == 0, "alignment");
+static_assert(OFF_RING % 128 == 0 && OFF_CONST % 16 == 0 && OFF_BAR % 8 == 0, "alignment");
 static_assert(SMEM_BYTES <= 232448, "shared memory budget");
 
-constexpr uint32_t TMEM_COLS = 256;     // 2 buffers x (S 64 + Y 64)
+constexpr uint32_t TMEM_COLS = 512;     // 2 buffers x (S 128 + Y 128)
 
 // Feature k of phi: k < 16 -> z_k * 1; 16 <= k < 152 -> z_a z_b; k >= 152 -> 0.
 __host__ __device__ constexpr int feat_a(int k) { return k < 16 ? k : tc_feat_row(k); }
@@ -152,8 +156,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) rollout_tc_kernel(const __grid_co
     float *qbuf = reinterpret_cast<float *>(smem + OFF_Q);
     float2 *obs_s = reinterpret_cast<float2 *>(smem + OFF_OBS);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + OFF_BAR);
-    uint64_t *stage_full = bars, *stage_empty = bars + 2, *acc_full = bars + 4, *acc_empty = bars + 6;
-    uint64_t *const_full = bars + 8, *const_empty = bars + 12, *phi_ready = bars + 16;
+    uint64_t *full = bars, *empty = bars + NSLOT, *acc_full = bars + 2 * NSLOT, *acc_empty = acc_full + 2;
+    uint64_t *const_full = acc_empty + 2, *const_empty = const_full + NCONST, *phi_ready = const_empty + NCONST;
     uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + OFF_TSLOT);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + OFF_ABORT);
 
@@ -169,9 +173,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) rollout_tc_kernel(const __grid_co
         tmem_relinquish();
     }
     if (tid == 0) {
+        for (int i = 0; i < NSLOT; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], 1);
+        }
         for (int i = 0; i < 2; ++i) {
-            mbar_init(&stage_full[i], 1);
-            mbar_init(&stage_empty[i], 1);
             mbar_init(&acc_full[i], 1);
             mbar_init(&acc_empty[i], NEPI);
         }
@@ -192,32 +198,38 @@ __global__ void __launch_bounds__(NTHREADS, 1) rollout_tc_kernel(const __grid_co
     if (warp == 0) {
         // -------------------------------------------------------------- producer
         if (lane == 0) {
-            long long issued = 0;
-            for (long long g = 0; g < total; ++g) {
-                const int s = (int)(g & 1), c = (int)(g & 3);
-                bool ok = true;
-                if (g >= 2) ok = mbar_wait_bounded(&stage_empty[s], (uint32_t)(((g >> 1) - 1) & 1), abort_flag);
-                if (ok && g >= 4) ok = mbar_wait_bounded(&const_empty[c], (uint32_t)(((g >> 2) - 1) & 1), abort_flag);
-                if (!ok) {
-                    if (!*abort_flag) atomicOr(a.err, DEVERR_TIMEOUT_EMPTY);
-                    *abort_flag = 1;
-                    break;
-                }
+            long long q = 0, issued_tiles = 0;             // chunks issued, tiles issued
+            int slot = 0;
+            bool ok = true;
+            for (long long g = 0; g < total && ok; ++g) {
+                const int c = (int)(g & 3);
+                if (g >= 4) ok = mbar_wait_bounded(&const_empty[c], (uint32_t)(((g >> 2) - 1) & 1), abort_flag);
+                if (!ok) break;
                 const long long tile = g % G;                   // (output, tile) in order
-                mbar_arrive_expect_tx(&stage_full[s], TC_TILE_BYTES);
-                bulk_g2s(smem + OFF_STAGE + s * TC_TILE_BYTES, a.wtiles + tile * TC_TILE_BYTES, TC_TILE_BYTES,
-                         &stage_full[s]);
                 mbar_arrive_expect_tx(&const_full[c], TC_CONST_BYTES);
                 bulk_g2s(smem + OFF_CONST + c * TC_CONST_BYTES, a.wconst + tile * TC_CONST_BYTES, TC_CONST_BYTES,
                          &const_full[c]);
-                issued = g + 1;
+                issued_tiles = g + 1;
+                for (int j = 0; j < NCH; ++j, ++q) {
+                    if (q >= NSLOT) {
+                        ok = mbar_wait_bounded(&empty[slot], (uint32_t)(((q / NSLOT) - 1) & 1), abort_flag);
+                        if (!ok) break;
+                    }
+                    mbar_arrive_expect_tx(&full[slot], TC_CHUNK_BYTES);
+                    bulk_g2s(smem + OFF_RING + slot * TC_CHUNK_BYTES,
+                             a.wtiles + tile * TC_TILE_BYTES + (size_t)j * TC_CHUNK_BYTES, TC_CHUNK_BYTES, &full[slot]);
+                    if (++slot == NSLOT) slot = 0;
+                }
             }
-            for (long long g = (issued > 4 ? issued - 4 : 0); g < issued; ++g) {
-                if (g >= issued - 2 && !mbar_wait_drain(&stage_full[g & 1], (uint32_t)((g >> 1) & 1)))
-                    atomicOr(a.err, DEVERR_TIMEOUT_DRAIN);
-                if (!mbar_wait_drain(&const_full[g & 3], (uint32_t)((g >> 2) & 1)))
-                    atomicOr(a.err, DEVERR_TIMEOUT_DRAIN);
+            if (!ok) {
+                if (!*abort_flag) atomicOr(a.err, DEVERR_TIMEOUT_EMPTY);
+                *abort_flag = 1;
             }
+            // keep the CTA alive until every copy issued has landed
+            for (long long r = (q > NSLOT ? q - NSLOT : 0); r < q; ++r)
+                if (!mbar_wait_drain(&full[r % NSLOT], (uint32_t)((r / NSLOT) & 1))) atomicOr(a.err, DEVERR_TIMEOUT_DRAIN);
+            for (long long g = (issued_tiles > NCONST ? issued_tiles - NCONST : 0); g < issued_tiles; ++g)
+                if (!mbar_wait_drain(&const_full[g & 3], (uint32_t)((g >> 2) & 1))) atomicOr(a.err, DEVERR_TIMEOUT_DRAIN);
         }
         __syncwarp();
     } else if (warp == 1) {
@@ -225,41 +237,51 @@ __global__ void __launch_bounds__(NTHREADS, 1) rollout_tc_kernel(const __grid_co
         if (lane == 0) {
             const uint32_t idesc = idesc_f16_f32(BM, TNF);
             const uint32_t phi_hi = smem_u32(smem + OFF_PHI_HI), phi_lo = smem_u32(smem + OFF_PHI_LO);
-            long long g = 0;
+            // descriptors: A = feature tile K step j (rows 2560 B apart), B = a
+            // chunk half (128 rows x 16 K, rows 256 B apart); slot/half offsets
+            // are added to the 14-bit start field (addresses stay < 256 KB).
+            uint64_t ah[KF / 16], al[KF / 16];
+#pragma unroll
+            for (int j = 0; j < KF / 16; ++j) {
+                ah[j] = smem_desc_kmajor(phi_hi + j * 256, 128, 16 * KF);
+                al[j] = smem_desc_kmajor(phi_lo + j * 256, 128, 16 * KF);
+            }
+            const uint64_t b0 = smem_desc_kmajor(smem_u32(smem + OFF_RING), 128, 256);
+            long long g = 0, q = 0, q_committed = -1;
+            int slot = 0;
             bool ok = true;
             for (int t = 0; t < nsteps && ok; ++t) {
                 ok = mbar_wait_bounded(phi_ready, (uint32_t)(t & 1), abort_flag);
                 tc_fence_after();
-                for (int j = 0; j < G && ok; ++j, ++g) {
-                    const int s = (int)(g & 1), buf = (int)(g & 1);
-                    ok = mbar_wait_bounded(&stage_full[s], (uint32_t)((g >> 1) & 1), abort_flag);
-                    if (ok && g >= 2) ok = mbar_wait_bounded(&acc_empty[buf], (uint32_t)(((g >> 1) - 1) & 1), abort_flag);
+                for (int jt = 0; jt < G && ok; ++jt, ++g) {
+                    const int buf = (int)(g & 1);
+                    if (g >= 2) ok = mbar_wait_bounded(&acc_empty[buf], (uint32_t)(((g >> 1) - 1) & 1), abort_flag);
                     if (!ok) break;
                     tc_fence_after();
-                    const uint32_t st = smem_u32(smem + OFF_STAGE + s * TC_TILE_BYTES);
-                    const uint32_t dS = tbase + buf * 128, dY = tbase + buf * 128 + 64;
-                    const uint32_t sbo_a = 16 * KF, sbo_s = 16 * KF, sbo_y = 16 * KY;
-#pragma unroll 1
-                    for (int ks = 0; ks < KF / 16; ++ks) {
-                        const uint64_t ah = smem_desc_kmajor(phi_hi + ks * 256, 128, sbo_a);
-                        const uint64_t al = smem_desc_kmajor(phi_lo + ks * 256, 128, sbo_a);
-                        const uint64_t bh = smem_desc_kmajor(st + TC_OFF_SHI + ks * 256, 128, sbo_s);
-                        const uint64_t bl = smem_desc_kmajor(st + TC_OFF_SLO + ks * 256, 128, sbo_s);
-                        mma_f16(dS, ah, bh, idesc, ks > 0);
-                        mma_f16(dS, ah, bl, idesc, true);
-                        mma_f16(dS, al, bh, idesc, true);
+                    const uint32_t dS = tbase + buf * 256, dY = dS + 128;
+#pragma unroll
+                    for (int j = 0; j < NCH; ++j) {
+                        if (ok) ok = mbar_wait_bounded(&full[slot], (uint32_t)((q / NSLOT) & 1), abort_flag);
+                        if (ok) {
+                            tc_fence_after();
+                            const uint64_t bh = b0 + (uint64_t)((slot * TC_CHUNK_BYTES) >> 4);
+                            const uint64_t bl = bh + (uint64_t)(TC_HALF_CHUNK >> 4);
+                            if (j < NCH - 1) {
+                                mma_f16(dS, ah[j], bh, idesc, j > 0);
+                                mma_f16(dS, ah[j], bl, idesc, true);
+                                mma_f16(dS, al[j], bh, idesc, true);
+                            } else {
+                                mma_f16(dY, ah[0], bh, idesc, false);
+                                mma_f16(dY, ah[0], bl, idesc, true);
+                                mma_f16(dY, al[0], bh, idesc, true);
+                            }
+                            mma_commit(&empty[slot]);
+                            q_committed = q;
+                        }
+                        ++q;
+                        if (++slot == NSLOT) slot = 0;
                     }
-                    {
-                        const uint64_t ah = smem_desc_kmajor(phi_hi, 128, sbo_a);
-                        const uint64_t al = smem_desc_kmajor(phi_lo, 128, sbo_a);
-                        const uint64_t bh = smem_desc_kmajor(st + TC_OFF_YHI, 128, sbo_y);
-                        const uint64_t bl = smem_desc_kmajor(st + TC_OFF_YLO, 128, sbo_y);
-                        mma_f16(dY, ah, bh, idesc, false);
-                        mma_f16(dY, ah, bl, idesc, true);
-                        mma_f16(dY, al, bh, idesc, true);
-                    }
-                    mma_commit(&stage_empty[s]);
-                    mma_commit(&acc_full[buf]);
+                    if (ok) mma_commit(&acc_full[buf]);
                 }
             }
             if (!ok) {
@@ -267,8 +289,14 @@ __global__ void __launch_bounds__(NTHREADS, 1) rollout_tc_kernel(const __grid_co
                 *abort_flag = 1;
             }
             // all MMAs issued must complete before the tensor memory is freed
-            if (g > 0 && !mbar_wait_drain(&acc_full[(g - 1) & 1], (uint32_t)(((g - 1) >> 1) & 1)))
+            if (g > 0 && ok && !mbar_wait_drain(&acc_full[(g - 1) & 1], (uint32_t)(((g - 1) >> 1) & 1)))
                 atomicOr(a.err, DEVERR_TIMEOUT_DRAIN);
+            if (!ok && q_committed >= 0) {
+                // on abort the last chunk commit tracks every MMA issued before it
+                const long long r = q_committed;
+                if (!mbar_wait_drain(&empty[r % NSLOT], (uint32_t)((r / NSLOT) & 1)))
+                    atomicOr(a.err, DEVERR_TIMEOUT_DRAIN);
+            }
         }
         __syncwarp();
     } else {
@@ -330,16 +358,16 @@ __global__ void __launch_bounds__(NTHREADS, 1) rollout_tc_kernel(const __grid_co
                     if (!aborted && !mbar_wait_bounded(&const_full[c], (uint32_t)((g >> 2) & 1), abort_flag))
                         aborted = true;
                     aborted = __any_sync(0xffffffffu, aborted);
-                    const float *cs = reinterpret_cast<const float *>(smem + OFF_CONST + c * TC_CONST_BYTES) + h * 32;
+                    const float *cs = reinterpret_cast<const float *>(smem + OFF_CONST + c * TC_CONST_BYTES) + h * HALF;
                     const float *cy = cs + TNF;
                     const float *cv = cs + 2 * TNF;
-                    const uint32_t base = tbase + lane_off + buf * 128 + h * 32;
+                    const uint32_t base = tbase + lane_off + buf * 256 + h * HALF;
 #pragma unroll
-                    for (int ch = 0; ch < 2; ++ch) {
+                    for (int ch = 0; ch < HALF / 16; ++ch) {
                         float sv[16], yv[16];
-                        if (!aborted) tmem_ld16x2_wait(base + 16 * ch, base + 64 + 16 * ch, sv, yv);
-                        if (ch == 1) {
-                            // both halves of the accumulator read: hand the buffer back
+                        if (!aborted) tmem_ld16x2_wait(base + 16 * ch, base + 128 + 16 * ch, sv, yv);
+                        if (ch == HALF / 16 - 1) {
+                            // every column of this half read: hand the buffer back
                             tc_fence_before();
                             __syncwarp();
                             if (lane == 0) mbar_arrive(&acc_empty[buf]);
