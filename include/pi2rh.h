@@ -215,6 +215,61 @@ int pi_rh_advance(pi_ctx *ctx, float *x0, const float *u_out, int T, float *u_no
 int pi_set_timing(pi_ctx *ctx, int enable);
 int pi_stage_times(pi_ctx *ctx, float *ms);
 
+/* ---------------------------------------------------------------------------
+ * Batched form: many independent controllers of uneven size (own model, cost,
+ * K, T, M, seed) updated by ONE persistent rollout launch over a work list of
+ * (controller, rollout block) items, plus one batched cost-to-go launch and one
+ * batched merge launch, captured in a CUDA graph on the first update and
+ * replayed afterwards (Sec. 3.1 update, per controller, as pi_update).
+ * ------------------------------------------------------------------------- */
+typedef struct pi_batch pi_batch;
+
+/* One controller of a batch.  ctx is borrowed (must outlive the batch); the
+ * device buffers x0 [12], u_nominal [T][4], u_out [T][4], costs_out [K] are
+ * fixed for the life of the batch (their contents may change between updates). */
+typedef struct {
+    pi_ctx *ctx;
+    int K;
+    int T;
+    const float *x0;
+    const float *u_nominal;
+    float *u_out;
+    float *costs_out;
+} pi_batch_item;
+
+enum {
+    PI_BATCH_ORDER_AS_GIVEN = 0,       /* items in controller order                     */
+    PI_BATCH_ORDER_LONGEST_FIRST = 1,  /* default: largest per-block work first (LPT)    */
+    PI_BATCH_ORDER_ROUND_ROBIN = 2     /* one block of each controller in turn           */
+};
+
+/* Creates a batch over n items, all of whose contexts live on one device.
+ * precision PI_PRECISION_FP32 uses the FP32 rollout kernel; PI_PRECISION_TC_FP16X3
+ * the tensor-core one (every context must then have been created with it).
+ * Allocates the per-controller scratch (about K*T*20 bytes each) and the
+ * device tables; synchronous.  Errors: INVALID_ARG, UNSUPPORTED, OOM, CUDA. */
+int pi_batch_create(const pi_batch_item *items, int n, int precision, pi_batch **out);
+
+/* Schedule knobs (used by the autotuner): work-list order and the number of
+ * persistent CTAs (0 = one per SM).  Re-captures the graph on the next update. */
+int pi_batch_set_schedule(pi_batch *b, int order, int grid);
+
+/* Stream the batch's work is ordered after (and that waits for it); NULL = legacy default stream. */
+int pi_batch_set_stream(pi_batch *b, void *stream);
+
+/* One update of every controller: lambda [n], sigma_u [n][4] (variances) and
+ * seed [n] are host arrays.  Asynchronous with respect to the host. */
+int pi_batch_update(pi_batch *b, const float *lambda, const float *sigma_u, const uint64_t *seed);
+
+/* Waits for the batch and reports device-side errors of its contexts (as pi_sync). */
+int pi_batch_sync(pi_batch *b);
+
+/* Kernel launches enqueued by the batch (3 per update). */
+uint64_t pi_batch_launch_count(const pi_batch *b);
+
+/* Frees the batch (not its contexts or item buffers).  NULL is accepted. */
+void pi_batch_destroy(pi_batch *b);
+
 /* Synchronizes the context's stream and reports device-side errors raised by
  * earlier work: PI_ERR_TIMEOUT if a bounded wait in a kernel expired (the
  * kernel returned early and its outputs are invalid), PI_ERR_INTERNAL for a

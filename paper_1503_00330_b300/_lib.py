@@ -38,6 +38,11 @@ class OptsC(ctypes.Structure):
                 ("device", ctypes.c_int)]
 
 
+class BatchItemC(ctypes.Structure):
+    _fields_ = [("ctx", _vp), ("K", ctypes.c_int), ("T", ctypes.c_int), ("x0", _vp), ("u_nominal", _vp),
+                ("u_out", _vp), ("costs_out", _vp)]
+
+
 class PiError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__(f"pi2rh error {ERR_NAMES.get(code, code)}: {msg}")
@@ -67,6 +72,13 @@ _SIGS = {
     "pi_set_timing": (ctypes.c_int, [_vp, ctypes.c_int]),
     "pi_stage_times": (ctypes.c_int, [_vp, _fp]),
     "pi_debug_tc_gemm": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _vp]),
+    "pi_batch_create": (ctypes.c_int, [ctypes.POINTER(BatchItemC), ctypes.c_int, ctypes.c_int, ctypes.POINTER(_vp)]),
+    "pi_batch_set_schedule": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
+    "pi_batch_set_stream": (ctypes.c_int, [_vp, _vp]),
+    "pi_batch_update": (ctypes.c_int, [_vp, _fp, _fp, ctypes.POINTER(ctypes.c_uint64)]),
+    "pi_batch_sync": (ctypes.c_int, [_vp]),
+    "pi_batch_launch_count": (ctypes.c_uint64, [_vp]),
+    "pi_batch_destroy": (None, [_vp]),
     "pi_debug_noise": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp]),
     "pi_debug_normals": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp,
                                         _vp]),

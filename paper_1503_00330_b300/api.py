@@ -190,3 +190,75 @@ def debug_normals(seed: int, K: int, T: int, m: int = 0, device: int = 0):
     s = torch.cuda.current_stream(dev).cuda_stream
     check(lib.pi_debug_normals(ctypes.c_uint64(seed), K, T, m, _ptr(ctrl), _ptr(model), ctypes.c_void_p(s)))
     return ctrl, model
+
+
+class Batch:
+    """Many controllers updated by one persistent launch under a CUDA graph.
+
+    Each controller keeps its own device buffers (x0, u_nom, u_out, costs),
+    exposed as lists of tensors; write new x0 / u_nom into them between
+    updates.  All controllers must use the batch's precision form."""
+
+    ORDERS = {"as_given": 0, "longest_first": 1, "round_robin": 2}
+
+    def __init__(self, controllers: list, Ks: list[int], Ts: list[int], precision: str = "fp32",
+                 x0=None, u_nom=None):
+        lib = _lib.load()
+        self._lib = lib
+        n = len(controllers)
+        self.controllers, self.Ks, self.Ts, self.precision = controllers, list(Ks), list(Ts), precision
+        dev = controllers[0].device
+        self.device = dev
+        self.x0 = [(_f32_dev(x0[i], dev) if x0 is not None else torch.zeros(NX, device=dev)).clone() for i in range(n)]
+        self.u_nom = [(_f32_dev(u_nom[i], dev) if u_nom is not None else torch.zeros((Ts[i], NU), device=dev)).clone()
+                      for i in range(n)]
+        self.u_out = [torch.empty((Ts[i], NU), dtype=torch.float32, device=dev) for i in range(n)]
+        self.costs = [torch.empty((Ks[i],), dtype=torch.float32, device=dev) for i in range(n)]
+        items = (_lib.BatchItemC * n)()
+        for i, c in enumerate(controllers):
+            items[i] = _lib.BatchItemC(c.handle, int(Ks[i]), int(Ts[i]), self.x0[i].data_ptr(), self.u_nom[i].data_ptr(),
+                                       self.u_out[i].data_ptr(), self.costs[i].data_ptr())
+        h = ctypes.c_void_p()
+        check(lib.pi_batch_create(items, n, Controller.PRECISIONS[precision], ctypes.byref(h)))
+        self._h = h
+        self._stream = None
+
+    @property
+    def n(self) -> int:
+        return len(self.controllers)
+
+    def rollout_steps(self) -> int:
+        return sum(K * T * c.M for K, T, c in zip(self.Ks, self.Ts, self.controllers))
+
+    def set_schedule(self, order: str = "longest_first", grid: int = 0):
+        check(self._lib.pi_batch_set_schedule(self._h, self.ORDERS[order], int(grid)))
+
+    def update(self, lam, sigma_u, seeds):
+        s = torch.cuda.current_stream(self.device).cuda_stream
+        if s != self._stream:
+            check(self._lib.pi_batch_set_stream(self._h, ctypes.c_void_p(s)))
+            self._stream = s
+        lam = np.ascontiguousarray(np.broadcast_to(np.asarray(lam, np.float32), (self.n,)))
+        su = np.ascontiguousarray(np.broadcast_to(np.asarray(sigma_u, np.float32).reshape(-1, 4), (self.n, 4)))
+        sd = np.ascontiguousarray(np.asarray(seeds, np.uint64).reshape(self.n))
+        check(self._lib.pi_batch_update(self._h, lam.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                        su.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                        sd.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))))
+        return self.u_out, self.costs
+
+    def sync(self):
+        check(self._lib.pi_batch_sync(self._h))
+
+    def launch_count(self) -> int:
+        return int(self._lib.pi_batch_launch_count(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.pi_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -35,7 +35,18 @@ constexpr int RF_SLOTS = 64;
 constexpr int RF_CONSUMER_WARPS = 8;
 constexpr int RF_PAIRS_PER_STAGE = RF_CONSUMER_WARPS;
 
+// Work list of the persistent batched rollout kernels: item = (controller,
+// slot block); CTAs claim items through *counter (zeroed before the launch).
+struct BatchArgs {
+    const RolloutArgs *args;   // [n_ctrl] per-controller arguments (FP32 form)
+    const int2 *items;         // [n_items] (controller, block of RF_SLOTS slots)
+    int n_items;
+    int *counter;
+    int *err;
+};
+
 cudaError_t launch_rollout_fp32(const RolloutArgs &a, cudaStream_t s);
+cudaError_t launch_rollout_fp32_batch(const BatchArgs &b, int grid, cudaStream_t s);
 cudaError_t launch_predict_fp32(const RolloutArgs &a, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
@@ -90,7 +101,15 @@ struct TcArgs {
     int *err;
 };
 
+struct TcBatchArgs {
+    const TcArgs *args;        // [n_ctrl] per-controller arguments (tensor-core form)
+    const int2 *items;         // [n_items] (controller, block of TC_SLOTS slots)
+    int n_items;
+    int *counter;
+};
+
 cudaError_t launch_rollout_tc(const TcArgs &a, cudaStream_t s);
+cudaError_t launch_rollout_tc_batch(const TcBatchArgs &b, int grid, cudaStream_t s);
 cudaError_t launch_predict_tc(const TcArgs &a, cudaStream_t s);
 const char *tc_launch_diag();   // resources of the tensor-core kernel (for error messages)
 
@@ -110,6 +129,22 @@ cudaError_t launch_rh_apply(float *x0, const float *y, float dt, const float *u_
 
 // Staged check of the tensor-core GEMM core: D[128x64] = A[128xK] B[64xK]^T, fp16 in, fp32 out.
 cudaError_t launch_tc_gemm_check(const void *A, const void *B, int K, float *D, int *err, cudaStream_t s);
+
+// Per-controller arguments of the batched reduction kernels.
+struct ReduceArgs {
+    const float *cost_tk;
+    const float *phi;
+    const float4 *eps_tk;
+    int K, T;
+    double dt, inv_lam_log2e;
+    float *costs_out;
+    double *part;
+    const float *u_nom;
+    float *u_out;
+};
+// scan items: (controller, block of RS_KC rollouts); merge items: (controller, first of 8 timesteps)
+cudaError_t launch_scan_lse_batch(const ReduceArgs *args, const int2 *items, int n_items, cudaStream_t s);
+cudaError_t launch_lse_merge_batch(const ReduceArgs *args, const int2 *items, int n_items, cudaStream_t s);
 
 // Staged noise kernels.
 cudaError_t launch_noise_raw(uint64_t seed, int K, int T, int m, uint32_t *raw, cudaStream_t s);

@@ -37,16 +37,14 @@ __device__ __forceinline__ double warp_sum_d(double v)
     return v;
 }
 
-__global__ void __launch_bounds__(NT) scan_lse_kernel(const float *__restrict__ cost_tk,
-                                                      const float *__restrict__ phi,
-                                                      const float4 *__restrict__ eps_tk, int K, int T,
-                                                      double dt, double inv_lam_log2e,
-                                                      float *__restrict__ costs_out,
-                                                      double *__restrict__ part)
+__device__ __forceinline__ void scan_lse_block(const float *__restrict__ cost_tk, const float *__restrict__ phi,
+                                               const float4 *__restrict__ eps_tk, int K, int T, double dt,
+                                               double inv_lam_log2e, float *__restrict__ costs_out,
+                                               double *__restrict__ part, int blk)
 {
     __shared__ double S_s[TC][KC];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int k0 = blockIdx.x * KC;
+    const int k0 = blk * KC;
     const int k = k0 + tid;
     double acc = 0.0;
     if (tid < KC && k < K) acc = (double)phi[k];
@@ -80,7 +78,7 @@ __global__ void __launch_bounds__(NT) scan_lse_kernel(const float *__restrict__ 
             double v2 = warp_sum_d((double)fmaf(wa, ea.z, wb * eb.z));
             double v3 = warp_sum_d((double)fmaf(wa, ea.w, wb * eb.w));
             if (lane == 0) {
-                double *p = part + ((size_t)blockIdx.x * T + i) * 6;
+                double *p = part + ((size_t)blk * T + i) * 6;
                 p[0] = mn;
                 p[1] = z;
                 p[2] = v0;
@@ -93,12 +91,29 @@ __global__ void __launch_bounds__(NT) scan_lse_kernel(const float *__restrict__ 
     }
 }
 
-__global__ void __launch_bounds__(256) lse_merge_kernel(const double *__restrict__ part, int nblk, int T,
-                                                        double inv_lam_log2e,
-                                                        const float *u_nom, float *u_out)
+__global__ void __launch_bounds__(NT) scan_lse_kernel(const float *__restrict__ cost_tk,
+                                                      const float *__restrict__ phi,
+                                                      const float4 *__restrict__ eps_tk, int K, int T,
+                                                      double dt, double inv_lam_log2e,
+                                                      float *__restrict__ costs_out,
+                                                      double *__restrict__ part)
+{
+    scan_lse_block(cost_tk, phi, eps_tk, K, T, dt, inv_lam_log2e, costs_out, part, blockIdx.x);
+}
+
+// Batched: block b handles item items[b] = (controller, rollout block).
+__global__ void __launch_bounds__(NT) scan_lse_batch_kernel(const ReduceArgs *__restrict__ args,
+                                                            const int2 *__restrict__ items)
+{
+    const int2 it = items[blockIdx.x];
+    const ReduceArgs &r = args[it.x];
+    scan_lse_block(r.cost_tk, r.phi, r.eps_tk, r.K, r.T, r.dt, r.inv_lam_log2e, r.costs_out, r.part, it.y);
+}
+
+__device__ __forceinline__ void lse_merge_warp(const double *__restrict__ part, int nblk, int T, double inv_lam_log2e,
+                                               const float *u_nom, float *u_out, int i)
 {
     const int lane = threadIdx.x & 31;
-    const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (i >= T) return;
     double mn = INFINITY;
     for (int c = lane; c < nblk; c += 32) mn = fmin(mn, part[((size_t)c * T + i) * 6]);
@@ -118,6 +133,21 @@ __global__ void __launch_bounds__(256) lse_merge_kernel(const double *__restrict
         const double va = lane == 0 ? v[0] : lane == 1 ? v[1] : lane == 2 ? v[2] : v[3];
         u_out[(size_t)i * 4 + lane] = (float)((double)u_nom[(size_t)i * 4 + lane] + va / z);
     }
+}
+
+__global__ void __launch_bounds__(256) lse_merge_kernel(const double *__restrict__ part, int nblk, int T,
+                                                        double inv_lam_log2e, const float *u_nom, float *u_out)
+{
+    lse_merge_warp(part, nblk, T, inv_lam_log2e, u_nom, u_out, blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5));
+}
+
+// Batched: block b handles 8 timesteps of controller items[b].x starting at items[b].y.
+__global__ void __launch_bounds__(256) lse_merge_batch_kernel(const ReduceArgs *__restrict__ args,
+                                                              const int2 *__restrict__ items)
+{
+    const int2 it = items[blockIdx.x];
+    const ReduceArgs &r = args[it.x];
+    lse_merge_warp(r.part, (r.K + KC - 1) / KC, r.T, r.inv_lam_log2e, r.u_nom, r.u_out, it.y + (threadIdx.x >> 5));
 }
 
 __global__ void noise_raw_kernel(uint64_t seed, int K, int T, int m, uint4 *raw)
@@ -158,6 +188,20 @@ cudaError_t launch_lse_merge(const double *part, int nblk, int T, double inv_lam
                              const float *u_nom, float *u_out, cudaStream_t s)
 {
     lse_merge_kernel<<<(T + 7) / 8, 256, 0, s>>>(part, nblk, T, inv_lam_log2e, u_nom, u_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scan_lse_batch(const ReduceArgs *args, const int2 *items, int n_items, cudaStream_t s)
+{
+    if (n_items <= 0) return cudaErrorInvalidValue;
+    scan_lse_batch_kernel<<<n_items, NT, 0, s>>>(args, items);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lse_merge_batch(const ReduceArgs *args, const int2 *items, int n_items, cudaStream_t s)
+{
+    if (n_items <= 0) return cudaErrorInvalidValue;
+    lse_merge_batch_kernel<<<n_items, 256, 0, s>>>(args, items);
     return cudaGetLastError();
 }
 

@@ -160,59 +160,68 @@ __device__ __forceinline__ void merge_partials(const float *pb, int slot, float 
     var = fmaxf(fmaf(-mean_e, mean_e, s2 * inv), 0.0f) + s3 * inv;
 }
 
-template <bool PREDICT>
-__global__ void __launch_bounds__(NTHREADS, 1) rollout_fp32_kernel(const __grid_constant__ RolloutArgs a)
+// Shared-memory views of one CTA.
+struct Fp32Smem {
+    unsigned char *stage_base;
+    float *part, *zbuf, *xbuf, *ybuf, *vbuf, *yrbuf, *qbuf;
+    float2 *obs_s;
+    uint64_t *full, *empty;
+    volatile int *abort_flag;
+};
+
+__device__ __forceinline__ Fp32Smem fp32_smem(unsigned char *smem)
 {
-    extern __shared__ __align__(128) unsigned char smem[];
-    unsigned char *stage_base = smem + OFF_STAGE;
-    float *part = reinterpret_cast<float *>(smem + OFF_PART);
-    float *zbuf = reinterpret_cast<float *>(smem + OFF_Z);
-    float *xbuf = reinterpret_cast<float *>(smem + OFF_X);
-    float *ybuf = reinterpret_cast<float *>(smem + OFF_Y);
-    float *vbuf = reinterpret_cast<float *>(smem + OFF_V);
-    float *yrbuf = reinterpret_cast<float *>(smem + OFF_YREF);
-    float *qbuf = reinterpret_cast<float *>(smem + OFF_Q);
-    float2 *obs_s = reinterpret_cast<float2 *>(smem + OFF_OBS);
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem + OFF_BAR);
-    uint64_t *empty = full + NSTAGE;
-    volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + OFF_ABORT);
+    Fp32Smem S;
+    S.stage_base = smem + OFF_STAGE;
+    S.part = reinterpret_cast<float *>(smem + OFF_PART);
+    S.zbuf = reinterpret_cast<float *>(smem + OFF_Z);
+    S.xbuf = reinterpret_cast<float *>(smem + OFF_X);
+    S.ybuf = reinterpret_cast<float *>(smem + OFF_Y);
+    S.vbuf = reinterpret_cast<float *>(smem + OFF_V);
+    S.yrbuf = reinterpret_cast<float *>(smem + OFF_YREF);
+    S.qbuf = reinterpret_cast<float *>(smem + OFF_Q);
+    S.obs_s = reinterpret_cast<float2 *>(smem + OFF_OBS);
+    S.full = reinterpret_cast<uint64_t *>(smem + OFF_BAR);
+    S.empty = S.full + NSTAGE;
+    S.abort_flag = reinterpret_cast<volatile int *>(smem + OFF_ABORT);
+    return S;
+}
 
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int P = a.P, spo = a.stages_per_out;
-    const int G = NY * spo;                       // stages per step
-    // Prediction mode runs the field loop twice: the second pass centers the
-    // local predictions on the first pass's mean, so the spread term of the
-    // variance does not cancel.
-    const int nsteps = PREDICT ? 2 : a.T;
-    const long long total = (long long)G * nsteps;
-    const int M = PREDICT ? 1 : a.M;
-
-    if (tid == 0) {
-        for (int s = 0; s < NSTAGE; ++s) {
-            mbar_init(&full[s], 1);
-            mbar_init(&empty[s], CW);
-        }
-        *abort_flag = 0;
-        fence_mbar_init();
+__device__ __forceinline__ void fp32_init_barriers(const Fp32Smem &S)
+{
+    for (int s = 0; s < NSTAGE; ++s) {
+        mbar_init(&S.full[s], 1);
+        mbar_init(&S.empty[s], CW);
     }
-    for (int i = tid; i < a.cost.n_obs; i += NTHREADS) obs_s[i] = a.cost.obs[i];
-    __syncthreads();
+    *S.abort_flag = 0;
+    fence_mbar_init();
+}
 
-    // ------------------------------------------------------------------ producer
-    if (warp == CW) {
-        if (lane != 0) return;
-        long long issued = 0;
-        for (long long g = 0; g < total; ++g) {
+// Producer (one lane): streams the field-pair records of one work item
+// (nsteps passes over the model) through the stage ring.  `g0` is the ring
+// position at the start of the item; returns the position after it, or -1
+// after a timeout (abort flag set).
+template <bool PREDICT>
+__device__ long long fp32_producer(const RolloutArgs &a, const Fp32Smem &S, long long g0, long long &issued)
+{
+    unsigned char *stage_base = S.stage_base;
+    uint64_t *full = S.full, *empty = S.empty;
+    volatile int *abort_flag = S.abort_flag;
+    const int P = a.P, spo = a.stages_per_out;
+    const int G = NY * spo;
+    const int nsteps = PREDICT ? 2 : a.T;
+    const long long total = g0 + (long long)G * nsteps;
+        for (long long g = g0; g < total; ++g) {
             const int slot = (int)(g % NSTAGE);
             if (g >= NSTAGE) {
                 const uint32_t par = (uint32_t)(((g / NSTAGE) - 1) & 1);
                 if (!mbar_wait_bounded(&empty[slot], par, abort_flag)) {
                     if (!*abort_flag) atomicOr(a.err, DEVERR_TIMEOUT_EMPTY);
                     *abort_flag = 1;
-                    break;
+                    return -1;
                 }
             }
-            const int gs = (int)(g % G);
+            const int gs = (int)((g - g0) % G);
             const int o = gs / spo, s = gs % spo;
             const int p0 = s * RF_PAIRS_PER_STAGE;
             const int np = min(RF_PAIRS_PER_STAGE, P - p0);
@@ -222,18 +231,26 @@ __global__ void __launch_bounds__(NTHREADS, 1) rollout_fp32_kernel(const __grid_
             bulk_g2s(stage_base + (size_t)slot * STAGE_BYTES, src, bytes, &full[slot]);
             issued = g + 1;
         }
-        // Keep the CTA alive until every copy issued has landed.
-        for (long long g = (issued > NSTAGE ? issued - NSTAGE : 0); g < issued; ++g) {
-            const int slot = (int)(g % NSTAGE);
-            if (!mbar_wait_drain(&full[slot], (uint32_t)((g / NSTAGE) & 1)))
-                atomicOr(a.err, DEVERR_TIMEOUT_DRAIN);
-        }
-        return;
-    }
+    return total;
+}
 
-    // ------------------------------------------------------------------ consumers
+// Consumers (8 warps): evaluate the LWPR model for the 64 slots of one work
+// item starting at slot_base, step the dynamics and write the item's outputs.
+// `g` is the ring position (advanced in step with the producer).
+template <bool PREDICT>
+__device__ void fp32_consumer(const RolloutArgs &a, const Fp32Smem &S, long long slot_base, long long &g, bool &aborted)
+{
+    unsigned char *stage_base = S.stage_base;
+    float *part = S.part, *zbuf = S.zbuf, *xbuf = S.xbuf, *ybuf = S.ybuf, *vbuf = S.vbuf, *yrbuf = S.yrbuf,
+          *qbuf = S.qbuf;
+    float2 *obs_s = S.obs_s;
+    uint64_t *full = S.full, *empty = S.empty;
+    volatile int *abort_flag = S.abort_flag;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int P = a.P, spo = a.stages_per_out;
+    const int nsteps = PREDICT ? 2 : a.T;
+    const int M = PREDICT ? 1 : a.M;
     const int slotA = lane, slotB = lane + 32;
-    const long long slot_base = (long long)blockIdx.x * SLOTS;
 
     // Step-thread state: thread tid < SLOTS owns slot tid.
     const bool stepper = tid < SLOTS;
@@ -268,8 +285,6 @@ __global__ void __launch_bounds__(NTHREADS, 1) rollout_fp32_kernel(const __grid_
     }
     named_bar_sync(1, NCONS);
 
-    long long g = 0;
-    bool aborted = false;
     for (int t = 0; t < nsteps; ++t) {
         float2 zA[NZ], zB[NZ];
 #pragma unroll
@@ -403,6 +418,69 @@ __global__ void __launch_bounds__(NTHREADS, 1) rollout_fp32_kernel(const __grid_
     }
 }
 
+template <bool PREDICT>
+__global__ void __launch_bounds__(NTHREADS, 1) rollout_fp32_kernel(const __grid_constant__ RolloutArgs a)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    const Fp32Smem S = fp32_smem(smem);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) fp32_init_barriers(S);
+    for (int i = tid; i < a.cost.n_obs; i += NTHREADS) S.obs_s[i] = a.cost.obs[i];
+    __syncthreads();
+    if (warp == CW) {
+        if (lane != 0) return;
+        long long issued = 0;
+        fp32_producer<PREDICT>(a, S, 0, issued);
+        // keep the CTA alive until every copy issued has landed
+        for (long long g = (issued > NSTAGE ? issued - NSTAGE : 0); g < issued; ++g)
+            if (!mbar_wait_drain(&S.full[g % NSTAGE], (uint32_t)((g / NSTAGE) & 1))) atomicOr(a.err, DEVERR_TIMEOUT_DRAIN);
+        return;
+    }
+    long long g = 0;
+    bool aborted = false;
+    fp32_consumer<PREDICT>(a, S, (long long)blockIdx.x * SLOTS, g, aborted);
+}
+
+// Persistent batched form: CTAs take (controller, slot block) work items from
+// an atomic counter until the list is exhausted; every controller has its own
+// RolloutArgs (model, cost, sizes, buffers).  Ring positions carry over
+// between items, so the barriers are initialized once.
+__global__ void __launch_bounds__(NTHREADS, 1) rollout_fp32_batch_kernel(const __grid_constant__ BatchArgs b)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ RolloutArgs s_args;
+    __shared__ int s_item;
+    const Fp32Smem S = fp32_smem(smem);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) fp32_init_barriers(S);
+    long long g = 0, issued = 0;
+    bool aborted = false;
+    for (;;) {
+        if (tid == 0) s_item = atomicAdd(b.counter, 1);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= b.n_items || *S.abort_flag) break;
+        const int2 it = b.items[item];
+        if (tid == 0) s_args = b.args[it.x];
+        __syncthreads();
+        const RolloutArgs &a = s_args;
+        for (int i = tid; i < a.cost.n_obs; i += NTHREADS) S.obs_s[i] = a.cost.obs[i];
+        __syncthreads();
+        if (warp == CW) {
+            if (lane == 0) {
+                const long long next = fp32_producer<false>(a, S, g, issued);
+                g = next < 0 ? g : next;
+            }
+        } else {
+            fp32_consumer<false>(a, S, (long long)it.y * SLOTS, g, aborted);
+        }
+        __syncthreads();
+    }
+    if (warp == CW && lane == 0)
+        for (long long r = (issued > NSTAGE ? issued - NSTAGE : 0); r < issued; ++r)
+            if (!mbar_wait_drain(&S.full[r % NSTAGE], (uint32_t)((r / NSTAGE) & 1))) atomicOr(b.err, DEVERR_TIMEOUT_DRAIN);
+}
+
 bool g_attr_set[2] = {false, false};
 
 template <bool PREDICT>
@@ -432,6 +510,21 @@ cudaError_t launch_rollout_fp32(const RolloutArgs &a, cudaStream_t s)
 cudaError_t launch_predict_fp32(const RolloutArgs &a, cudaStream_t s)
 {
     return launch_impl<true>(a, s, (long long)a.n_pred);
+}
+
+bool g_batch_attr = false;
+
+cudaError_t launch_rollout_fp32_batch(const BatchArgs &b, int grid, cudaStream_t s)
+{
+    if (!g_batch_attr) {
+        cudaError_t e = cudaFuncSetAttribute(rollout_fp32_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             SMEM_BYTES);
+        if (e != cudaSuccess) return e;
+        g_batch_attr = true;
+    }
+    if (grid <= 0) return cudaErrorInvalidValue;
+    rollout_fp32_batch_kernel<<<grid, NTHREADS, SMEM_BYTES, s>>>(b);
+    return cudaGetLastError();
 }
 
 }  // namespace pi2rh

@@ -143,377 +143,514 @@ __device__ __forceinline__ void build_features(unsigned char *smem, int r, const
     }
 }
 
-template <bool PREDICT>
-__global__ void __launch_bounds__(NTHREADS, 1) rollout_tc_kernel(const __grid_constant__ TcArgs a)
+struct TcSmem {
+    unsigned char *base;
+    float *part, *zbuf, *xbuf, *ybuf, *vbuf, *yrbuf, *qbuf;
+    float2 *obs_s;
+    uint64_t *full, *empty, *acc_full, *acc_empty, *const_full, *const_empty, *phi_ready;
+    uint32_t *tslot;
+    volatile int *abort_flag;
+};
+
+__device__ __forceinline__ TcSmem tc_smem(unsigned char *smem)
 {
-    extern __shared__ __align__(1024) unsigned char smem[];
-    float *part = reinterpret_cast<float *>(smem + OFF_PART);
-    float *zbuf = reinterpret_cast<float *>(smem + OFF_Z);
-    float *xbuf = reinterpret_cast<float *>(smem + OFF_X);
-    float *ybuf = reinterpret_cast<float *>(smem + OFF_Y);
-    float *vbuf = reinterpret_cast<float *>(smem + OFF_V);
-    float *yrbuf = reinterpret_cast<float *>(smem + OFF_YREF);
-    float *qbuf = reinterpret_cast<float *>(smem + OFF_Q);
-    float2 *obs_s = reinterpret_cast<float2 *>(smem + OFF_OBS);
+    TcSmem S;
+    S.base = smem;
+    S.part = reinterpret_cast<float *>(smem + OFF_PART);
+    S.zbuf = reinterpret_cast<float *>(smem + OFF_Z);
+    S.xbuf = reinterpret_cast<float *>(smem + OFF_X);
+    S.ybuf = reinterpret_cast<float *>(smem + OFF_Y);
+    S.vbuf = reinterpret_cast<float *>(smem + OFF_V);
+    S.yrbuf = reinterpret_cast<float *>(smem + OFF_YREF);
+    S.qbuf = reinterpret_cast<float *>(smem + OFF_Q);
+    S.obs_s = reinterpret_cast<float2 *>(smem + OFF_OBS);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + OFF_BAR);
-    uint64_t *full = bars, *empty = bars + NSLOT, *acc_full = bars + 2 * NSLOT, *acc_empty = acc_full + 2;
-    uint64_t *const_full = acc_empty + 2, *const_empty = const_full + NCONST, *phi_ready = const_empty + NCONST;
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + OFF_TSLOT);
-    volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + OFF_ABORT);
+    S.full = bars;
+    S.empty = bars + NSLOT;
+    S.acc_full = bars + 2 * NSLOT;
+    S.acc_empty = S.acc_full + 2;
+    S.const_full = S.acc_empty + 2;
+    S.const_empty = S.const_full + NCONST;
+    S.phi_ready = S.const_empty + NCONST;
+    S.tslot = reinterpret_cast<uint32_t *>(smem + OFF_TSLOT);
+    S.abort_flag = reinterpret_cast<volatile int *>(smem + OFF_ABORT);
+    return S;
+}
 
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int ntiles = a.tiles_per_out;
-    const int G = NY * ntiles;                                  // tiles per step
-    const int nsteps = PREDICT ? 2 : a.T;
-    const long long total = (long long)G * nsteps;
-    const int M = PREDICT ? 1 : a.M;
-
+// One-time set-up: TMEM allocation (warp 1) and barrier initialization (thread 0).
+__device__ __forceinline__ void tc_setup(const TcSmem &S)
+{
+    const int tid = threadIdx.x, warp = tid >> 5;
     if (warp == 1) {
-        tmem_alloc(tslot, TMEM_COLS);
+        tmem_alloc(S.tslot, TMEM_COLS);
         tmem_relinquish();
     }
     if (tid == 0) {
         for (int i = 0; i < NSLOT; ++i) {
-            mbar_init(&full[i], 1);
-            mbar_init(&empty[i], 1);
+            mbar_init(&S.full[i], 1);
+            mbar_init(&S.empty[i], 1);
         }
         for (int i = 0; i < 2; ++i) {
-            mbar_init(&acc_full[i], 1);
-            mbar_init(&acc_empty[i], NEPI);
+            mbar_init(&S.acc_full[i], 1);
+            mbar_init(&S.acc_empty[i], NEPI);
         }
         for (int i = 0; i < NCONST; ++i) {
-            mbar_init(&const_full[i], 1);
-            mbar_init(&const_empty[i], NEPI);
+            mbar_init(&S.const_full[i], 1);
+            mbar_init(&S.const_empty[i], NEPI);
         }
-        mbar_init(phi_ready, NEPI);
-        *abort_flag = 0;
+        mbar_init(S.phi_ready, NEPI);
+        *S.abort_flag = 0;
         fence_mbar_init();
     }
-    for (int i = tid; i < a.cost.n_obs; i += NTHREADS) obs_s[i] = a.cost.obs[i];
+}
+
+// Persistent per-role positions in the rings (carried across work items).
+struct TcProducer {
+    long long g = 0, q = 0, issued_tiles = 0;
+    int slot = 0;
+};
+struct TcIssuer {
+    long long g = 0, q = 0, q_committed = -1, ts = 0;
+    int slot = 0;
+};
+
+// Producer (lane 0 of warp 0) for one work item; false after a timeout.
+template <bool PREDICT>
+__device__ bool tc_producer_item(const TcArgs &a, const TcSmem &S, TcProducer &P)
+{
+    unsigned char *smem = S.base;
+    uint64_t *full = S.full, *empty = S.empty, *const_full = S.const_full, *const_empty = S.const_empty;
+    volatile int *abort_flag = S.abort_flag;
+    const int G = NY * a.tiles_per_out;
+    const int nsteps = PREDICT ? 2 : a.T;
+    long long &g = P.g, &q = P.q, &issued_tiles = P.issued_tiles;
+    int &slot = P.slot;
+    bool ok = true;
+    const long long g0 = g, g_end = g + (long long)G * nsteps;
+    for (; g < g_end && ok; ++g) {
+        const int c = (int)(g & 3);
+        if (g >= 4) ok = mbar_wait_bounded(&const_empty[c], (uint32_t)(((g >> 2) - 1) & 1), abort_flag);
+        if (!ok) break;
+        const long long tile = (g - g0) % G;            // (output, tile) in order
+        mbar_arrive_expect_tx(&const_full[c], TC_CONST_BYTES);
+        bulk_g2s(smem + OFF_CONST + c * TC_CONST_BYTES, a.wconst + tile * TC_CONST_BYTES, TC_CONST_BYTES,
+                 &const_full[c]);
+        issued_tiles = g + 1;
+        for (int j = 0; j < NCH; ++j, ++q) {
+            if (q >= NSLOT) {
+                ok = mbar_wait_bounded(&empty[slot], (uint32_t)(((q / NSLOT) - 1) & 1), abort_flag);
+                if (!ok) break;
+            }
+            mbar_arrive_expect_tx(&full[slot], TC_CHUNK_BYTES);
+            bulk_g2s(smem + OFF_RING + slot * TC_CHUNK_BYTES,
+                     a.wtiles + tile * TC_TILE_BYTES + (size_t)j * TC_CHUNK_BYTES, TC_CHUNK_BYTES, &full[slot]);
+            if (++slot == NSLOT) slot = 0;
+        }
+    }
+    return ok;
+}
+
+// MMA issuer (lane 0 of warp 1) for one work item; false after a timeout.
+template <bool PREDICT>
+__device__ bool tc_issuer_item(const TcArgs &a, const TcSmem &S, uint32_t tbase, TcIssuer &I)
+{
+    unsigned char *smem = S.base;
+    uint64_t *full = S.full, *empty = S.empty, *acc_full = S.acc_full, *acc_empty = S.acc_empty;
+    uint64_t *phi_ready = S.phi_ready;
+    volatile int *abort_flag = S.abort_flag;
+    const int G = NY * a.tiles_per_out;
+    const int nsteps = PREDICT ? 2 : a.T;
+    long long &g = I.g, &q = I.q, &q_committed = I.q_committed, &ts = I.ts;
+    int &slot = I.slot;
+    const uint32_t idesc = idesc_f16_f32(BM, TNF);
+    const uint32_t phi_hi = smem_u32(smem + OFF_PHI_HI), phi_lo = smem_u32(smem + OFF_PHI_LO);
+    // descriptors: A = feature tile K step j (rows 2560 B apart), B = a
+    // chunk half (128 rows x 16 K, rows 256 B apart); slot/half offsets
+    // are added to the 14-bit start field (addresses stay < 256 KB).
+    uint64_t ah[KF / 16], al[KF / 16];
+#pragma unroll
+    for (int j = 0; j < KF / 16; ++j) {
+        ah[j] = smem_desc_kmajor(phi_hi + j * 256, 128, 16 * KF);
+        al[j] = smem_desc_kmajor(phi_lo + j * 256, 128, 16 * KF);
+    }
+    const uint64_t b0 = smem_desc_kmajor(smem_u32(smem + OFF_RING), 128, 256);
+    bool ok = true;
+    for (int t = 0; t < nsteps && ok; ++t, ++ts) {
+        ok = mbar_wait_bounded(phi_ready, (uint32_t)(ts & 1), abort_flag);
+        tc_fence_after();
+        for (int jt = 0; jt < G && ok; ++jt, ++g) {
+            const int buf = (int)(g & 1);
+            if (g >= 2) ok = mbar_wait_bounded(&acc_empty[buf], (uint32_t)(((g >> 1) - 1) & 1), abort_flag);
+            if (!ok) break;
+            tc_fence_after();
+            const uint32_t dS = tbase + buf * 256, dY = dS + 128;
+#pragma unroll
+            for (int j = 0; j < NCH; ++j) {
+                if (ok) ok = mbar_wait_bounded(&full[slot], (uint32_t)((q / NSLOT) & 1), abort_flag);
+                if (ok) {
+                    tc_fence_after();
+                    const uint64_t bh = b0 + (uint64_t)((slot * TC_CHUNK_BYTES) >> 4);
+                    const uint64_t bl = bh + (uint64_t)(TC_HALF_CHUNK >> 4);
+                    if (j < NCH - 1) {
+                        mma_f16(dS, ah[j], bh, idesc, j > 0);
+                        mma_f16(dS, ah[j], bl, idesc, true);
+                        mma_f16(dS, al[j], bh, idesc, true);
+                    } else {
+                        mma_f16(dY, ah[0], bh, idesc, false);
+                        mma_f16(dY, ah[0], bl, idesc, true);
+                        mma_f16(dY, al[0], bh, idesc, true);
+                    }
+                    mma_commit(&empty[slot]);
+                    q_committed = q;
+                }
+                ++q;
+                if (++slot == NSLOT) slot = 0;
+            }
+            if (ok) mma_commit(&acc_full[buf]);
+        }
+    }
+    return ok;
+}
+
+// Epilogue warps (2-9) for one work item: the 128 slots starting at slot_base.
+template <bool PREDICT>
+__device__ void tc_epilogue_item(const TcArgs &a, const TcSmem &S, uint32_t tbase, long long slot_base, long long &g,
+                                 bool &aborted)
+{
+    unsigned char *smem = S.base;
+    float *part = S.part, *zbuf = S.zbuf, *xbuf = S.xbuf, *ybuf = S.ybuf, *vbuf = S.vbuf, *yrbuf = S.yrbuf,
+          *qbuf = S.qbuf;
+    float2 *obs_s = S.obs_s;
+    uint64_t *acc_full = S.acc_full, *acc_empty = S.acc_empty, *const_full = S.const_full,
+             *const_empty = S.const_empty, *phi_ready = S.phi_ready;
+    volatile int *abort_flag = S.abort_flag;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    (void)tid;
+    const int ntiles = a.tiles_per_out;
+    const int nsteps = PREDICT ? 2 : a.T;
+    const int M = PREDICT ? 1 : a.M;
+    const int ew = warp - 2;
+    const int q = warp & 3, h = ew >> 2;                 // lane quarter, column half
+    const int r = 32 * q + lane;                         // slot row of this thread
+    const bool owner = h == 0;
+    const long long gslot = slot_base + r;
+    const int k = (int)(gslot / M), m = (int)(gslot % M);
+    const bool writer = owner && !PREDICT && k < a.K && m == 0;
+    const uint32_t lane_off = (uint32_t)(32 * q) << 16;
+
+    // initial feature tile
+    if (owner) {
+        float zext[17];
+        if (PREDICT) {
+            const bool okp = gslot < a.n_pred;
+#pragma unroll
+            for (int c = 0; c < NZ; ++c) zext[c] = okp ? a.z_in[(size_t)gslot * NZ + c] : 0.0f;
+        } else {
+            const float4 n = box_muller4(noise_block(a.seed, (uint32_t)k, 0u, 0u, 0u));
+            const float eps[4] = {a.sqrt_sigma_u[0] * n.x, a.sqrt_sigma_u[1] * n.y, a.sqrt_sigma_u[2] * n.z,
+                                  a.sqrt_sigma_u[3] * n.w};
+#pragma unroll
+            for (int c = 0; c < NX; ++c) {
+                zext[c] = a.x0[c];
+                xbuf[c * BM + r] = zext[c];
+            }
+#pragma unroll
+            for (int c = 0; c < NU; ++c) zext[NX + c] = a.u_nom[c] + eps[c];
+            if (writer) a.eps_tk[k] = make_float4(eps[0], eps[1], eps[2], eps[3]);
+        }
+        zext[16] = 1.0f;
+#pragma unroll
+        for (int c = 0; c < NZ; ++c) zbuf[c * BM + r] = zext[c];
+#pragma unroll
+        for (int o = 0; o < NY; ++o) yrbuf[o * BM + r] = 0.0f;
+        build_features(smem, r, zext);
+    }
+    fence_proxy_async_smem();
+    __syncwarp();
+    if (lane == 0) mbar_arrive(phi_ready);
+    // both column halves read the owners' y_ref (and x) of step 0
+    named_bar_sync(1, NE);
+
+    for (int t = 0; t < nsteps; ++t) {
+        for (int o = 0; o < NY; ++o) {
+            const float yref = yrbuf[o * BM + r];
+            Soft st{-INFINITY, 0.f, 0.f, 0.f, 0.f};
+            for (int j = 0; j < ntiles; ++j, ++g) {
+                const int buf = (int)(g & 1), c = (int)(g & 3);
+                if (!aborted && !mbar_wait_bounded(&acc_full[buf], (uint32_t)((g >> 1) & 1), abort_flag))
+                    aborted = true;
+                aborted = __any_sync(0xffffffffu, aborted);   // the TMEM loads below are warp-collective
+                tc_fence_after();
+                if (!aborted && !mbar_wait_bounded(&const_full[c], (uint32_t)((g >> 2) & 1), abort_flag))
+                    aborted = true;
+                aborted = __any_sync(0xffffffffu, aborted);
+                const float *cs = reinterpret_cast<const float *>(smem + OFF_CONST + c * TC_CONST_BYTES) + h * HALF;
+                const float *cy = cs + TNF;
+                const float *cv = cs + 2 * TNF;
+                const uint32_t base = tbase + lane_off + buf * 256 + h * HALF;
+#pragma unroll
+                for (int ch = 0; ch < HALF / 16; ++ch) {
+                    float sv[16], yv[16];
+                    if (!aborted) tmem_ld16x2_wait(base + 16 * ch, base + 128 + 16 * ch, sv, yv);
+                    if (ch == HALF / 16 - 1) {
+                        // every column of this half read: hand the buffer back
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(&acc_empty[buf]);
+                    }
+                    if (!aborted) {
+                        float sm = -INFINITY;
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) {
+                            sv[i] += cs[16 * ch + i];
+                            sm = fmaxf(sm, sv[i]);
+                        }
+                        const float mn = fmaxf(st.m, sm);
+                        const float mns = mn == -INFINITY ? 0.0f : mn;
+                        const float sc = ex2(st.m - mns);
+                        float s0 = st.s0 * sc, s1 = st.s1 * sc, s2 = st.s2 * sc, s3 = st.s3 * sc;
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) {
+                            const float w = ex2(sv[i] - mns);
+                            const float e = yv[i] + (cy[16 * ch + i] - yref);
+                            const float we = w * e;
+                            s0 += w;
+                            s1 += we;
+                            s2 = fmaf(we, e, s2);
+                            s3 = fmaf(w, cv[16 * ch + i], s3);
+                        }
+                        st = Soft{mn, s0, s1, s2, s3};
+                    }
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&const_empty[c]);
+            }
+            // merge the two column halves of this output
+            float *pb = part + (o & 1) * 5 * BM;
+            if (!owner) {
+                pb[0 * BM + r] = st.m;
+                pb[1 * BM + r] = st.s0;
+                pb[2 * BM + r] = st.s1;
+                pb[3 * BM + r] = st.s2;
+                pb[4 * BM + r] = st.s3;
+            }
+            named_bar_sync(1, NE);
+            if (owner) {
+                const Soft other{pb[0 * BM + r], pb[1 * BM + r], pb[2 * BM + r], pb[3 * BM + r], pb[4 * BM + r]};
+                merge_into(st, other);
+                const float inv = 1.0f / st.s0;
+                const float me = st.s1 * inv;
+                ybuf[o * BM + r] = yref + me;
+                vbuf[o * BM + r] = fmaxf(fmaf(-me, me, st.s2 * inv), 0.0f) + st.s3 * inv;
+            }
+        }
+
+        // ---------------------------------------------------------- dynamics
+        if (owner) {
+            float y[NY], var[NY], zext[17];
+#pragma unroll
+            for (int o = 0; o < NY; ++o) {
+                y[o] = ybuf[o * BM + r];
+                var[o] = vbuf[o * BM + r];
+            }
+            if (PREDICT) {
+                if (t == 0) {
+#pragma unroll
+                    for (int o = 0; o < NY; ++o) yrbuf[o * BM + r] = y[o];
+                } else if (gslot < a.n_pred) {
+#pragma unroll
+                    for (int o = 0; o < NY; ++o) {
+                        a.y_out[(size_t)gslot * NY + o] = y[o];
+                        a.var_out[(size_t)gslot * NY + o] = var[o];
+                    }
+                }
+#pragma unroll
+                for (int c = 0; c < NZ; ++c) zext[c] = zbuf[c * BM + r];
+            } else {
+                float x[NX];
+#pragma unroll
+                for (int c = 0; c < NX; ++c) x[c] = xbuf[c * BM + r];
+                qbuf[r] = running_cost(a.cost, obs_s, x, var);
+                float n[NY];
+                if (a.model_noise) {
+#pragma unroll
+                    for (int b = 0; b < 3; ++b) {
+                        const float4 nb = box_muller4(
+                            noise_block(a.seed, (uint32_t)k, (uint32_t)t, (uint32_t)(b + 1), (uint32_t)m));
+                        n[4 * b] = nb.x;
+                        n[4 * b + 1] = nb.y;
+                        n[4 * b + 2] = nb.z;
+                        n[4 * b + 3] = nb.w;
+                    }
+                } else {
+#pragma unroll
+                    for (int o = 0; o < NY; ++o) n[o] = 0.0f;
+                }
+#pragma unroll
+                for (int c = 0; c < NX; ++c) {
+                    const float xdot = fmaf(sqrtf(var[c]), n[c], y[c]);
+                    x[c] = fmaf(a.dt, xdot, x[c]);
+                    xbuf[c * BM + r] = x[c];
+                    zext[c] = x[c];
+                    yrbuf[c * BM + r] = y[c];
+                }
+                named_bar_sync(2, BM);
+                if (writer) {
+                    float qs = 0.0f;
+                    for (int i = 0; i < M; ++i) qs += qbuf[r + i];
+                    a.cost_tk[(size_t)t * a.K + k] = qs / (float)M;
+                }
+                if (t + 1 < a.T) {
+                    const float4 nn =
+                        box_muller4(noise_block(a.seed, (uint32_t)k, (uint32_t)(t + 1), 0u, 0u));
+                    const float eps[4] = {a.sqrt_sigma_u[0] * nn.x, a.sqrt_sigma_u[1] * nn.y,
+                                          a.sqrt_sigma_u[2] * nn.z, a.sqrt_sigma_u[3] * nn.w};
+#pragma unroll
+                    for (int c = 0; c < NU; ++c) zext[NX + c] = a.u_nom[(size_t)(t + 1) * NU + c] + eps[c];
+                    if (writer)
+                        a.eps_tk[(size_t)(t + 1) * a.K + k] = make_float4(eps[0], eps[1], eps[2], eps[3]);
+                } else {
+#pragma unroll
+                    for (int c = 0; c < NU; ++c) zext[NX + c] = 0.0f;
+                    named_bar_sync(2, BM);
+                    qbuf[r] = terminal_cost(a.cost, x);
+                    named_bar_sync(2, BM);
+                    if (writer) {
+                        float ps = 0.0f;
+                        for (int i = 0; i < M; ++i) ps += qbuf[r + i];
+                        a.phi[k] = ps / (float)M;
+                    }
+                }
+            }
+            zext[16] = 1.0f;
+            if (t + 1 < nsteps) build_features(smem, r, zext);
+        }
+        const bool any_abort = bar_sync_or(3, NE, aborted || *abort_flag != 0);
+        if (any_abort) break;
+        if (t + 1 < nsteps) {
+            fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(phi_ready);
+        }
+    }
+}
+
+__device__ __forceinline__ void tc_drain(const TcArgs &a, const TcSmem &S, const TcProducer &P, const TcIssuer &I,
+                                         bool issuer_ok)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp == 0 && lane == 0) {
+        // keep the CTA alive until every copy issued has landed
+        for (long long r = (P.q > NSLOT ? P.q - NSLOT : 0); r < P.q; ++r)
+            if (!mbar_wait_drain(&S.full[r % NSLOT], (uint32_t)((r / NSLOT) & 1))) atomicOr(a.err, DEVERR_TIMEOUT_DRAIN);
+        for (long long g = (P.issued_tiles > NCONST ? P.issued_tiles - NCONST : 0); g < P.issued_tiles; ++g)
+            if (!mbar_wait_drain(&S.const_full[g & 3], (uint32_t)((g >> 2) & 1))) atomicOr(a.err, DEVERR_TIMEOUT_DRAIN);
+    }
+    if (warp == 1 && lane == 0) {
+        // every MMA issued must complete before the tensor memory is freed
+        if (issuer_ok && I.g > 0 &&
+            !mbar_wait_drain(&S.acc_full[(I.g - 1) & 1], (uint32_t)(((I.g - 1) >> 1) & 1)))
+            atomicOr(a.err, DEVERR_TIMEOUT_DRAIN);
+        if (!issuer_ok && I.q_committed >= 0) {
+            const long long r = I.q_committed;   // the last chunk commit tracks every MMA before it
+            if (!mbar_wait_drain(&S.empty[r % NSLOT], (uint32_t)((r / NSLOT) & 1))) atomicOr(a.err, DEVERR_TIMEOUT_DRAIN);
+        }
+    }
+}
+
+__device__ __forceinline__ void tc_flag_abort(const TcArgs &a, const TcSmem &S, int code)
+{
+    if (!*S.abort_flag) atomicOr(a.err, code);
+    *S.abort_flag = 1;
+}
+
+template <bool PREDICT>
+__global__ void __launch_bounds__(NTHREADS, 1) rollout_tc_kernel(const __grid_constant__ TcArgs a)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const TcSmem S = tc_smem(smem);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    tc_setup(S);
+    for (int i = tid; i < a.cost.n_obs; i += NTHREADS) S.obs_s[i] = a.cost.obs[i];
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    const uint32_t tbase = *tslot;
-
+    const uint32_t tbase = *S.tslot;
+    TcProducer P;
+    TcIssuer I;
+    bool issuer_ok = true;
     if (warp == 0) {
-        // -------------------------------------------------------------- producer
-        if (lane == 0) {
-            long long q = 0, issued_tiles = 0;             // chunks issued, tiles issued
-            int slot = 0;
-            bool ok = true;
-            for (long long g = 0; g < total && ok; ++g) {
-                const int c = (int)(g & 3);
-                if (g >= 4) ok = mbar_wait_bounded(&const_empty[c], (uint32_t)(((g >> 2) - 1) & 1), abort_flag);
-                if (!ok) break;
-                const long long tile = g % G;                   // (output, tile) in order
-                mbar_arrive_expect_tx(&const_full[c], TC_CONST_BYTES);
-                bulk_g2s(smem + OFF_CONST + c * TC_CONST_BYTES, a.wconst + tile * TC_CONST_BYTES, TC_CONST_BYTES,
-                         &const_full[c]);
-                issued_tiles = g + 1;
-                for (int j = 0; j < NCH; ++j, ++q) {
-                    if (q >= NSLOT) {
-                        ok = mbar_wait_bounded(&empty[slot], (uint32_t)(((q / NSLOT) - 1) & 1), abort_flag);
-                        if (!ok) break;
-                    }
-                    mbar_arrive_expect_tx(&full[slot], TC_CHUNK_BYTES);
-                    bulk_g2s(smem + OFF_RING + slot * TC_CHUNK_BYTES,
-                             a.wtiles + tile * TC_TILE_BYTES + (size_t)j * TC_CHUNK_BYTES, TC_CHUNK_BYTES, &full[slot]);
-                    if (++slot == NSLOT) slot = 0;
-                }
-            }
-            if (!ok) {
-                if (!*abort_flag) atomicOr(a.err, DEVERR_TIMEOUT_EMPTY);
-                *abort_flag = 1;
-            }
-            // keep the CTA alive until every copy issued has landed
-            for (long long r = (q > NSLOT ? q - NSLOT : 0); r < q; ++r)
-                if (!mbar_wait_drain(&full[r % NSLOT], (uint32_t)((r / NSLOT) & 1))) atomicOr(a.err, DEVERR_TIMEOUT_DRAIN);
-            for (long long g = (issued_tiles > NCONST ? issued_tiles - NCONST : 0); g < issued_tiles; ++g)
-                if (!mbar_wait_drain(&const_full[g & 3], (uint32_t)((g >> 2) & 1))) atomicOr(a.err, DEVERR_TIMEOUT_DRAIN);
-        }
+        if (lane == 0 && !tc_producer_item<PREDICT>(a, S, P)) tc_flag_abort(a, S, DEVERR_TIMEOUT_EMPTY);
         __syncwarp();
     } else if (warp == 1) {
-        // -------------------------------------------------------------- MMA issuer
         if (lane == 0) {
-            const uint32_t idesc = idesc_f16_f32(BM, TNF);
-            const uint32_t phi_hi = smem_u32(smem + OFF_PHI_HI), phi_lo = smem_u32(smem + OFF_PHI_LO);
-            // descriptors: A = feature tile K step j (rows 2560 B apart), B = a
-            // chunk half (128 rows x 16 K, rows 256 B apart); slot/half offsets
-            // are added to the 14-bit start field (addresses stay < 256 KB).
-            uint64_t ah[KF / 16], al[KF / 16];
-#pragma unroll
-            for (int j = 0; j < KF / 16; ++j) {
-                ah[j] = smem_desc_kmajor(phi_hi + j * 256, 128, 16 * KF);
-                al[j] = smem_desc_kmajor(phi_lo + j * 256, 128, 16 * KF);
-            }
-            const uint64_t b0 = smem_desc_kmajor(smem_u32(smem + OFF_RING), 128, 256);
-            long long g = 0, q = 0, q_committed = -1;
-            int slot = 0;
-            bool ok = true;
-            for (int t = 0; t < nsteps && ok; ++t) {
-                ok = mbar_wait_bounded(phi_ready, (uint32_t)(t & 1), abort_flag);
-                tc_fence_after();
-                for (int jt = 0; jt < G && ok; ++jt, ++g) {
-                    const int buf = (int)(g & 1);
-                    if (g >= 2) ok = mbar_wait_bounded(&acc_empty[buf], (uint32_t)(((g >> 1) - 1) & 1), abort_flag);
-                    if (!ok) break;
-                    tc_fence_after();
-                    const uint32_t dS = tbase + buf * 256, dY = dS + 128;
-#pragma unroll
-                    for (int j = 0; j < NCH; ++j) {
-                        if (ok) ok = mbar_wait_bounded(&full[slot], (uint32_t)((q / NSLOT) & 1), abort_flag);
-                        if (ok) {
-                            tc_fence_after();
-                            const uint64_t bh = b0 + (uint64_t)((slot * TC_CHUNK_BYTES) >> 4);
-                            const uint64_t bl = bh + (uint64_t)(TC_HALF_CHUNK >> 4);
-                            if (j < NCH - 1) {
-                                mma_f16(dS, ah[j], bh, idesc, j > 0);
-                                mma_f16(dS, ah[j], bl, idesc, true);
-                                mma_f16(dS, al[j], bh, idesc, true);
-                            } else {
-                                mma_f16(dY, ah[0], bh, idesc, false);
-                                mma_f16(dY, ah[0], bl, idesc, true);
-                                mma_f16(dY, al[0], bh, idesc, true);
-                            }
-                            mma_commit(&empty[slot]);
-                            q_committed = q;
-                        }
-                        ++q;
-                        if (++slot == NSLOT) slot = 0;
-                    }
-                    if (ok) mma_commit(&acc_full[buf]);
-                }
-            }
-            if (!ok) {
-                if (!*abort_flag) atomicOr(a.err, DEVERR_TIMEOUT_FULL);
-                *abort_flag = 1;
-            }
-            // all MMAs issued must complete before the tensor memory is freed
-            if (g > 0 && ok && !mbar_wait_drain(&acc_full[(g - 1) & 1], (uint32_t)(((g - 1) >> 1) & 1)))
-                atomicOr(a.err, DEVERR_TIMEOUT_DRAIN);
-            if (!ok && q_committed >= 0) {
-                // on abort the last chunk commit tracks every MMA issued before it
-                const long long r = q_committed;
-                if (!mbar_wait_drain(&empty[r % NSLOT], (uint32_t)((r / NSLOT) & 1)))
-                    atomicOr(a.err, DEVERR_TIMEOUT_DRAIN);
-            }
+            issuer_ok = tc_issuer_item<PREDICT>(a, S, tbase, I);
+            if (!issuer_ok) tc_flag_abort(a, S, DEVERR_TIMEOUT_FULL);
         }
         __syncwarp();
     } else {
-        // -------------------------------------------------------------- epilogue
-        const int ew = warp - 2;
-        const int q = warp & 3, h = ew >> 2;                 // lane quarter, column half
-        const int r = 32 * q + lane;                         // slot row of this thread
-        const bool owner = h == 0;
-        const long long gslot = (long long)blockIdx.x * BM + r;
-        const int k = (int)(gslot / M), m = (int)(gslot % M);
-        const bool writer = owner && !PREDICT && k < a.K && m == 0;
-        const uint32_t lane_off = (uint32_t)(32 * q) << 16;
-
-        // initial feature tile
-        if (owner) {
-            float zext[17];
-            if (PREDICT) {
-                const bool okp = gslot < a.n_pred;
-#pragma unroll
-                for (int c = 0; c < NZ; ++c) zext[c] = okp ? a.z_in[(size_t)gslot * NZ + c] : 0.0f;
-            } else {
-                const float4 n = box_muller4(noise_block(a.seed, (uint32_t)k, 0u, 0u, 0u));
-                const float eps[4] = {a.sqrt_sigma_u[0] * n.x, a.sqrt_sigma_u[1] * n.y, a.sqrt_sigma_u[2] * n.z,
-                                      a.sqrt_sigma_u[3] * n.w};
-#pragma unroll
-                for (int c = 0; c < NX; ++c) {
-                    zext[c] = a.x0[c];
-                    xbuf[c * BM + r] = zext[c];
-                }
-#pragma unroll
-                for (int c = 0; c < NU; ++c) zext[NX + c] = a.u_nom[c] + eps[c];
-                if (writer) a.eps_tk[k] = make_float4(eps[0], eps[1], eps[2], eps[3]);
-            }
-            zext[16] = 1.0f;
-#pragma unroll
-            for (int c = 0; c < NZ; ++c) zbuf[c * BM + r] = zext[c];
-#pragma unroll
-            for (int o = 0; o < NY; ++o) yrbuf[o * BM + r] = 0.0f;
-            build_features(smem, r, zext);
-        }
-        fence_proxy_async_smem();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(phi_ready);
-        // both column halves read the owners' y_ref (and x) of step 0
-        named_bar_sync(1, NE);
-
         long long g = 0;
         bool aborted = false;
-        for (int t = 0; t < nsteps; ++t) {
-            for (int o = 0; o < NY; ++o) {
-                const float yref = yrbuf[o * BM + r];
-                Soft st{-INFINITY, 0.f, 0.f, 0.f, 0.f};
-                for (int j = 0; j < ntiles; ++j, ++g) {
-                    const int buf = (int)(g & 1), c = (int)(g & 3);
-                    if (!aborted && !mbar_wait_bounded(&acc_full[buf], (uint32_t)((g >> 1) & 1), abort_flag))
-                        aborted = true;
-                    aborted = __any_sync(0xffffffffu, aborted);   // the TMEM loads below are warp-collective
-                    tc_fence_after();
-                    if (!aborted && !mbar_wait_bounded(&const_full[c], (uint32_t)((g >> 2) & 1), abort_flag))
-                        aborted = true;
-                    aborted = __any_sync(0xffffffffu, aborted);
-                    const float *cs = reinterpret_cast<const float *>(smem + OFF_CONST + c * TC_CONST_BYTES) + h * HALF;
-                    const float *cy = cs + TNF;
-                    const float *cv = cs + 2 * TNF;
-                    const uint32_t base = tbase + lane_off + buf * 256 + h * HALF;
-#pragma unroll
-                    for (int ch = 0; ch < HALF / 16; ++ch) {
-                        float sv[16], yv[16];
-                        if (!aborted) tmem_ld16x2_wait(base + 16 * ch, base + 128 + 16 * ch, sv, yv);
-                        if (ch == HALF / 16 - 1) {
-                            // every column of this half read: hand the buffer back
-                            tc_fence_before();
-                            __syncwarp();
-                            if (lane == 0) mbar_arrive(&acc_empty[buf]);
-                        }
-                        if (!aborted) {
-                            float sm = -INFINITY;
-#pragma unroll
-                            for (int i = 0; i < 16; ++i) {
-                                sv[i] += cs[16 * ch + i];
-                                sm = fmaxf(sm, sv[i]);
-                            }
-                            const float mn = fmaxf(st.m, sm);
-                            const float mns = mn == -INFINITY ? 0.0f : mn;
-                            const float sc = ex2(st.m - mns);
-                            float s0 = st.s0 * sc, s1 = st.s1 * sc, s2 = st.s2 * sc, s3 = st.s3 * sc;
-#pragma unroll
-                            for (int i = 0; i < 16; ++i) {
-                                const float w = ex2(sv[i] - mns);
-                                const float e = yv[i] + (cy[16 * ch + i] - yref);
-                                const float we = w * e;
-                                s0 += w;
-                                s1 += we;
-                                s2 = fmaf(we, e, s2);
-                                s3 = fmaf(w, cv[16 * ch + i], s3);
-                            }
-                            st = Soft{mn, s0, s1, s2, s3};
-                        }
-                    }
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(&const_empty[c]);
-                }
-                // merge the two column halves of this output
-                float *pb = part + (o & 1) * 5 * BM;
-                if (!owner) {
-                    pb[0 * BM + r] = st.m;
-                    pb[1 * BM + r] = st.s0;
-                    pb[2 * BM + r] = st.s1;
-                    pb[3 * BM + r] = st.s2;
-                    pb[4 * BM + r] = st.s3;
-                }
-                named_bar_sync(1, NE);
-                if (owner) {
-                    const Soft other{pb[0 * BM + r], pb[1 * BM + r], pb[2 * BM + r], pb[3 * BM + r], pb[4 * BM + r]};
-                    merge_into(st, other);
-                    const float inv = 1.0f / st.s0;
-                    const float me = st.s1 * inv;
-                    ybuf[o * BM + r] = yref + me;
-                    vbuf[o * BM + r] = fmaxf(fmaf(-me, me, st.s2 * inv), 0.0f) + st.s3 * inv;
-                }
-            }
-
-            // ---------------------------------------------------------- dynamics
-            if (owner) {
-                float y[NY], var[NY], zext[17];
-#pragma unroll
-                for (int o = 0; o < NY; ++o) {
-                    y[o] = ybuf[o * BM + r];
-                    var[o] = vbuf[o * BM + r];
-                }
-                if (PREDICT) {
-                    if (t == 0) {
-#pragma unroll
-                        for (int o = 0; o < NY; ++o) yrbuf[o * BM + r] = y[o];
-                    } else if (gslot < a.n_pred) {
-#pragma unroll
-                        for (int o = 0; o < NY; ++o) {
-                            a.y_out[(size_t)gslot * NY + o] = y[o];
-                            a.var_out[(size_t)gslot * NY + o] = var[o];
-                        }
-                    }
-#pragma unroll
-                    for (int c = 0; c < NZ; ++c) zext[c] = zbuf[c * BM + r];
-                } else {
-                    float x[NX];
-#pragma unroll
-                    for (int c = 0; c < NX; ++c) x[c] = xbuf[c * BM + r];
-                    qbuf[r] = running_cost(a.cost, obs_s, x, var);
-                    float n[NY];
-                    if (a.model_noise) {
-#pragma unroll
-                        for (int b = 0; b < 3; ++b) {
-                            const float4 nb = box_muller4(
-                                noise_block(a.seed, (uint32_t)k, (uint32_t)t, (uint32_t)(b + 1), (uint32_t)m));
-                            n[4 * b] = nb.x;
-                            n[4 * b + 1] = nb.y;
-                            n[4 * b + 2] = nb.z;
-                            n[4 * b + 3] = nb.w;
-                        }
-                    } else {
-#pragma unroll
-                        for (int o = 0; o < NY; ++o) n[o] = 0.0f;
-                    }
-#pragma unroll
-                    for (int c = 0; c < NX; ++c) {
-                        const float xdot = fmaf(sqrtf(var[c]), n[c], y[c]);
-                        x[c] = fmaf(a.dt, xdot, x[c]);
-                        xbuf[c * BM + r] = x[c];
-                        zext[c] = x[c];
-                        yrbuf[c * BM + r] = y[c];
-                    }
-                    named_bar_sync(2, BM);
-                    if (writer) {
-                        float qs = 0.0f;
-                        for (int i = 0; i < M; ++i) qs += qbuf[r + i];
-                        a.cost_tk[(size_t)t * a.K + k] = qs / (float)M;
-                    }
-                    if (t + 1 < a.T) {
-                        const float4 nn =
-                            box_muller4(noise_block(a.seed, (uint32_t)k, (uint32_t)(t + 1), 0u, 0u));
-                        const float eps[4] = {a.sqrt_sigma_u[0] * nn.x, a.sqrt_sigma_u[1] * nn.y,
-                                              a.sqrt_sigma_u[2] * nn.z, a.sqrt_sigma_u[3] * nn.w};
-#pragma unroll
-                        for (int c = 0; c < NU; ++c) zext[NX + c] = a.u_nom[(size_t)(t + 1) * NU + c] + eps[c];
-                        if (writer)
-                            a.eps_tk[(size_t)(t + 1) * a.K + k] = make_float4(eps[0], eps[1], eps[2], eps[3]);
-                    } else {
-#pragma unroll
-                        for (int c = 0; c < NU; ++c) zext[NX + c] = 0.0f;
-                        named_bar_sync(2, BM);
-                        qbuf[r] = terminal_cost(a.cost, x);
-                        named_bar_sync(2, BM);
-                        if (writer) {
-                            float ps = 0.0f;
-                            for (int i = 0; i < M; ++i) ps += qbuf[r + i];
-                            a.phi[k] = ps / (float)M;
-                        }
-                    }
-                }
-                zext[16] = 1.0f;
-                if (t + 1 < nsteps) build_features(smem, r, zext);
-            }
-            const bool any_abort = bar_sync_or(3, NE, aborted || *abort_flag != 0);
-            if (any_abort) break;
-            if (t + 1 < nsteps) {
-                fence_proxy_async_smem();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(phi_ready);
-            }
-        }
-        if (aborted || *abort_flag) {
-            if (lane == 0 && !*abort_flag) atomicOr(a.err, DEVERR_TIMEOUT_FULL);
-            *abort_flag = 1;
-        }
+        tc_epilogue_item<PREDICT>(a, S, tbase, (long long)blockIdx.x * BM, g, aborted);
+        if (aborted) tc_flag_abort(a, S, DEVERR_TIMEOUT_FULL);
     }
-
+    tc_drain(a, S, P, I, issuer_ok);
     // all roles done: free the tensor memory
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tbase, TMEM_COLS);
+    }
+}
+
+// Persistent batched form (see rollout_fp32_batch_kernel): CTAs claim
+// (controller, 128-slot block) items; every ring position and the TMEM
+// allocation carry over between items.
+__global__ void __launch_bounds__(NTHREADS, 1) rollout_tc_batch_kernel(const __grid_constant__ TcBatchArgs b)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ TcArgs s_args;
+    __shared__ int s_item;
+    const TcSmem S = tc_smem(smem);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    tc_setup(S);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = *S.tslot;
+    TcProducer P;
+    TcIssuer I;
+    bool issuer_ok = true;
+    long long g = 0;
+    bool aborted = false;
+    for (;;) {
+        if (tid == 0) s_item = atomicAdd(b.counter, 1);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= b.n_items || *S.abort_flag) break;
+        const int2 it = b.items[item];
+        if (tid == 0) s_args = b.args[it.x];
+        __syncthreads();
+        const TcArgs &a = s_args;
+        for (int i = tid; i < a.cost.n_obs; i += NTHREADS) S.obs_s[i] = a.cost.obs[i];
+        __syncthreads();
+        if (warp == 0) {
+            if (lane == 0 && !tc_producer_item<false>(a, S, P)) tc_flag_abort(a, S, DEVERR_TIMEOUT_EMPTY);
+            __syncwarp();
+        } else if (warp == 1) {
+            if (lane == 0 && issuer_ok) {
+                issuer_ok = tc_issuer_item<false>(a, S, tbase, I);
+                if (!issuer_ok) tc_flag_abort(a, S, DEVERR_TIMEOUT_FULL);
+            }
+            __syncwarp();
+        } else {
+            tc_epilogue_item<false>(a, S, tbase, (long long)it.y * BM, g, aborted);
+            if (aborted) tc_flag_abort(a, S, DEVERR_TIMEOUT_FULL);
+        }
+        __syncthreads();
+    }
+    tc_drain(b.args[0], S, P, I, issuer_ok);
     tc_fence_before();
     __syncthreads();
     if (warp == 1) {
@@ -562,6 +699,21 @@ cudaError_t launch_rollout_tc(const TcArgs &a, cudaStream_t s)
 cudaError_t launch_predict_tc(const TcArgs &a, cudaStream_t s)
 {
     return launch_tc_impl<true>(a, s, (long long)a.n_pred);
+}
+
+bool g_tc_batch_attr = false;
+
+cudaError_t launch_rollout_tc_batch(const TcBatchArgs &b, int grid, cudaStream_t s)
+{
+    if (!g_tc_batch_attr) {
+        cudaError_t e = cudaFuncSetAttribute(rollout_tc_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             SMEM_BYTES);
+        if (e != cudaSuccess) return e;
+        g_tc_batch_attr = true;
+    }
+    if (grid <= 0) return cudaErrorInvalidValue;
+    rollout_tc_batch_kernel<<<grid, NTHREADS, SMEM_BYTES, s>>>(b);
+    return cudaGetLastError();
 }
 
 }  // namespace pi2rh
