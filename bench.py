@@ -275,6 +275,79 @@ def time_form(precision, p, args, dev):
             "roofline": roof}
 
 
+def run_batched(args):
+    """64 independent controllers (K ~ logU[1024, 32768], T ~ U{30..150},
+    L ~ logU[128, 2048], own model/obstacles/seed each) updated by one
+    persistent launch under a CUDA graph; both forms timed."""
+    import torch
+    from paper_1503_00330_b300 import build
+    from paper_1503_00330_b300 import workloads as W
+    from paper_1503_00330_b300.api import Batch, Controller
+    build.build()
+    dev = torch.device("cuda", 0)
+    probs = W.batched(64, seed=0)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    forms = {}
+    order = [args.precision] + ([] if args.no_compare else [f for f in ("fp32", "tc") if f != args.precision])
+    for form in order:
+        ctls = [Controller(p.model, p.cost, M=p.M, model_noise=p.model_noise, precision=form) for p in probs]
+        batch = Batch(ctls, [p.K for p in probs], [p.T for p in probs], precision=form,
+                      x0=[p.x0 for p in probs], u_nom=[p.u_nom for p in probs])
+        lam = [p.lam for p in probs]
+        su = [p.sigma_u for p in probs]
+        for i in range(args.warmup):
+            batch.update(lam, su, [p.seed + i for p in probs])
+        batch.sync()
+        ms = []
+        launches0 = batch.launch_count()
+        with ClockSampler(0) as clocks:
+            for i in range(args.steps):
+                flush.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                batch.update(lam, su, [p.seed + args.warmup + i for p in probs])
+                b.record(stream)
+                b.synchronize()
+                ms.append(a.elapsed_time(b))
+        batch.sync()
+        rs = batch.rollout_steps()
+        useful = sum(p.K * p.T * p.M * 12 * p.model.L for p in probs) * FLOPS_PER_FIELD
+        entry = {"value": rs * args.steps / (sum(ms) / 1e3), "ms_per_update": statistics.mean(ms),
+                 "gpu_launches": batch.launch_count() - launches0, "clocks": clocks.summary()}
+        if form == "fp32":
+            peak = torch.cuda.get_device_properties(dev).multi_processor_count * FP32_LANES_PER_SM * 2 * \
+                float(measured_peaks().get("sm_max_mhz", 2032.0)) * 1e6 / 1e12
+            ach = useful / (statistics.mean(ms) / 1e3) / 1e12
+            entry["roofline"] = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                                 "kernel": "rollout_fp32_batch_kernel (time of the whole batched update)"}
+        else:
+            issued = sum(p.K * p.T * p.M * 12 * (-(-p.model.L // TC_FIELDS_PER_TILE) * TC_FIELDS_PER_TILE)
+                         for p in probs) * TC_MMA_FLOPS_PER_FIELD
+            peak = float(measured_peaks().get("bf16_tflops_sustained", 1366.3))
+            ach = issued / (statistics.mean(ms) / 1e3) / 1e12
+            entry["roofline"] = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                                 "frac": ach / peak, "useful_tflops": useful / (statistics.mean(ms) / 1e3) / 1e12,
+                                 "kernel": "rollout_tc_batch_kernel (time of the whole batched update)"}
+        forms[form] = entry
+        batch.close()
+        for c in ctls:
+            c.close()
+    main = forms[args.precision]
+    rs_total = sum(p.K * p.T * p.M for p in probs)
+    line = {"metric": METRIC, "value": main["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": main["ms_per_update"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded generator)",
+            "config": {"workload": "batched: 64 controllers, K ~ logU[1024, 32768], T ~ U{30..150}, "
+                                   "L ~ logU[128, 2048], one persistent launch under a CUDA graph",
+                       "controllers": len(probs), "rollout_steps_per_update": rs_total,
+                       "precision": args.precision, "schedule": "longest_first",
+                       "l2": "flushed between timed steps (256 MiB write outside the event window)"},
+            "gpu_launches": main["gpu_launches"], "roofline": main["roofline"], "forms": forms,
+            "clocks": main["clocks"]}
+    print(json.dumps(line), flush=True)
+
+
 def run_ours(args):
     import torch
     from paper_1503_00330_b300 import build
@@ -384,7 +457,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["realtime", "realtime_short", "small", "precision", "precision_short"], default="realtime")
+    ap.add_argument("--workload", choices=["realtime", "realtime_short", "small", "precision", "precision_short", "batched"], default="realtime")
     ap.add_argument("--cpu-sample", type=int, default=256, help="rollouts in the CPU-baseline sample")
     ap.add_argument("--ref-sample", type=int, default=64, help="rollouts per reference-arm step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -396,6 +469,8 @@ def main():
         raise SystemExit("--warmup must be >= 3")
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batched":
+        run_batched(args)
     else:
         run_ours(args)
 
