@@ -348,6 +348,91 @@ def run_batched(args):
     print(json.dumps(line), flush=True)
 
 
+def run_serving(args):
+    """256 simulated quadrotors over one shared LWPR model (L = 1024 fields per
+    output): each issues update requests as a Poisson process at 50 Hz with
+    K ~ U{2048..16384}, T ~ U{50..120}; the continuous-batching server admits
+    them by free lanes and pool memory.  A quadrotor whose previous plan has not
+    come back skips its tick (the arrival is dropped).  Timed twice: at the
+    offered 50 Hz (far above what one GPU serves at these sizes, so the server
+    runs saturated) and at half the capacity measured in that run, where the
+    latency is that of a loaded but stable server."""
+    import numpy as np
+    import torch
+    from paper_1503_00330_b300 import build
+    from paper_1503_00330_b300 import workloads as W
+    from paper_1503_00330_b300.api import Controller, Server
+    build.build()
+    n_quad, L, lam = 256, 1024, 1.0
+    model = W.make_lwpr(L, seed=4)
+    cost = W.make_cost(16, seed=4)
+    ctl = Controller(model, cost, precision=args.precision)
+    srv = Server(ctl, n_quad, K_max=16384, T_max=120, max_inflight=args.serve_lanes, max_group=args.serve_group)
+    rng = np.random.default_rng(5)
+    for a in range(n_quad):
+        srv.set_agent(a, rng.normal(0, 0.1, 12).astype(np.float32), None, seed=1000 + a)
+    for i in range(args.warmup):                      # warm-up requests (one per agent 0..W-1)
+        srv.submit(i, 4096, 100, lam, W.SIGMA_U, keep=False)
+    srv.drain()
+    srv.poll(1 << 16)
+    L_pad = -(-L // TC_FIELDS_PER_TILE) * TC_FIELDS_PER_TILE
+
+    def run(rate_hz, seconds, seed):
+        trace = W.serving_requests(n_quad, rate_hz, seconds, seed=seed)
+        st0 = srv.stats()
+        with ClockSampler(0) as clocks:
+            rec, dropped = srv.replay(trace, lam, W.SIGMA_U)
+        st1 = srv.stats()
+        t0 = int(rec["t_submit_ns"].min()) - int(trace[0][0] * 1e9)
+        span = (int(rec["t_result_ns"].max()) - t0) / 1e9
+        steps = float(np.sum(rec["K"].astype(np.float64) * rec["T"]))
+        lat = (rec["t_result_ns"] - rec["t_submit_ns"]) / 1e6
+        queue = (rec["t_launch_ns"] - rec["t_submit_ns"]) / 1e6
+        useful = steps * 12 * L * FLOPS_PER_FIELD
+        if args.precision == "tc":
+            issued = steps * 12 * L_pad * TC_MMA_FLOPS_PER_FIELD
+            peak = float(measured_peaks().get("bf16_tflops_sustained", 1366.3))
+            roof = {"bound": "tensor", "achieved": issued / span / 1e12, "peak": peak, "unit": "TFLOP/s",
+                    "frac": issued / span / 1e12 / peak, "useful_tflops": useful / span / 1e12,
+                    "kernel": "rollout_tc_batch_kernel (issued MMA flops over the whole serving span)"}
+        else:
+            peak = torch.cuda.get_device_properties(0).multi_processor_count * FP32_LANES_PER_SM * 2 * \
+                float(measured_peaks().get("sm_max_mhz", 2032.0)) * 1e6 / 1e12
+            roof = {"bound": "alu", "achieved": useful / span / 1e12, "peak": peak, "unit": "TFLOP/s",
+                    "frac": useful / span / 1e12 / peak,
+                    "kernel": "rollout_fp32_batch_kernel (useful flops over the whole serving span)"}
+        return {"offered_hz_per_quad": rate_hz, "trace_s": seconds, "arrivals": len(trace), "served": int(len(rec)),
+                "dropped": dropped, "span_s": span, "rollout_steps_per_s": steps / span,
+                "requests_per_s": len(rec) / span,
+                "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                               "mean": float(lat.mean()), "max": float(lat.max())},
+                "queue_ms": {"p50": float(np.percentile(queue, 50)), "p99": float(np.percentile(queue, 99))},
+                "group_size": {"mean": float(rec["group_size"].mean()), "max": int(rec["group_size"].max())},
+                "gpu_launches": int(st1["launches"] - st0["launches"]), "groups": int(st1["groups"] - st0["groups"]),
+                "pool_peak_bytes": int(st1["pool_peak_bytes"]), "roofline": roof, "clocks": clocks.summary(),
+                "all_ok": bool(np.all(rec["status"] == 0))}
+
+    full = run(50.0, args.serve_seconds, seed=1)
+    half_rate = 0.5 * full["requests_per_s"] / n_quad
+    half = run(half_rate, max(args.serve_seconds, 160.0 / (0.5 * full["requests_per_s"])), seed=2)
+    srv.close()
+    line = {"metric": METRIC, "value": full["rollout_steps_per_s"], "unit": UNIT, "n_gpus": 1,
+            "steps": full["served"], "warmup": args.warmup, "ms_per_step": 1e3 / full["requests_per_s"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded generator; quadrotor-shaped LWPR model, Poisson request trace)",
+            "config": {"workload": "serving: 256 quadrotors, Poisson 50 Hz each, K ~ U{2048..16384}, "
+                                   "T ~ U{50..120}, shared LWPR model L=1024, continuous batching",
+                       "precision": args.precision, "lanes": args.serve_lanes, "max_group": args.serve_group,
+                       "step": "one served request (ms_per_step = 1 / served request rate)",
+                       "l2": "inputs of a saturated group exceed L2 (each request's scratch ~K*T*20 bytes)"},
+            "e2e": {"value": full["rollout_steps_per_s"], "unit": UNIT,
+                    "note": "requests enter on the host and plans return to pinned host memory inside the span"},
+            "gpu_launches": full["gpu_launches"], "roofline": full["roofline"],
+            "latency_ms": full["latency_ms"], "at_offered_rate": full, "at_half_capacity": half,
+            "clocks": full["clocks"]}
+    print(json.dumps(line), flush=True)
+
+
 def run_ours(args):
     import torch
     from paper_1503_00330_b300 import build
@@ -457,13 +542,17 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["realtime", "realtime_short", "small", "precision", "precision_short", "batched"], default="realtime")
+    ap.add_argument("--workload", choices=["realtime", "realtime_short", "small", "precision", "precision_short", "batched",
+                                                   "serving"], default="realtime")
     ap.add_argument("--cpu-sample", type=int, default=256, help="rollouts in the CPU-baseline sample")
     ap.add_argument("--ref-sample", type=int, default=64, help="rollouts per reference-arm step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", choices=["fp32", "tc"], default="fp32",
                     help="form of the headline line (the other form is timed too and reported under 'forms')")
     ap.add_argument("--no-compare", action="store_true", help="skip timing the other form")
+    ap.add_argument("--serve-seconds", type=float, default=3.0, help="serving: trace length at the offered rate")
+    ap.add_argument("--serve-lanes", type=int, default=2, help="serving: groups on the GPU at once")
+    ap.add_argument("--serve-group", type=int, default=64, help="serving: most requests per group")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
@@ -471,6 +560,8 @@ def main():
         run_reference(args)
     elif args.workload == "batched":
         run_batched(args)
+    elif args.workload == "serving":
+        run_serving(args)
     else:
         run_ours(args)
 

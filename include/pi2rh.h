@@ -60,7 +60,8 @@ enum {
     PI_ERR_CUDA = 3,        /* a CUDA runtime call or kernel launch failed         */
     PI_ERR_TIMEOUT = 4,     /* a bounded device-side wait expired (see pi_sync)    */
     PI_ERR_INTERNAL = 5,    /* a device-side consistency check failed              */
-    PI_ERR_UNSUPPORTED = 6  /* option not available in this build                  */
+    PI_ERR_UNSUPPORTED = 6, /* option not available in this build                  */
+    PI_ERR_BUSY = 7         /* the object has work in flight that the call needs finished */
 };
 
 /* PI_PRECISION_FP32: receptive fields evaluated on the FP32 FMA pipe.
@@ -269,6 +270,145 @@ uint64_t pi_batch_launch_count(const pi_batch *b);
 
 /* Frees the batch (not its contexts or item buffers).  NULL is accepted. */
 void pi_batch_destroy(pi_batch *b);
+
+/* ---------------------------------------------------------------------------
+ * Serving form: a receding-horizon request loop for many simulated vehicles
+ * that share one LWPR model and cost (one pi_ctx).  Each request is one
+ * control update of one vehicle ("agent") followed, on the device, by the
+ * receding-horizon advance of that agent (Sec. 3.1, PI^2-RH: execute the
+ * first control of the plan on the simulated plant -- one Euler step of the
+ * LWPR mean at [x0, u_out_0] -- and warm-start the next plan with the shifted
+ * remainder, the last control held).  The paper runs one controller; serving
+ * many of them is an engineering extension with no counterpart there.
+ *
+ * Per-agent state stays in device memory for the life of the server: the
+ * state x0 [12], the warm-start plan [T_max][4] and an update counter.  The
+ * noise seed of an agent's n-th update is agent_seed + n * 0x9E3779B97F4A7C15
+ * (mod 2^64), formed on the device from that counter.
+ *
+ * A native scheduler thread admits queued requests in arrival order when a
+ * launch lane (a CUDA stream) is free and the request's scratch (about
+ * K*T*20 bytes) fits in the server's HBM pool; the requests admitted together
+ * form one group, updated by one persistent batched rollout launch plus the
+ * batched cost-to-go, merge and advance launches.  Groups on different lanes
+ * overlap on the device.  An agent has at most one request on the GPU; later
+ * requests of a busy agent wait in the queue without holding back others.
+ * Every result equals, bitwise, the result of the same update run alone
+ * (pi_update followed by pi_rh_advance with the same seed).
+ * ------------------------------------------------------------------------- */
+typedef struct pi_server pi_server;
+
+typedef struct {
+    int n_agents;       /* simulated vehicles (device-resident state slots), >= 1          */
+    int K_max;          /* largest K a request may ask for                                  */
+    int T_max;          /* longest horizon a request may ask for (warm-start plan length)   */
+    int max_inflight;   /* launch lanes: groups that may be on the GPU at once (>= 1)       */
+    int max_group;      /* most requests packed into one group (>= 1)                       */
+    size_t hbm_budget;  /* bytes of the scratch pool; 0 = half the free device memory,
+                           at most 32 GiB                                                   */
+    int want_costs;     /* 1: each kept result also holds the K per-rollout costs           */
+} pi_server_opts;
+
+/* One control update request of one agent. */
+typedef struct {
+    int agent;          /* 0 .. n_agents-1                                                   */
+    int K, T;           /* rollouts and horizon: 1 <= K <= K_max, 1 <= T <= T_max            */
+    float lambda;       /* temperature (> 0)                                                 */
+    float sigma_u[4];   /* control-noise variances (>= 0)                                    */
+    const float *x0;    /* host [12]: measured state replacing the agent's device state
+                           before the update; NULL = use the device-resident state          */
+    int keep_result;    /* 1: hold u_out (and costs) on the host for pi_server_result        */
+} pi_serve_request;
+
+/* Completion record of one request.  Times are host monotonic-clock
+ * nanoseconds: submission, the group's launch, and the moment the scheduler
+ * saw the result in host memory. */
+typedef struct {
+    uint64_t ticket;
+    int agent, K, T;
+    int status;         /* PI_OK, or PI_ERR_TIMEOUT / PI_ERR_INTERNAL / PI_ERR_CUDA           */
+    int group_size;     /* requests in the launch that carried this one                      */
+    int64_t t_submit_ns, t_launch_ns, t_result_ns;
+} pi_serve_done;
+
+/* One arrival of a replayed trace: at t_ns after the replay starts, agent asks
+ * for an update of size (K, T). */
+typedef struct {
+    int64_t t_ns;
+    int agent, K, T;
+} pi_serve_arrival;
+
+typedef struct {
+    uint64_t submitted, completed, groups, launches;
+    uint64_t memory_waits;      /* scheduler passes whose next eligible request did not fit the pool */
+    size_t pool_bytes, pool_peak_bytes;
+    int peak_inflight_requests, peak_group_size;
+} pi_server_stats;
+
+/* Defaults: n_agents 1, K_max 16384, T_max 128, max_inflight 2, max_group 64,
+ * hbm_budget 0, want_costs 0. */
+void pi_server_default_opts(pi_server_opts *opts);
+
+/* Creates a server over ctx's model and cost (ctx is borrowed and must
+ * outlive the server; its stream and scratch are not used) in the context's
+ * precision, and starts the scheduler thread.  Agents start at x0 = 0, a zero
+ * plan, counter 0 and seed = agent index.  Synchronous.
+ * Errors: INVALID_ARG, OOM (pool or tables do not fit), CUDA. */
+int pi_server_create(pi_ctx *ctx, const pi_server_opts *opts, pi_server **out);
+
+/* Sets an agent's device state: x0 [12] (host), plan u_warm [T_max][4] (host,
+ * NULL = zeros) and seed; resets its counter to 0.  The agent must have no
+ * request queued or in flight (else PI_ERR_BUSY).  Synchronous. */
+int pi_server_set_agent(pi_server *s, int agent, const float *x0, const float *u_warm, uint64_t seed);
+
+/* Queues a request (copies it, including *x0); returns at once with its
+ * ticket.  Errors: INVALID_ARG (sizes, parameters, or a request whose scratch
+ * exceeds the whole pool). */
+int pi_server_submit(pi_server *s, const pi_serve_request *req, uint64_t *ticket);
+
+/* Moves up to max completion records into out (oldest first), waiting up to
+ * timeout_us microseconds for the first one (0 = do not wait); *n_out = count. */
+int pi_server_poll(pi_server *s, pi_serve_done *out, int max, int64_t timeout_us, int *n_out);
+
+/* Copies a kept result and releases it: u_out [T][4] (host) and, if the server
+ * keeps costs, costs [K] (host, may be NULL).  INVALID_ARG if the ticket has no
+ * kept result (unknown, not finished, not kept, or already fetched). */
+int pi_server_result(pi_server *s, uint64_t ticket, float *u_out, float *costs);
+
+/* Waits until nothing is queued or on the GPU; PI_ERR_TIMEOUT after timeout_ms. */
+int pi_server_drain(pi_server *s, int64_t timeout_ms);
+
+/* Replays a trace in real time (arrivals sorted by t_ns) in the calling
+ * thread: an arrival whose agent still waits for its previous result is
+ * dropped (a controller that has no new plan yet keeps its old one); the rest
+ * are submitted with the parameters of proto (agent, K, T and x0 taken from
+ * the arrival / the device state, results not kept).  Returns when every
+ * submitted request has completed.  done [n] receives the completion records
+ * in completion order; *n_done and *n_dropped count them.  The server must
+ * be idle when the replay starts (else PI_ERR_BUSY); PI_ERR_TIMEOUT if no
+ * request completes for 60 s. */
+int pi_server_replay(pi_server *s, const pi_serve_arrival *arrivals, int n, const pi_serve_request *proto,
+                     pi_serve_done *done, int *n_done, int *n_dropped);
+
+/* Checkpoint / resume of every agent's state (host arrays): x0 [n][12],
+ * plan [n][T_max][4], counter [n], seed [n].  The server must be idle
+ * (PI_ERR_BUSY otherwise).  Synchronous. */
+int pi_server_state_save(pi_server *s, float *x0, float *u_warm, uint64_t *counter, uint64_t *seed);
+int pi_server_state_load(pi_server *s, const float *x0, const float *u_warm, const uint64_t *counter,
+                         const uint64_t *seed);
+
+int pi_server_get_stats(const pi_server *s, pi_server_stats *out);
+
+/* Stops the scheduler, waits for the groups on the GPU, drops queued requests
+ * and frees the server.  NULL is accepted. */
+void pi_server_destroy(pi_server *s);
+
+/* Host-only check of the server's pool allocator (no GPU): runs n operations
+ * on a pool of `capacity` bytes -- op[i] = 1 allocates size[i] bytes, op[i] = 0
+ * frees the block allocated by operation size[i] -- and writes each
+ * allocation's offset (or -1 if it did not fit) to offset[i] and, at the end,
+ * the number of free extents to *free_extents. */
+int pi_debug_pool(size_t capacity, const int *op, const size_t *size, int n, int64_t *offset, int *free_extents);
 
 /* Synchronizes the context's stream and reports device-side errors raised by
  * earlier work: PI_ERR_TIMEOUT if a bounded wait in a kernel expired (the

@@ -13,8 +13,10 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "lib", "libpi2rh.so")
 HEADER = os.path.join(os.path.dirname(PKG), "include", "pi2rh.h")
 
-PI_OK, PI_ERR_INVALID_ARG, PI_ERR_OOM, PI_ERR_CUDA, PI_ERR_TIMEOUT, PI_ERR_INTERNAL, PI_ERR_UNSUPPORTED = range(7)
-ERR_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "TIMEOUT", 5: "INTERNAL", 6: "UNSUPPORTED"}
+(PI_OK, PI_ERR_INVALID_ARG, PI_ERR_OOM, PI_ERR_CUDA, PI_ERR_TIMEOUT, PI_ERR_INTERNAL, PI_ERR_UNSUPPORTED,
+ PI_ERR_BUSY) = range(8)
+ERR_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "TIMEOUT", 5: "INTERNAL", 6: "UNSUPPORTED",
+             7: "BUSY"}
 
 _fp = ctypes.POINTER(ctypes.c_float)
 _vp = ctypes.c_void_p
@@ -41,6 +43,34 @@ class OptsC(ctypes.Structure):
 class BatchItemC(ctypes.Structure):
     _fields_ = [("ctx", _vp), ("K", ctypes.c_int), ("T", ctypes.c_int), ("x0", _vp), ("u_nominal", _vp),
                 ("u_out", _vp), ("costs_out", _vp)]
+
+
+class ServerOptsC(ctypes.Structure):
+    _fields_ = [("n_agents", ctypes.c_int), ("K_max", ctypes.c_int), ("T_max", ctypes.c_int),
+                ("max_inflight", ctypes.c_int), ("max_group", ctypes.c_int), ("hbm_budget", ctypes.c_size_t),
+                ("want_costs", ctypes.c_int)]
+
+
+class ServeRequestC(ctypes.Structure):
+    _fields_ = [("agent", ctypes.c_int), ("K", ctypes.c_int), ("T", ctypes.c_int), ("lam", ctypes.c_float),
+                ("sigma_u", ctypes.c_float * 4), ("x0", _vp), ("keep_result", ctypes.c_int)]
+
+
+class ServeDoneC(ctypes.Structure):
+    _fields_ = [("ticket", ctypes.c_uint64), ("agent", ctypes.c_int), ("K", ctypes.c_int), ("T", ctypes.c_int),
+                ("status", ctypes.c_int), ("group_size", ctypes.c_int), ("t_submit_ns", ctypes.c_int64),
+                ("t_launch_ns", ctypes.c_int64), ("t_result_ns", ctypes.c_int64)]
+
+
+class ServeArrivalC(ctypes.Structure):
+    _fields_ = [("t_ns", ctypes.c_int64), ("agent", ctypes.c_int), ("K", ctypes.c_int), ("T", ctypes.c_int)]
+
+
+class ServerStatsC(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("groups", ctypes.c_uint64),
+                ("launches", ctypes.c_uint64), ("memory_waits", ctypes.c_uint64), ("pool_bytes", ctypes.c_size_t),
+                ("pool_peak_bytes", ctypes.c_size_t), ("peak_inflight_requests", ctypes.c_int),
+                ("peak_group_size", ctypes.c_int)]
 
 
 class PiError(RuntimeError):
@@ -79,6 +109,25 @@ _SIGS = {
     "pi_batch_sync": (ctypes.c_int, [_vp]),
     "pi_batch_launch_count": (ctypes.c_uint64, [_vp]),
     "pi_batch_destroy": (None, [_vp]),
+    "pi_server_default_opts": (None, [ctypes.POINTER(ServerOptsC)]),
+    "pi_server_create": (ctypes.c_int, [_vp, ctypes.POINTER(ServerOptsC), ctypes.POINTER(_vp)]),
+    "pi_server_set_agent": (ctypes.c_int, [_vp, ctypes.c_int, _fp, _fp, ctypes.c_uint64]),
+    "pi_server_submit": (ctypes.c_int, [_vp, ctypes.POINTER(ServeRequestC), ctypes.POINTER(ctypes.c_uint64)]),
+    "pi_server_poll": (ctypes.c_int, [_vp, ctypes.POINTER(ServeDoneC), ctypes.c_int, ctypes.c_int64,
+                                      ctypes.POINTER(ctypes.c_int)]),
+    "pi_server_result": (ctypes.c_int, [_vp, ctypes.c_uint64, _fp, _fp]),
+    "pi_server_drain": (ctypes.c_int, [_vp, ctypes.c_int64]),
+    "pi_server_replay": (ctypes.c_int, [_vp, ctypes.POINTER(ServeArrivalC), ctypes.c_int,
+                                        ctypes.POINTER(ServeRequestC), ctypes.POINTER(ServeDoneC),
+                                        ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    "pi_server_state_save": (ctypes.c_int, [_vp, _fp, _fp, ctypes.POINTER(ctypes.c_uint64),
+                                            ctypes.POINTER(ctypes.c_uint64)]),
+    "pi_server_state_load": (ctypes.c_int, [_vp, _fp, _fp, ctypes.POINTER(ctypes.c_uint64),
+                                            ctypes.POINTER(ctypes.c_uint64)]),
+    "pi_server_get_stats": (ctypes.c_int, [_vp, ctypes.POINTER(ServerStatsC)]),
+    "pi_server_destroy": (None, [_vp]),
+    "pi_debug_pool": (ctypes.c_int, [ctypes.c_size_t, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_size_t),
+                                     ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int)]),
     "pi_debug_noise": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp]),
     "pi_debug_normals": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp,
                                         _vp]),

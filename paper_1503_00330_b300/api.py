@@ -262,3 +262,169 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+SEED_STEP = 0x9E3779B97F4A7C15   # seed of an agent's n-th update: seed + n * SEED_STEP (mod 2^64)
+
+DONE_DTYPE = np.dtype([("ticket", np.uint64), ("agent", np.int32), ("K", np.int32), ("T", np.int32),
+                       ("status", np.int32), ("group_size", np.int32), ("t_submit_ns", np.int64),
+                       ("t_launch_ns", np.int64), ("t_result_ns", np.int64)])
+
+
+def update_seed(seed: int, n: int) -> int:
+    """Noise seed of an agent's n-th served update."""
+    return (int(seed) + int(n) * SEED_STEP) % (1 << 64)
+
+
+def _done_array(buf, n: int) -> np.ndarray:
+    out = np.zeros(n, DONE_DTYPE)
+    for i in range(n):
+        d = buf[i]
+        out[i] = (d.ticket, d.agent, d.K, d.T, d.status, d.group_size, d.t_submit_ns, d.t_launch_ns, d.t_result_ns)
+    return out
+
+
+class Server:
+    """Receding-horizon serving loop over one shared model (``pi_server``).
+
+    ``controller`` supplies the model, cost, M and precision form; it must
+    outlive the server.  Agents' states, warm-start plans and update counters
+    stay in device memory; requests are queued with :meth:`submit` and their
+    completion records read with :meth:`poll`."""
+
+    def __init__(self, controller: Controller, n_agents: int, K_max: int = 16384, T_max: int = 128,
+                 max_inflight: int = 2, max_group: int = 64, hbm_budget: int = 0, want_costs: bool = False):
+        lib = _lib.load()
+        self._lib = lib
+        self.controller = controller
+        o = _lib.ServerOptsC()
+        lib.pi_server_default_opts(ctypes.byref(o))
+        o.n_agents, o.K_max, o.T_max = int(n_agents), int(K_max), int(T_max)
+        o.max_inflight, o.max_group, o.hbm_budget = int(max_inflight), int(max_group), int(hbm_budget)
+        o.want_costs = 1 if want_costs else 0
+        self.n_agents, self.K_max, self.T_max, self.want_costs = int(n_agents), int(K_max), int(T_max), want_costs
+        h = ctypes.c_void_p()
+        check(lib.pi_server_create(controller.handle, ctypes.byref(o), ctypes.byref(h)))
+        self._h = h
+
+    def set_agent(self, agent: int, x0, u_warm=None, seed: int = 0):
+        x = np.ascontiguousarray(np.asarray(x0, np.float32).reshape(NX))
+        w = None if u_warm is None else np.ascontiguousarray(np.asarray(u_warm, np.float32).reshape(self.T_max, NU))
+        fp = ctypes.POINTER(ctypes.c_float)
+        check(self._lib.pi_server_set_agent(self._h, int(agent), x.ctypes.data_as(fp),
+                                            None if w is None else w.ctypes.data_as(fp), int(seed) % (1 << 64)))
+
+    @staticmethod
+    def _request(agent, K, T, lam, sigma_u, x0=None, keep=True):
+        s = np.asarray(sigma_u, np.float32).reshape(4)
+        q = _lib.ServeRequestC(int(agent), int(K), int(T), float(lam), (ctypes.c_float * 4)(*s), None,
+                               1 if keep else 0)
+        xbuf = None
+        if x0 is not None:
+            xbuf = np.ascontiguousarray(np.asarray(x0, np.float32).reshape(NX))
+            q.x0 = xbuf.ctypes.data
+        return q, xbuf
+
+    def submit(self, agent: int, K: int, T: int, lam: float, sigma_u, x0=None, keep: bool = True) -> int:
+        q, _xbuf = self._request(agent, K, T, lam, sigma_u, x0, keep)
+        t = ctypes.c_uint64()
+        check(self._lib.pi_server_submit(self._h, ctypes.byref(q), ctypes.byref(t)))
+        return int(t.value)
+
+    def poll(self, max_n: int = 1024, timeout_us: int = 0) -> np.ndarray:
+        buf = (_lib.ServeDoneC * max_n)()
+        n = ctypes.c_int()
+        check(self._lib.pi_server_poll(self._h, buf, int(max_n), int(timeout_us), ctypes.byref(n)))
+        return _done_array(buf, n.value)
+
+    def result(self, ticket: int, T: int, K: int | None = None):
+        u = np.empty((T, NU), np.float32)
+        fp = ctypes.POINTER(ctypes.c_float)
+        c = np.empty(K, np.float32) if (K is not None and self.want_costs) else None
+        check(self._lib.pi_server_result(self._h, int(ticket), u.ctypes.data_as(fp),
+                                         None if c is None else c.ctypes.data_as(fp)))
+        return u, c
+
+    def drain(self, timeout_ms: int = 600_000):
+        check(self._lib.pi_server_drain(self._h, int(timeout_ms)))
+
+    def wait(self, tickets, timeout_s: float = 600.0) -> dict:
+        """Polls until every ticket in ``tickets`` has a completion record; returns them by ticket."""
+        want = set(int(t) for t in tickets)
+        got = {}
+        import time
+        t_end = time.monotonic() + timeout_s
+        while want - got.keys():
+            if time.monotonic() > t_end:
+                raise TimeoutError("requests did not complete")
+            for d in self.poll(1024, 100_000):
+                got[int(d["ticket"])] = d
+        return got
+
+    def replay(self, arrivals, lam: float, sigma_u):
+        """Real-time replay of ``arrivals`` = [(t_s, agent, K, T), ...] (sorted by time).
+
+        Returns (completion records, number of dropped arrivals)."""
+        n = len(arrivals)
+        arr = (_lib.ServeArrivalC * max(n, 1))()
+        for i, (t, a, K, T) in enumerate(arrivals):
+            arr[i] = _lib.ServeArrivalC(int(round(t * 1e9)), int(a), int(K), int(T))
+        proto, _ = self._request(0, 1, 1, lam, sigma_u, None, False)
+        done = (_lib.ServeDoneC * max(n, 1))()
+        nd, ndrop = ctypes.c_int(), ctypes.c_int()
+        check(self._lib.pi_server_replay(self._h, arr, n, ctypes.byref(proto), done, ctypes.byref(nd),
+                                         ctypes.byref(ndrop)))
+        return _done_array(done, nd.value), int(ndrop.value)
+
+    def state_save(self):
+        na = self.n_agents
+        x0 = np.empty((na, NX), np.float32)
+        w = np.empty((na, self.T_max, NU), np.float32)
+        ctr = np.empty(na, np.uint64)
+        sd = np.empty(na, np.uint64)
+        fp, up = ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_uint64)
+        check(self._lib.pi_server_state_save(self._h, x0.ctypes.data_as(fp), w.ctypes.data_as(fp),
+                                             ctr.ctypes.data_as(up), sd.ctypes.data_as(up)))
+        return {"x0": x0, "u_warm": w, "counter": ctr, "seed": sd}
+
+    def state_load(self, state: dict):
+        fp, up = ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_uint64)
+        x0 = np.ascontiguousarray(state["x0"], np.float32)
+        w = np.ascontiguousarray(state["u_warm"], np.float32)
+        ctr = np.ascontiguousarray(state["counter"], np.uint64)
+        sd = np.ascontiguousarray(state["seed"], np.uint64)
+        check(self._lib.pi_server_state_load(self._h, x0.ctypes.data_as(fp), w.ctypes.data_as(fp),
+                                             ctr.ctypes.data_as(up), sd.ctypes.data_as(up)))
+
+    def stats(self) -> dict:
+        s = _lib.ServerStatsC()
+        check(self._lib.pi_server_get_stats(self._h, ctypes.byref(s)))
+        return {f: getattr(s, f) for f, _ in s._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.pi_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def debug_pool(capacity: int, ops):
+    """Runs the serving pool allocator on the host: ops = [("alloc", nbytes) | ("free", op_index)].
+
+    Returns (offsets, free_extents); offsets[i] is the allocation's offset, -1 if it did not fit,
+    or the freed block's offset for a free."""
+    lib = _lib.load()
+    n = len(ops)
+    op = np.array([1 if k == "alloc" else 0 for k, _ in ops], np.int32)
+    sz = np.array([v for _, v in ops], np.uint64)
+    off = np.zeros(max(n, 1), np.int64)
+    ext = ctypes.c_int()
+    check(lib.pi_debug_pool(int(capacity), op.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                            sz.ctypes.data_as(ctypes.POINTER(ctypes.c_size_t)), n,
+                            off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), ctypes.byref(ext)))
+    return off[:n], int(ext.value)

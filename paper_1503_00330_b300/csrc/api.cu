@@ -132,33 +132,9 @@ int check_update_args(const float *lambda_p, float lambda, const float *sigma_u)
     return PI_OK;
 }
 
-RolloutArgs base_args(const pi_ctx *c)
-{
-    RolloutArgs a{};
-    a.rec = c->d_rec;
-    a.P = c->P;
-    a.stages_per_out = c->spo;
-    a.cost = c->cost;
-    a.dt = c->dt;
-    a.M = c->opts.M;
-    a.model_noise = c->opts.model_noise == PI_NOISE_SAMPLED ? 1 : 0;
-    a.err = c->d_err;
-    return a;
-}
+RolloutArgs base_args(const pi_ctx *c) { return ctx_rollout_args(c); }
 
-TcArgs tc_args(const pi_ctx *c)
-{
-    TcArgs t{};
-    t.wtiles = c->d_wtiles;
-    t.wconst = c->d_wconst;
-    t.tiles_per_out = c->tiles_per_out;
-    t.cost = c->cost;
-    t.dt = c->dt;
-    t.M = c->opts.M;
-    t.model_noise = c->opts.model_noise == PI_NOISE_SAMPLED ? 1 : 0;
-    t.err = c->d_err;
-    return t;
-}
+TcArgs tc_args(const pi_ctx *c) { return ctx_tc_args(c); }
 
 int launch_rollouts(pi_ctx *c, const float *x0, const float *u_nom, int K, int T,
                     const float *sigma_u, uint64_t seed, float *cost, float4 *eps, float *phi)

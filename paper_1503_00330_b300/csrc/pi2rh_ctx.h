@@ -7,6 +7,7 @@
 
 #include "pi2rh.h"
 #include "pi2rh_device.cuh"
+#include "pi2rh_kernels.h"
 
 struct pi_ctx {
     int device = 0;
@@ -40,3 +41,32 @@ struct pi_ctx {
 
 // Records msg as the calling thread's last error (pi_last_error) and returns code.
 int pi2rh_fail(int code, const char *msg);
+
+// Kernel arguments that depend only on the context (model, cost, options).
+inline pi2rh::RolloutArgs ctx_rollout_args(const pi_ctx *c)
+{
+    pi2rh::RolloutArgs a{};
+    a.rec = c->d_rec;
+    a.P = c->P;
+    a.stages_per_out = c->spo;
+    a.cost = c->cost;
+    a.dt = c->dt;
+    a.M = c->opts.M;
+    a.model_noise = c->opts.model_noise == PI_NOISE_SAMPLED ? 1 : 0;
+    a.err = c->d_err;
+    return a;
+}
+
+inline pi2rh::TcArgs ctx_tc_args(const pi_ctx *c)
+{
+    pi2rh::TcArgs t{};
+    t.wtiles = c->d_wtiles;
+    t.wconst = c->d_wconst;
+    t.tiles_per_out = c->tiles_per_out;
+    t.cost = c->cost;
+    t.dt = c->dt;
+    t.M = c->opts.M;
+    t.model_noise = c->opts.model_noise == PI_NOISE_SAMPLED ? 1 : 0;
+    t.err = c->d_err;
+    return t;
+}
