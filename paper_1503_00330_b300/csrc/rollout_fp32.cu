@@ -197,18 +197,19 @@ __device__ __forceinline__ void fp32_init_barriers(const Fp32Smem &S)
     fence_mbar_init();
 }
 
-// Producer (one lane): streams the field-pair records of one work item
-// (nsteps passes over the model) through the stage ring.  `g0` is the ring
-// position at the start of the item; returns the position after it, or -1
-// after a timeout (abort flag set).
+// Producer (one lane): streams the field-pair records of outputs o_lo ..
+// o_lo + n_out - 1 for one work item (nsteps passes over them) through the
+// stage ring.  `g0` is the ring position at the start of the item; returns
+// the position after it, or -1 after a timeout (abort flag set).
 template <bool PREDICT>
-__device__ long long fp32_producer(const RolloutArgs &a, const Fp32Smem &S, long long g0, long long &issued)
+__device__ long long fp32_producer(const RolloutArgs &a, const Fp32Smem &S, long long g0, long long &issued,
+                                   int o_lo = 0, int n_out = NY)
 {
     unsigned char *stage_base = S.stage_base;
     uint64_t *full = S.full, *empty = S.empty;
     volatile int *abort_flag = S.abort_flag;
     const int P = a.P, spo = a.stages_per_out;
-    const int G = NY * spo;
+    const int G = n_out * spo;
     const int nsteps = PREDICT ? 2 : a.T;
     const long long total = g0 + (long long)G * nsteps;
         for (long long g = g0; g < total; ++g) {
@@ -222,7 +223,7 @@ __device__ long long fp32_producer(const RolloutArgs &a, const Fp32Smem &S, long
                 }
             }
             const int gs = (int)((g - g0) % G);
-            const int o = gs / spo, s = gs % spo;
+            const int o = o_lo + gs / spo, s = gs % spo;
             const int p0 = s * RF_PAIRS_PER_STAGE;
             const int np = min(RF_PAIRS_PER_STAGE, P - p0);
             const uint32_t bytes = (uint32_t)np * REC_BYTES;
@@ -236,9 +237,12 @@ __device__ long long fp32_producer(const RolloutArgs &a, const Fp32Smem &S, long
 
 // Consumers (8 warps): evaluate the LWPR model for the 64 slots of one work
 // item starting at slot_base, step the dynamics and write the item's outputs.
-// `g` is the ring position (advanced in step with the producer).
+// `g` is the ring position (advanced in step with the producer).  Prediction
+// mode may cover only outputs o_lo .. o_lo + n_out - 1 (each output's mean and
+// variance depend on that output's fields alone).
 template <bool PREDICT>
-__device__ void fp32_consumer(const RolloutArgs &a, const Fp32Smem &S, long long slot_base, long long &g, bool &aborted)
+__device__ void fp32_consumer(const RolloutArgs &a, const Fp32Smem &S, long long slot_base, long long &g, bool &aborted,
+                              int o_lo = 0, int n_out = NY)
 {
     unsigned char *stage_base = S.stage_base;
     float *part = S.part, *zbuf = S.zbuf, *xbuf = S.xbuf, *ybuf = S.ybuf, *vbuf = S.vbuf, *yrbuf = S.yrbuf,
@@ -293,7 +297,7 @@ __device__ void fp32_consumer(const RolloutArgs &a, const Fp32Smem &S, long long
             zA[c] = make_float2(va, va);
             zB[c] = make_float2(vb, vb);
         }
-        for (int o = 0; o < NY; ++o) {
+        for (int o = o_lo; o < o_lo + n_out; ++o) {
             const float ya = -yrbuf[o * SLOTS + slotA], yb = -yrbuf[o * SLOTS + slotB];
             const float2 yrA = make_float2(ya, ya), yrB = make_float2(yb, yb);
             Soft stA, stB;
@@ -338,25 +342,24 @@ __device__ void fp32_consumer(const RolloutArgs &a, const Fp32Smem &S, long long
             }
         }
 
-        if (stepper) {
+        if (stepper && PREDICT) {
+            if (t == 0) {
+                for (int o = o_lo; o < o_lo + n_out; ++o) yrbuf[o * SLOTS + tid] = ybuf[o * SLOTS + tid];
+            } else if (gslot < a.n_pred) {
+                for (int o = o_lo; o < o_lo + n_out; ++o) {
+                    a.y_out[(size_t)gslot * NY + o] = ybuf[o * SLOTS + tid];
+                    a.var_out[(size_t)gslot * NY + o] = vbuf[o * SLOTS + tid];
+                }
+            }
+        }
+        if (stepper && !PREDICT) {
             float y[NY], var[NY];
 #pragma unroll
             for (int o = 0; o < NY; ++o) {
                 y[o] = ybuf[o * SLOTS + tid];
                 var[o] = vbuf[o * SLOTS + tid];
             }
-            if (PREDICT) {
-                if (t == 0) {
-#pragma unroll
-                    for (int o = 0; o < NY; ++o) yrbuf[o * SLOTS + tid] = y[o];
-                } else if (gslot < a.n_pred) {
-#pragma unroll
-                    for (int o = 0; o < NY; ++o) {
-                        a.y_out[(size_t)gslot * NY + o] = y[o];
-                        a.var_out[(size_t)gslot * NY + o] = var[o];
-                    }
-                }
-            } else {
+            {
                 float x[NX];
 #pragma unroll
                 for (int c = 0; c < NX; ++c) x[c] = xbuf[c * SLOTS + tid];
@@ -418,19 +421,23 @@ __device__ void fp32_consumer(const RolloutArgs &a, const Fp32Smem &S, long long
     }
 }
 
+// blockIdx.x = 64-slot block; in prediction mode blockIdx.y selects a group
+// of NY / gridDim.y outputs.
 template <bool PREDICT>
 __global__ void __launch_bounds__(NTHREADS, 1) rollout_fp32_kernel(const __grid_constant__ RolloutArgs a)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     const Fp32Smem S = fp32_smem(smem);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int n_out = PREDICT ? NY / (int)gridDim.y : NY;
+    const int o_lo = PREDICT ? (int)blockIdx.y * n_out : 0;
     if (tid == 0) fp32_init_barriers(S);
     for (int i = tid; i < a.cost.n_obs; i += NTHREADS) S.obs_s[i] = a.cost.obs[i];
     __syncthreads();
     if (warp == CW) {
         if (lane != 0) return;
         long long issued = 0;
-        fp32_producer<PREDICT>(a, S, 0, issued);
+        fp32_producer<PREDICT>(a, S, 0, issued, o_lo, n_out);
         // keep the CTA alive until every copy issued has landed
         for (long long g = (issued > NSTAGE ? issued - NSTAGE : 0); g < issued; ++g)
             if (!mbar_wait_drain(&S.full[g % NSTAGE], (uint32_t)((g / NSTAGE) & 1))) atomicOr(a.err, DEVERR_TIMEOUT_DRAIN);
@@ -438,7 +445,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) rollout_fp32_kernel(const __grid_
     }
     long long g = 0;
     bool aborted = false;
-    fp32_consumer<PREDICT>(a, S, (long long)blockIdx.x * SLOTS, g, aborted);
+    fp32_consumer<PREDICT>(a, S, (long long)blockIdx.x * SLOTS, g, aborted, o_lo, n_out);
 }
 
 // Persistent batched form: CTAs take (controller, slot block) work items from
@@ -495,7 +502,10 @@ cudaError_t launch_impl(const RolloutArgs &a, cudaStream_t s, long long slots)
     }
     const long long blocks = (slots + SLOTS - 1) / SLOTS;
     if (blocks <= 0 || blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
-    rollout_fp32_kernel<PREDICT><<<(unsigned)blocks, NTHREADS, SMEM_BYTES, s>>>(a);
+    // prediction of a few rows (the receding-horizon plant step): one CTA per
+    // output instead of one CTA sweeping all 12 outputs
+    const unsigned out_groups = PREDICT && blocks * NY <= 4 * 148 ? NY : 1;
+    rollout_fp32_kernel<PREDICT><<<dim3((unsigned)blocks, out_groups), NTHREADS, SMEM_BYTES, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -33,6 +33,7 @@
 // Every wait is bounded; on expiry the kernel flags the device error word,
 // drains its copies and MMAs, frees its tensor memory and returns.
 #include <cstdio>
+#include <cstdlib>
 
 #include <cuda_fp16.h>
 
@@ -70,8 +71,8 @@ constexpr int OFF_Q = OFF_YREF + NY * BM * 4;                   // [BM]
 constexpr int OFF_OBS = OFF_Q + BM * 4;
 constexpr int OFF_BAR = OFF_OBS + MAX_OBS * 8;
 // barriers: full[NSLOT], empty[NSLOT], acc_full[2], acc_empty[2],
-//           const_full[4], const_empty[4], phi_ready
-constexpr int NBARS = 2 * NSLOT + 4 + 2 * NCONST + 1;
+//           const_full[4], const_empty[4], phi_ready, xfull, xfree
+constexpr int NBARS = 2 * NSLOT + 4 + 2 * NCONST + 3;
 constexpr int OFF_TSLOT = OFF_BAR + NBARS * 8;
 constexpr int OFF_ABORT = OFF_TSLOT + 8;
 constexpr int SMEM_BYTES = OFF_ABORT + 16;
@@ -148,6 +149,7 @@ struct TcSmem {
     float *part, *zbuf, *xbuf, *ybuf, *vbuf, *yrbuf, *qbuf;
     float2 *obs_s;
     uint64_t *full, *empty, *acc_full, *acc_empty, *const_full, *const_empty, *phi_ready;
+    uint64_t *xfull, *xfree;   // output exchange between the CTAs of a cluster (split form)
     uint32_t *tslot;
     volatile int *abort_flag;
 };
@@ -172,13 +174,16 @@ __device__ __forceinline__ TcSmem tc_smem(unsigned char *smem)
     S.const_full = S.acc_empty + 2;
     S.const_empty = S.const_full + NCONST;
     S.phi_ready = S.const_empty + NCONST;
+    S.xfull = S.phi_ready + 1;
+    S.xfree = S.phi_ready + 2;
     S.tslot = reinterpret_cast<uint32_t *>(smem + OFF_TSLOT);
     S.abort_flag = reinterpret_cast<volatile int *>(smem + OFF_ABORT);
     return S;
 }
 
-// One-time set-up: TMEM allocation (warp 1) and barrier initialization (thread 0).
-__device__ __forceinline__ void tc_setup(const TcSmem &S)
+// One-time set-up: TMEM allocation (warp 1) and barrier initialization
+// (thread 0).  ncl = CTAs in the cluster (1 unless the outputs are split).
+__device__ __forceinline__ void tc_setup(const TcSmem &S, uint32_t ncl)
 {
     const int tid = threadIdx.x, warp = tid >> 5;
     if (warp == 1) {
@@ -199,6 +204,10 @@ __device__ __forceinline__ void tc_setup(const TcSmem &S)
             mbar_init(&S.const_empty[i], NEPI);
         }
         mbar_init(S.phi_ready, NEPI);
+        // every owner thread of every other CTA arrives once per step
+        const uint32_t xc = ncl > 1 ? (ncl - 1) * BM : 1;
+        mbar_init(S.xfull, xc);
+        mbar_init(S.xfree, xc);
         *S.abort_flag = 0;
         fence_mbar_init();
     }
@@ -214,14 +223,16 @@ struct TcIssuer {
     int slot = 0;
 };
 
-// Producer (lane 0 of warp 0) for one work item; false after a timeout.
+// Producer (lane 0 of warp 0) for one work item -- the tiles of outputs
+// o_begin .. o_begin + n_out - 1 -- ; false after a timeout.
 template <bool PREDICT>
-__device__ bool tc_producer_item(const TcArgs &a, const TcSmem &S, TcProducer &P)
+__device__ bool tc_producer_item(const TcArgs &a, const TcSmem &S, TcProducer &P, int o_begin, int n_out)
 {
     unsigned char *smem = S.base;
     uint64_t *full = S.full, *empty = S.empty, *const_full = S.const_full, *const_empty = S.const_empty;
     volatile int *abort_flag = S.abort_flag;
-    const int G = NY * a.tiles_per_out;
+    const int G = n_out * a.tiles_per_out;
+    const long long tile0 = (long long)o_begin * a.tiles_per_out;
     const int nsteps = PREDICT ? 2 : a.T;
     long long &g = P.g, &q = P.q, &issued_tiles = P.issued_tiles;
     int &slot = P.slot;
@@ -231,7 +242,7 @@ __device__ bool tc_producer_item(const TcArgs &a, const TcSmem &S, TcProducer &P
         const int c = (int)(g & 3);
         if (g >= 4) ok = mbar_wait_bounded(&const_empty[c], (uint32_t)(((g >> 2) - 1) & 1), abort_flag);
         if (!ok) break;
-        const long long tile = (g - g0) % G;            // (output, tile) in order
+        const long long tile = tile0 + (g - g0) % G;    // (output, tile) in order
         mbar_arrive_expect_tx(&const_full[c], TC_CONST_BYTES);
         bulk_g2s(smem + OFF_CONST + c * TC_CONST_BYTES, a.wconst + tile * TC_CONST_BYTES, TC_CONST_BYTES,
                  &const_full[c]);
@@ -252,13 +263,13 @@ __device__ bool tc_producer_item(const TcArgs &a, const TcSmem &S, TcProducer &P
 
 // MMA issuer (lane 0 of warp 1) for one work item; false after a timeout.
 template <bool PREDICT>
-__device__ bool tc_issuer_item(const TcArgs &a, const TcSmem &S, uint32_t tbase, TcIssuer &I)
+__device__ bool tc_issuer_item(const TcArgs &a, const TcSmem &S, uint32_t tbase, TcIssuer &I, int n_out)
 {
     unsigned char *smem = S.base;
     uint64_t *full = S.full, *empty = S.empty, *acc_full = S.acc_full, *acc_empty = S.acc_empty;
     uint64_t *phi_ready = S.phi_ready;
     volatile int *abort_flag = S.abort_flag;
-    const int G = NY * a.tiles_per_out;
+    const int G = n_out * a.tiles_per_out;
     const int nsteps = PREDICT ? 2 : a.T;
     long long &g = I.g, &q = I.q, &q_committed = I.q_committed, &ts = I.ts;
     int &slot = I.slot;
@@ -312,11 +323,22 @@ __device__ bool tc_issuer_item(const TcArgs &a, const TcSmem &S, uint32_t tbase,
     return ok;
 }
 
-// Epilogue warps (2-9) for one work item: the 128 slots starting at slot_base.
-template <bool PREDICT>
+// Epilogue warps (2-9) for one work item: the 128 slots starting at
+// slot_base, outputs o_begin .. o_begin + n_out - 1.  With ncl > 1 CTAs in
+// the cluster (split form, rollouts only), every CTA evaluates its own share
+// of the outputs, sends their means and variances to the other CTAs'
+// y / var buffers (distributed shared memory) and then steps the dynamics of
+// all 128 slots itself -- the same arithmetic on the same values in every
+// CTA; only rank 0 writes the outputs.  Per step, xfull completes when the
+// other CTAs' values have landed and xfree when they have read this CTA's
+// previous ones, so a CTA is never more than one step ahead of another.
+template <bool PREDICT, int NSPLIT>
 __device__ void tc_epilogue_item(const TcArgs &a, const TcSmem &S, uint32_t tbase, long long slot_base, long long &g,
-                                 bool &aborted)
+                                 bool &aborted, uint32_t rank)
 {
+    constexpr int n_out = NY / NSPLIT;
+    constexpr uint32_t ncl = NSPLIT;
+    const int o_begin = (int)rank * n_out;
     unsigned char *smem = S.base;
     float *part = S.part, *zbuf = S.zbuf, *xbuf = S.xbuf, *ybuf = S.ybuf, *vbuf = S.vbuf, *yrbuf = S.yrbuf,
           *qbuf = S.qbuf;
@@ -335,7 +357,7 @@ __device__ void tc_epilogue_item(const TcArgs &a, const TcSmem &S, uint32_t tbas
     const bool owner = h == 0;
     const long long gslot = slot_base + r;
     const int k = (int)(gslot / M), m = (int)(gslot % M);
-    const bool writer = owner && !PREDICT && k < a.K && m == 0;
+    const bool writer = owner && rank == 0 && !PREDICT && k < a.K && m == 0;
     const uint32_t lane_off = (uint32_t)(32 * q) << 16;
 
     // initial feature tile
@@ -372,7 +394,7 @@ __device__ void tc_epilogue_item(const TcArgs &a, const TcSmem &S, uint32_t tbas
     named_bar_sync(1, NE);
 
     for (int t = 0; t < nsteps; ++t) {
-        for (int o = 0; o < NY; ++o) {
+        for (int o = o_begin; o < o_begin + n_out; ++o) {
             const float yref = yrbuf[o * BM + r];
             Soft st{-INFINITY, 0.f, 0.f, 0.f, 0.f};
             for (int j = 0; j < ntiles; ++j, ++g) {
@@ -445,6 +467,27 @@ __device__ void tc_epilogue_item(const TcArgs &a, const TcSmem &S, uint32_t tbas
             }
         }
 
+        // ------------------------------------------ exchange (split form only)
+        if (!PREDICT && ncl > 1 && owner) {
+            if (t > 0 && !aborted && !mbar_wait_cluster_bounded(S.xfree, (uint32_t)((t - 1) & 1), abort_flag))
+                aborted = true;
+            if (!aborted) {
+                for (uint32_t pr = 0; pr < ncl; ++pr) {
+                    if (pr == rank) continue;
+                    // the peer's y / var rows of this CTA's outputs (same offsets as here)
+                    const uint32_t ry = mapa_shared(ybuf, pr) + (uint32_t)((o_begin * BM + r) * 4);
+                    const uint32_t rv = mapa_shared(vbuf, pr) + (uint32_t)((o_begin * BM + r) * 4);
+#pragma unroll
+                    for (int i = 0; i < n_out; ++i) {
+                        st_cluster_f32(ry + i * BM * 4, ybuf[(o_begin + i) * BM + r]);
+                        st_cluster_f32(rv + i * BM * 4, vbuf[(o_begin + i) * BM + r]);
+                    }
+                    mbar_arrive_remote(mapa_shared(S.xfull, pr));
+                }
+            }
+            if (!aborted && !mbar_wait_cluster_bounded(S.xfull, (uint32_t)(t & 1), abort_flag)) aborted = true;
+        }
+
         // ---------------------------------------------------------- dynamics
         if (owner) {
             float y[NY], var[NY], zext[17];
@@ -453,6 +496,9 @@ __device__ void tc_epilogue_item(const TcArgs &a, const TcSmem &S, uint32_t tbas
                 y[o] = ybuf[o * BM + r];
                 var[o] = vbuf[o * BM + r];
             }
+            if (!PREDICT && ncl > 1 && !aborted)
+                for (uint32_t pr = 0; pr < ncl; ++pr)
+                    if (pr != rank) mbar_arrive_remote(mapa_shared(S.xfree, pr));
             if (PREDICT) {
                 if (t == 0) {
 #pragma unroll
@@ -564,34 +610,43 @@ __device__ __forceinline__ void tc_flag_abort(const TcArgs &a, const TcSmem &S, 
     *S.abort_flag = 1;
 }
 
-template <bool PREDICT>
+// Single-controller kernel.  NSPLIT = 1: one CTA per 128-slot block.
+// NSPLIT = 2, 3, 4 (rollouts only): launched in clusters of NSPLIT CTAs that
+// share one slot block and split its 12 outputs (see tc_epilogue_item).
+template <bool PREDICT, int NSPLIT>
 __global__ void __launch_bounds__(NTHREADS, 1) rollout_tc_kernel(const __grid_constant__ TcArgs a)
 {
+    static_assert(NSPLIT == 1 || !PREDICT, "prediction mode is not split");
     extern __shared__ __align__(1024) unsigned char smem[];
     const TcSmem S = tc_smem(smem);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    tc_setup(S);
+    constexpr uint32_t ncl = NSPLIT;
+    const uint32_t rank = NSPLIT > 1 ? cluster_rank() : 0u;
+    constexpr int n_out = NY / NSPLIT;
+    const int o_begin = (int)rank * n_out;
+    tc_setup(S, ncl);
     for (int i = tid; i < a.cost.n_obs; i += NTHREADS) S.obs_s[i] = a.cost.obs[i];
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
+    if (ncl > 1) cluster_sync_all();   // every CTA's barriers exist before any remote arrival
     const uint32_t tbase = *S.tslot;
     TcProducer P;
     TcIssuer I;
     bool issuer_ok = true;
     if (warp == 0) {
-        if (lane == 0 && !tc_producer_item<PREDICT>(a, S, P)) tc_flag_abort(a, S, DEVERR_TIMEOUT_EMPTY);
+        if (lane == 0 && !tc_producer_item<PREDICT>(a, S, P, o_begin, n_out)) tc_flag_abort(a, S, DEVERR_TIMEOUT_EMPTY);
         __syncwarp();
     } else if (warp == 1) {
         if (lane == 0) {
-            issuer_ok = tc_issuer_item<PREDICT>(a, S, tbase, I);
+            issuer_ok = tc_issuer_item<PREDICT>(a, S, tbase, I, n_out);
             if (!issuer_ok) tc_flag_abort(a, S, DEVERR_TIMEOUT_FULL);
         }
         __syncwarp();
     } else {
         long long g = 0;
         bool aborted = false;
-        tc_epilogue_item<PREDICT>(a, S, tbase, (long long)blockIdx.x * BM, g, aborted);
+        tc_epilogue_item<PREDICT, NSPLIT>(a, S, tbase, (long long)(blockIdx.x / ncl) * BM, g, aborted, rank);
         if (aborted) tc_flag_abort(a, S, DEVERR_TIMEOUT_FULL);
     }
     tc_drain(a, S, P, I, issuer_ok);
@@ -602,6 +657,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) rollout_tc_kernel(const __grid_co
         tc_fence_after();
         tmem_dealloc(tbase, TMEM_COLS);
     }
+    if (ncl > 1) cluster_sync_all();   // no CTA leaves while another may still write into it
 }
 
 // Persistent batched form (see rollout_fp32_batch_kernel): CTAs claim
@@ -614,7 +670,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) rollout_tc_batch_kernel(const __g
     __shared__ int s_item;
     const TcSmem S = tc_smem(smem);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    tc_setup(S);
+    tc_setup(S, 1);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -636,16 +692,16 @@ __global__ void __launch_bounds__(NTHREADS, 1) rollout_tc_batch_kernel(const __g
         for (int i = tid; i < a.cost.n_obs; i += NTHREADS) S.obs_s[i] = a.cost.obs[i];
         __syncthreads();
         if (warp == 0) {
-            if (lane == 0 && !tc_producer_item<false>(a, S, P)) tc_flag_abort(a, S, DEVERR_TIMEOUT_EMPTY);
+            if (lane == 0 && !tc_producer_item<false>(a, S, P, 0, NY)) tc_flag_abort(a, S, DEVERR_TIMEOUT_EMPTY);
             __syncwarp();
         } else if (warp == 1) {
             if (lane == 0 && issuer_ok) {
-                issuer_ok = tc_issuer_item<false>(a, S, tbase, I);
+                issuer_ok = tc_issuer_item<false>(a, S, tbase, I, NY);
                 if (!issuer_ok) tc_flag_abort(a, S, DEVERR_TIMEOUT_FULL);
             }
             __syncwarp();
         } else {
-            tc_epilogue_item<false>(a, S, tbase, (long long)it.y * BM, g, aborted);
+            tc_epilogue_item<false, 1>(a, S, tbase, (long long)it.y * BM, g, aborted, 0);
             if (aborted) tc_flag_abort(a, S, DEVERR_TIMEOUT_FULL);
         }
         __syncthreads();
@@ -659,31 +715,99 @@ __global__ void __launch_bounds__(NTHREADS, 1) rollout_tc_batch_kernel(const __g
     }
 }
 
-bool g_tc_attr[2] = {false, false};
 char g_tc_diag[256] = "";
 
-template <bool PREDICT>
-cudaError_t launch_tc_impl(const TcArgs &a, cudaStream_t s, long long slots)
+void split_config(cudaLaunchConfig_t &cfg, cudaLaunchAttribute *at, long long blocks, int split, cudaStream_t s)
 {
-    if (a.cost.n_obs > MAX_OBS || a.tiles_per_out <= 0) return cudaErrorInvalidValue;
-    if (!g_tc_attr[PREDICT]) {
-        cudaError_t e = cudaFuncSetAttribute(rollout_tc_kernel<PREDICT>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-        if (e != cudaSuccess) return e;
-        cudaFuncAttributes fa;
-        e = cudaFuncGetAttributes(&fa, rollout_tc_kernel<PREDICT>);
-        if (e != cudaSuccess) return e;
-        snprintf(g_tc_diag, sizeof g_tc_diag,
-                 "regs %d, maxThreadsPerBlock %d, dynamic smem %d (max %d), static smem %zu, local %zu",
-                 fa.numRegs, fa.maxThreadsPerBlock, SMEM_BYTES, fa.maxDynamicSharedSizeBytes, fa.sharedSizeBytes,
-                 fa.localSizeBytes);
-        if (fa.maxThreadsPerBlock < NTHREADS) return cudaErrorLaunchOutOfResources;
-        g_tc_attr[PREDICT] = true;
+    cfg.gridDim = dim3((unsigned)(blocks * split));
+    cfg.blockDim = dim3(NTHREADS);
+    cfg.dynamicSmemBytes = SMEM_BYTES;
+    cfg.stream = s;
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)split;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+}
+
+// Sets the shared-memory attribute of one kernel instantiation once and
+// checks that it can be launched with NTHREADS threads.
+template <bool PREDICT, int NSPLIT>
+cudaError_t prepare_tc()
+{
+    static bool done = false;
+    if (done) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(rollout_tc_kernel<PREDICT, NSPLIT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, rollout_tc_kernel<PREDICT, NSPLIT>);
+    if (e != cudaSuccess) return e;
+    snprintf(g_tc_diag, sizeof g_tc_diag,
+             "split %d: regs %d, maxThreadsPerBlock %d, dynamic smem %d (max %d), static smem %zu, local %zu", NSPLIT,
+             fa.numRegs, fa.maxThreadsPerBlock, SMEM_BYTES, fa.maxDynamicSharedSizeBytes, fa.sharedSizeBytes,
+             fa.localSizeBytes);
+    if (fa.maxThreadsPerBlock < NTHREADS) return cudaErrorLaunchOutOfResources;
+    done = true;
+    return cudaSuccess;
+}
+
+template <int NSPLIT>
+bool all_clusters_resident(long long blocks)
+{
+    if (prepare_tc<false, NSPLIT>() != cudaSuccess) {
+        cudaGetLastError();
+        return false;
     }
-    const long long blocks = (slots + BM - 1) / BM;
-    if (blocks <= 0 || blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
-    rollout_tc_kernel<PREDICT><<<(unsigned)blocks, NTHREADS, SMEM_BYTES, s>>>(a);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    split_config(cfg, at, blocks, NSPLIT, nullptr);
+    int clusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&clusters, rollout_tc_kernel<false, NSPLIT>, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return clusters >= blocks;
+}
+
+// Output split of the single-controller rollout launch: the largest of 4, 3, 2
+// CTAs per slot block such that every cluster is resident at once (one wave);
+// 1 when the slot blocks alone fill the GPU.  PI2RH_TC_SPLIT = 1..4 forces a
+// value (the results are bitwise the same for every split).
+int choose_split(long long blocks)
+{
+    if (const char *e = getenv("PI2RH_TC_SPLIT")) {
+        const int v = atoi(e);
+        if (v >= 1 && v <= 4) return v;
+    }
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (blocks * 4 <= sms && all_clusters_resident<4>(blocks)) return 4;
+    if (blocks * 3 <= sms && all_clusters_resident<3>(blocks)) return 3;
+    if (blocks * 2 <= sms && all_clusters_resident<2>(blocks)) return 2;
+    return 1;
+}
+
+template <int NSPLIT>
+cudaError_t launch_split(const TcArgs &a, long long blocks, cudaStream_t s)
+{
+    cudaError_t e = prepare_tc<false, NSPLIT>();
+    if (e != cudaSuccess) return e;
+    if (NSPLIT == 1) {
+        rollout_tc_kernel<false, NSPLIT><<<(unsigned)blocks, NTHREADS, SMEM_BYTES, s>>>(a);
+        return cudaGetLastError();
+    }
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    split_config(cfg, at, blocks, NSPLIT, s);
+    return cudaLaunchKernelEx(&cfg, rollout_tc_kernel<false, NSPLIT>, a);
+}
+
+cudaError_t check_tc_args(const TcArgs &a)
+{
+    return a.cost.n_obs > MAX_OBS || a.tiles_per_out <= 0 ? cudaErrorInvalidValue : cudaSuccess;
 }
 
 }  // namespace
@@ -693,12 +817,27 @@ const char *tc_launch_diag() { return g_tc_diag; }
 cudaError_t launch_rollout_tc(const TcArgs &a, cudaStream_t s)
 {
     if (a.M < 1 || a.M > BM || (a.M & (a.M - 1)) != 0) return cudaErrorInvalidValue;
-    return launch_tc_impl<false>(a, s, (long long)a.K * a.M);
+    cudaError_t e = check_tc_args(a);
+    if (e != cudaSuccess) return e;
+    const long long blocks = ((long long)a.K * a.M + BM - 1) / BM;
+    if (blocks <= 0 || blocks > 0x7fffffffLL / 4) return cudaErrorInvalidValue;
+    switch (choose_split(blocks)) {
+    case 4: return launch_split<4>(a, blocks, s);
+    case 3: return launch_split<3>(a, blocks, s);
+    case 2: return launch_split<2>(a, blocks, s);
+    default: return launch_split<1>(a, blocks, s);
+    }
 }
 
 cudaError_t launch_predict_tc(const TcArgs &a, cudaStream_t s)
 {
-    return launch_tc_impl<true>(a, s, (long long)a.n_pred);
+    cudaError_t e = check_tc_args(a);
+    if (e == cudaSuccess) e = prepare_tc<true, 1>();
+    if (e != cudaSuccess) return e;
+    const long long blocks = ((long long)a.n_pred + BM - 1) / BM;
+    if (blocks <= 0 || blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+    rollout_tc_kernel<true, 1><<<(unsigned)blocks, NTHREADS, SMEM_BYTES, s>>>(a);
+    return cudaGetLastError();
 }
 
 bool g_tc_batch_attr = false;

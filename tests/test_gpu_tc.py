@@ -108,3 +108,23 @@ def test_tc_precision_workload_sampled(ctl, oracle):
         print(f"TC precision rollout {k}: rel err {abs(c[k] - S0) / S0:.3g}")
         assert abs(c[k] - S0) / S0 <= 1e-5
     assert np.all(np.isfinite(u.cpu().numpy()))
+
+
+@pytest.mark.parametrize("K,T,L,M", [(256, 20, 300, 1), (300, 9, 64, 2), (1, 4, 5, 1)])
+def test_tc_output_split_is_bitwise_invariant(ctl, monkeypatch, K, T, L, M):
+    """The single-controller rollout may split a slot block's 12 outputs over
+    a cluster of 2, 3 or 4 CTAs that exchange their means and variances
+    through distributed shared memory; every split gives the same bits."""
+    p = W.problem(K, T, L, seed=21, n_obs=5, M=M)
+    p.u_nom = np.random.default_rng(2).normal(0, 0.2, (T, 4)).astype(np.float32)
+    c = _tc(p)
+    out = {}
+    for split in ("1", "2", "3", "4"):
+        monkeypatch.setenv("PI2RH_TC_SPLIT", split)
+        u, cs = c.update(p.x0, p.u_nom, p.K, p.T, p.lam, p.sigma_u, p.seed)
+        c.sync()
+        out[split] = (u.cpu().numpy(), cs.cpu().numpy())
+    for split in ("2", "3", "4"):
+        assert np.array_equal(out[split][0], out["1"][0]), f"u_out differs with split {split}"
+        assert np.array_equal(out[split][1], out["1"][1]), f"costs differ with split {split}"
+    assert np.all(np.isfinite(out["1"][0]))
