@@ -154,6 +154,19 @@ def dist_setup():
     return rank, ws, local, dist
 
 
+def job_throughput(dist, units: float, seconds: float, device="cpu") -> float:
+    """Whole-job rate of independent replicas: the units every rank processed,
+    summed, over the slowest rank's time."""
+    if dist is None:
+        return units / seconds
+    import torch
+    u = torch.tensor([units], dtype=torch.float64, device=device)
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(u.item()) / float(t.item())
+
+
 def reduce_max(dist, v: float, device):
     if dist is None:
         return v
@@ -484,7 +497,7 @@ def run_ours(args):
     ctl.sync()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_s = reduce_max(dist, sum(step_ms) / 1e3, dev)
-    value = ws * K * T * M * args.steps / total_s
+    value = job_throughput(dist, K * T * M * args.steps, sum(step_ms) / 1e3, dev)
 
     # ---- end to end through the host-buffer entry point ----------------------
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float32)).pin_memory().numpy()
@@ -499,8 +512,7 @@ def run_ours(args):
         hu[-1] = hout[-1]
         if i >= args.warmup:
             e2e_times.append(el)
-    e2e_total = reduce_max(dist, sum(e2e_times), dev)
-    e2e_value = ws * K * T * M * args.steps / e2e_total
+    e2e_value = job_throughput(dist, K * T * M * args.steps, sum(e2e_times), dev)
 
     if rank != 0:
         dist.destroy_process_group()

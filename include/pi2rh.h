@@ -456,6 +456,15 @@ int pi_debug_reduce(pi_ctx *ctx, const float *cost, const float *phi, const floa
                     const float *u_nominal, int K, int T, float lambda, float *u_out,
                     float *costs_out);
 
+/* Failure path of the device-side waits, exercised without a fault: one
+ * kernel waits on an mbarrier that no thread arrives at, using the same
+ * bounded wait as every kernel, with a limit of limit_ns nanoseconds
+ * (1e3 .. 1e9).  The wait gives up, the kernel flags the timeout in the
+ * context's device error word and returns, so the next pi_sync reports
+ * PI_ERR_TIMEOUT and the context stays usable.  Asynchronous on the
+ * context's stream. */
+int pi_debug_wait_timeout(pi_ctx *ctx, int64_t limit_ns);
+
 /* Tensor-core GEMM core of the tensor-core form, checked on its own:
  * D [128][64] f32 = A [128][K] x B [64][K]^T with A, B fp16 (IEEE binary16,
  * row-major, device), K a multiple of 16 in [16, 160].  One CTA; operands are

@@ -102,6 +102,7 @@ _SIGS = {
     "pi_set_timing": (ctypes.c_int, [_vp, ctypes.c_int]),
     "pi_stage_times": (ctypes.c_int, [_vp, _fp]),
     "pi_debug_tc_gemm": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _vp]),
+    "pi_debug_wait_timeout": (ctypes.c_int, [_vp, ctypes.c_int64]),
     "pi_batch_create": (ctypes.c_int, [ctypes.POINTER(BatchItemC), ctypes.c_int, ctypes.c_int, ctypes.POINTER(_vp)]),
     "pi_batch_set_schedule": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
     "pi_batch_set_stream": (ctypes.c_int, [_vp, _vp]),

@@ -135,6 +135,11 @@ class Controller:
         check(self._lib.pi_sync(self._h))
 
     # ------------------------------------------------------------- staged
+    def debug_wait_timeout(self, limit_ns: int = 5_000_000):
+        """One device-side bounded wait that nothing satisfies (see pi_debug_wait_timeout)."""
+        self._use_current_stream()
+        check(self._lib.pi_debug_wait_timeout(self._h, int(limit_ns)))
+
     def debug_lwpr(self, z):
         self._use_current_stream()
         z = _f32_dev(z, self.device).reshape(-1, NZ)

@@ -631,6 +631,17 @@ int pi_debug_reduce(pi_ctx *c, const float *cost, const float *phi, const float 
                          costs_out);
 }
 
+int pi_debug_wait_timeout(pi_ctx *c, int64_t limit_ns)
+{
+    if (!c) return fail(PI_ERR_INVALID_ARG, "ctx is NULL");
+    if (limit_ns < 1000 || limit_ns > 1000000000) return fail(PI_ERR_INVALID_ARG, "limit_ns outside [1e3, 1e9]");
+    DeviceGuard dg(c->device);
+    PI_CUDA(dg.err, "cudaSetDevice");
+    PI_CUDA(launch_wait_timeout(c->d_err, (unsigned long long)limit_ns, c->stream), "wait kernel launch");
+    c->launches += 1;
+    return PI_OK;
+}
+
 int pi_debug_tc_gemm(pi_ctx *c, const void *A, const void *B, int K, float *D)
 {
     if (!c) return fail(PI_ERR_INVALID_ARG, "ctx is NULL");

@@ -226,7 +226,8 @@ __device__ __forceinline__ unsigned long long globaltimer()
 // Waits for the phase with the given parity to complete.  Gives up (returns
 // false) when *abort is set or after WAIT_LIMIT_NS.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity,
-                                                  volatile int *abort)
+                                                  volatile int *abort,
+                                                  unsigned long long limit_ns = WAIT_LIMIT_NS)
 {
     if (mbar_try_wait(bar, parity)) return true;
     unsigned long long t0 = globaltimer();
@@ -234,7 +235,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
         if (mbar_try_wait(bar, parity)) return true;
         if ((it & 31u) == 0u) {
             if (*abort) return false;
-            if (globaltimer() - t0 > WAIT_LIMIT_NS) return false;
+            if (globaltimer() - t0 > limit_ns) return false;
         }
     }
 }

@@ -146,6 +146,9 @@ struct ReduceArgs {
 cudaError_t launch_scan_lse_batch(const ReduceArgs *args, const int2 *items, int n_items, cudaStream_t s);
 cudaError_t launch_lse_merge_batch(const ReduceArgs *args, const int2 *items, int n_items, cudaStream_t s);
 
+// One bounded device-side wait that is never satisfied (failure-path check).
+cudaError_t launch_wait_timeout(int *err, unsigned long long limit_ns, cudaStream_t s);
+
 // Staged noise kernels.
 cudaError_t launch_noise_raw(uint64_t seed, int K, int T, int m, uint32_t *raw, cudaStream_t s);
 cudaError_t launch_noise_normals(uint64_t seed, int K, int T, int m, float *ctrl, float *model,

@@ -171,7 +171,29 @@ __global__ void noise_normals_kernel(uint64_t seed, int K, int T, int m, float4 
             box_muller4(noise_block(seed, (uint32_t)k, (uint32_t)t, (uint32_t)blk, (uint32_t)m));
 }
 
+// One bounded wait on an mbarrier that no thread ever arrives at: the wait
+// gives up after limit_ns, the kernel flags the timeout in the error word and
+// returns (the failure path of every device-side wait, without a fault).
+__global__ void wait_timeout_kernel(int *err, unsigned long long limit_ns)
+{
+    __shared__ uint64_t bar;
+    __shared__ int abort_flag;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        abort_flag = 0;
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && !mbar_wait_bounded(&bar, 0u, &abort_flag, limit_ns)) atomicOr(err, DEVERR_TIMEOUT_FULL);
+}
+
 }  // namespace
+
+cudaError_t launch_wait_timeout(int *err, unsigned long long limit_ns, cudaStream_t s)
+{
+    wait_timeout_kernel<<<1, 32, 0, s>>>(err, limit_ns);
+    return cudaGetLastError();
+}
 
 int scan_blocks(int K) { return (K + KC - 1) / KC; }
 

@@ -240,6 +240,31 @@ def test_fault_injection_host_side(monkeypatch):
     ctl.sync()
 
 
+def test_device_wait_timeout_reports_and_recovers():
+    """A device-side wait that nothing satisfies gives up after its limit: the
+    kernel returns, pi_sync reports PI_ERR_TIMEOUT once, and the context keeps
+    working (the next update matches a fresh context bitwise)."""
+    import time
+    from paper_1503_00330_b300._lib import PiError, PI_ERR_TIMEOUT
+    p = W.problem(64, 5, 8, seed=3)
+    ctl = _ctrl(p)
+    t0 = time.perf_counter()
+    ctl.debug_wait_timeout(20_000_000)            # 20 ms
+    with pytest.raises(PiError) as ei:
+        ctl.sync()
+    assert ei.value.code == PI_ERR_TIMEOUT
+    assert time.perf_counter() - t0 >= 0.019
+    ctl.sync()                                    # the error word was cleared
+    u, c = ctl.update(p.x0, p.u_nom, p.K, p.T, p.lam, p.sigma_u, p.seed)
+    ctl.sync()
+    fresh = _ctrl(p)
+    u2, c2 = fresh.update(p.x0, p.u_nom, p.K, p.T, p.lam, p.sigma_u, p.seed)
+    fresh.sync()
+    assert torch.equal(u, u2) and torch.equal(c, c2)
+    with pytest.raises(PiError):
+        ctl.debug_wait_timeout(10)                # limit below 1 us is rejected on the host
+
+
 def test_invalid_update_arguments():
     from paper_1503_00330_b300._lib import PiError
     p = W.problem(16, 4, 2, seed=1)
