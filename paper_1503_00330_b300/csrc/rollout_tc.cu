@@ -49,6 +49,9 @@ constexpr int TNF = TC_TILE_FIELDS;     // fields per tile (MMA N)
 constexpr int KF = TC_KF;               // feature columns of phi (S GEMM K)
 constexpr int NCH = TC_CHUNKS_PER_TILE; // chunks per tile
 constexpr int NSLOT = 12;               // chunk slots in the ring
+constexpr int CPG = 4;                  // chunks per copy group (one bulk copy per contiguous run, one barrier pair)
+constexpr int NGRP = NSLOT / CPG;       // groups in the ring
+static_assert(NSLOT % CPG == 0, "the ring holds whole groups");
 constexpr int NCONST = 4;
 constexpr int NEPI = 8;                 // epilogue warps
 constexpr int NTHREADS = (2 + NEPI) * 32;
@@ -70,9 +73,9 @@ constexpr int OFF_YREF = OFF_V + NY * BM * 4;
 constexpr int OFF_Q = OFF_YREF + NY * BM * 4;                   // [BM]
 constexpr int OFF_OBS = OFF_Q + BM * 4;
 constexpr int OFF_BAR = OFF_OBS + MAX_OBS * 8;
-// barriers: full[NSLOT], empty[NSLOT], acc_full[2], acc_empty[2],
+// barriers: full[NGRP], empty[NGRP], acc_full[2], acc_empty[2],
 //           const_full[4], const_empty[4], phi_ready, xfull, xfree
-constexpr int NBARS = 2 * NSLOT + 4 + 2 * NCONST + 3;
+constexpr int NBARS = 2 * NGRP + 4 + 2 * NCONST + 3;
 constexpr int OFF_TSLOT = OFF_BAR + NBARS * 8;
 constexpr int OFF_ABORT = OFF_TSLOT + 8;
 constexpr int SMEM_BYTES = OFF_ABORT + 16;
@@ -168,8 +171,8 @@ __device__ __forceinline__ TcSmem tc_smem(unsigned char *smem)
     S.obs_s = reinterpret_cast<float2 *>(smem + OFF_OBS);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + OFF_BAR);
     S.full = bars;
-    S.empty = bars + NSLOT;
-    S.acc_full = bars + 2 * NSLOT;
+    S.empty = bars + NGRP;
+    S.acc_full = bars + 2 * NGRP;
     S.acc_empty = S.acc_full + 2;
     S.const_full = S.acc_empty + 2;
     S.const_empty = S.const_full + NCONST;
@@ -191,7 +194,7 @@ __device__ __forceinline__ void tc_setup(const TcSmem &S, uint32_t ncl)
         tmem_relinquish();
     }
     if (tid == 0) {
-        for (int i = 0; i < NSLOT; ++i) {
+        for (int i = 0; i < NGRP; ++i) {
             mbar_init(&S.full[i], 1);
             mbar_init(&S.empty[i], 1);
         }
@@ -213,18 +216,25 @@ __device__ __forceinline__ void tc_setup(const TcSmem &S, uint32_t ncl)
     }
 }
 
-// Persistent per-role positions in the rings (carried across work items).
+// Persistent per-role positions in the rings (carried across work items):
+// g counts tiles (constant ring), grp counts chunk groups (coefficient ring).
 struct TcProducer {
-    long long g = 0, q = 0, issued_tiles = 0;
-    int slot = 0;
+    long long g = 0, grp = 0, issued_tiles = 0;
 };
 struct TcIssuer {
-    long long g = 0, q = 0, q_committed = -1, ts = 0;
-    int slot = 0;
+    long long g = 0, grp = 0, grp_committed = -1, ts = 0;
 };
 
 // Producer (lane 0 of warp 0) for one work item -- the tiles of outputs
 // o_begin .. o_begin + n_out - 1 -- ; false after a timeout.
+//
+// The coefficient chunks of a step are one contiguous run of global memory
+// (tiles of consecutive outputs are adjacent), and a bulk copy costs about the
+// same whatever its size up to tens of KB, so chunks travel in groups of CPG:
+// one copy per contiguous run (two when a step boundary falls inside the
+// group), one full/empty barrier pair per group.  Groups never straddle work
+// items.  A tile's constants are issued before the group holding its first
+// chunk.
 template <bool PREDICT>
 __device__ bool tc_producer_item(const TcArgs &a, const TcSmem &S, TcProducer &P, int o_begin, int n_out)
 {
@@ -234,34 +244,45 @@ __device__ bool tc_producer_item(const TcArgs &a, const TcSmem &S, TcProducer &P
     const int G = n_out * a.tiles_per_out;
     const long long tile0 = (long long)o_begin * a.tiles_per_out;
     const int nsteps = PREDICT ? 2 : a.T;
-    long long &g = P.g, &q = P.q, &issued_tiles = P.issued_tiles;
-    int &slot = P.slot;
+    const long long step_chunks = (long long)G * NCH;
+    const long long nchunk = step_chunks * nsteps;
+    const unsigned char *step_src = a.wtiles + tile0 * TC_TILE_BYTES;   // chunk i of a step at + i * 8 KB
     bool ok = true;
-    const long long g0 = g, g_end = g + (long long)G * nsteps;
-    for (; g < g_end && ok; ++g) {
-        const int c = (int)(g & 3);
-        if (g >= 4) ok = mbar_wait_bounded(&const_empty[c], (uint32_t)(((g >> 2) - 1) & 1), abort_flag);
-        if (!ok) break;
-        const long long tile = tile0 + (g - g0) % G;    // (output, tile) in order
-        mbar_arrive_expect_tx(&const_full[c], TC_CONST_BYTES);
-        bulk_g2s(smem + OFF_CONST + c * TC_CONST_BYTES, a.wconst + tile * TC_CONST_BYTES, TC_CONST_BYTES,
-                 &const_full[c]);
-        issued_tiles = g + 1;
-        for (int j = 0; j < NCH; ++j, ++q) {
-            if (q >= NSLOT) {
-                ok = mbar_wait_bounded(&empty[slot], (uint32_t)(((q / NSLOT) - 1) & 1), abort_flag);
-                if (!ok) break;
-            }
-            mbar_arrive_expect_tx(&full[slot], TC_CHUNK_BYTES);
-            bulk_g2s(smem + OFF_RING + slot * TC_CHUNK_BYTES,
-                     a.wtiles + tile * TC_TILE_BYTES + (size_t)j * TC_CHUNK_BYTES, TC_CHUNK_BYTES, &full[slot]);
-            if (++slot == NSLOT) slot = 0;
+    long long next_tile = 0;   // item-local tiles whose constants are issued
+    for (long long c0 = 0; c0 < nchunk && ok; c0 += CPG) {
+        const int n = (int)(nchunk - c0 < CPG ? nchunk - c0 : CPG);
+        const long long last_tile = (c0 + n - 1) / NCH;
+        for (; next_tile <= last_tile; ++next_tile) {
+            const long long gt = P.g;
+            const int c = (int)(gt & 3);
+            if (gt >= 4) ok = mbar_wait_bounded(&const_empty[c], (uint32_t)(((gt >> 2) - 1) & 1), abort_flag);
+            if (!ok) break;
+            const long long tile = tile0 + next_tile % G;
+            mbar_arrive_expect_tx(&const_full[c], TC_CONST_BYTES);
+            bulk_g2s(smem + OFF_CONST + c * TC_CONST_BYTES, a.wconst + tile * TC_CONST_BYTES, TC_CONST_BYTES,
+                     &const_full[c]);
+            P.g = gt + 1;
+            P.issued_tiles = P.g;
         }
+        if (!ok) break;
+        const long long grp = P.grp;
+        const int gs = (int)(grp % NGRP);
+        if (grp >= NGRP) ok = mbar_wait_bounded(&empty[gs], (uint32_t)(((grp / NGRP) - 1) & 1), abort_flag);
+        if (!ok) break;
+        unsigned char *dst = smem + OFF_RING + gs * CPG * TC_CHUNK_BYTES;
+        const long long i0 = c0 % step_chunks;
+        const int n1 = (int)(step_chunks - i0 < n ? step_chunks - i0 : n);
+        mbar_arrive_expect_tx(&full[gs], (uint32_t)(n * TC_CHUNK_BYTES));
+        bulk_g2s(dst, step_src + i0 * TC_CHUNK_BYTES, (uint32_t)(n1 * TC_CHUNK_BYTES), &full[gs]);
+        if (n1 < n) bulk_g2s(dst + n1 * TC_CHUNK_BYTES, step_src, (uint32_t)((n - n1) * TC_CHUNK_BYTES), &full[gs]);
+        P.grp = grp + 1;
     }
     return ok;
 }
 
 // MMA issuer (lane 0 of warp 1) for one work item; false after a timeout.
+// Waits once per chunk group and releases the group's slots with one commit
+// after its last MMA; the group's chunk c sits in ring slot group * CPG + c.
 template <bool PREDICT>
 __device__ bool tc_issuer_item(const TcArgs &a, const TcSmem &S, uint32_t tbase, TcIssuer &I, int n_out)
 {
@@ -271,8 +292,8 @@ __device__ bool tc_issuer_item(const TcArgs &a, const TcSmem &S, uint32_t tbase,
     volatile int *abort_flag = S.abort_flag;
     const int G = n_out * a.tiles_per_out;
     const int nsteps = PREDICT ? 2 : a.T;
-    long long &g = I.g, &q = I.q, &q_committed = I.q_committed, &ts = I.ts;
-    int &slot = I.slot;
+    const long long nchunk = (long long)G * nsteps * NCH;
+    long long &g = I.g, &ts = I.ts;
     const uint32_t idesc = idesc_f16_f32(BM, TNF);
     const uint32_t phi_hi = smem_u32(smem + OFF_PHI_HI), phi_lo = smem_u32(smem + OFF_PHI_LO);
     // descriptors: A = feature tile K step j (rows 2560 B apart), B = a
@@ -285,6 +306,11 @@ __device__ bool tc_issuer_item(const TcArgs &a, const TcSmem &S, uint32_t tbase,
         al[j] = smem_desc_kmajor(phi_lo + j * 256, 128, 16 * KF);
     }
     const uint64_t b0 = smem_desc_kmajor(smem_u32(smem + OFF_RING), 128, 256);
+    // group state: counter, ring group, its phase, chunk within it
+    long long grp = I.grp;
+    uint32_t gs = (uint32_t)(grp % NGRP), gph = (uint32_t)((grp / NGRP) & 1);
+    int cg = 0;
+    long long ci = 0;   // chunks of this item consumed
     bool ok = true;
     for (int t = 0; t < nsteps && ok; ++t, ++ts) {
         ok = mbar_wait_bounded(phi_ready, (uint32_t)(ts & 1), abort_flag);
@@ -297,10 +323,12 @@ __device__ bool tc_issuer_item(const TcArgs &a, const TcSmem &S, uint32_t tbase,
             const uint32_t dS = tbase + buf * 256, dY = dS + 128;
 #pragma unroll
             for (int j = 0; j < NCH; ++j) {
-                if (ok) ok = mbar_wait_bounded(&full[slot], (uint32_t)((q / NSLOT) & 1), abort_flag);
-                if (ok) {
+                if (cg == 0 && ok) {
+                    ok = mbar_wait_bounded(&full[gs], gph, abort_flag);
                     tc_fence_after();
-                    const uint64_t bh = b0 + (uint64_t)((slot * TC_CHUNK_BYTES) >> 4);
+                }
+                if (ok) {
+                    const uint64_t bh = b0 + (uint64_t)((gs * CPG + cg) * (TC_CHUNK_BYTES >> 4));
                     const uint64_t bl = bh + (uint64_t)(TC_HALF_CHUNK >> 4);
                     if (j < NCH - 1) {
                         mma_f16(dS, ah[j], bh, idesc, j > 0);
@@ -311,15 +339,25 @@ __device__ bool tc_issuer_item(const TcArgs &a, const TcSmem &S, uint32_t tbase,
                         mma_f16(dY, ah[0], bl, idesc, true);
                         mma_f16(dY, al[0], bh, idesc, true);
                     }
-                    mma_commit(&empty[slot]);
-                    q_committed = q;
                 }
-                ++q;
-                if (++slot == NSLOT) slot = 0;
+                ++ci;
+                if (++cg == CPG || ci == nchunk) {
+                    if (ok) {
+                        mma_commit(&empty[gs]);
+                        I.grp_committed = grp;
+                    }
+                    cg = 0;
+                    ++grp;
+                    if (++gs == NGRP) {
+                        gs = 0;
+                        gph ^= 1;
+                    }
+                }
             }
             if (ok) mma_commit(&acc_full[buf]);
         }
     }
+    I.grp = grp;
     return ok;
 }
 
@@ -587,8 +625,8 @@ __device__ __forceinline__ void tc_drain(const TcArgs &a, const TcSmem &S, const
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (warp == 0 && lane == 0) {
         // keep the CTA alive until every copy issued has landed
-        for (long long r = (P.q > NSLOT ? P.q - NSLOT : 0); r < P.q; ++r)
-            if (!mbar_wait_drain(&S.full[r % NSLOT], (uint32_t)((r / NSLOT) & 1))) atomicOr(a.err, DEVERR_TIMEOUT_DRAIN);
+        for (long long r = (P.grp > NGRP ? P.grp - NGRP : 0); r < P.grp; ++r)
+            if (!mbar_wait_drain(&S.full[r % NGRP], (uint32_t)((r / NGRP) & 1))) atomicOr(a.err, DEVERR_TIMEOUT_DRAIN);
         for (long long g = (P.issued_tiles > NCONST ? P.issued_tiles - NCONST : 0); g < P.issued_tiles; ++g)
             if (!mbar_wait_drain(&S.const_full[g & 3], (uint32_t)((g >> 2) & 1))) atomicOr(a.err, DEVERR_TIMEOUT_DRAIN);
     }
@@ -597,9 +635,9 @@ __device__ __forceinline__ void tc_drain(const TcArgs &a, const TcSmem &S, const
         if (issuer_ok && I.g > 0 &&
             !mbar_wait_drain(&S.acc_full[(I.g - 1) & 1], (uint32_t)(((I.g - 1) >> 1) & 1)))
             atomicOr(a.err, DEVERR_TIMEOUT_DRAIN);
-        if (!issuer_ok && I.q_committed >= 0) {
-            const long long r = I.q_committed;   // the last chunk commit tracks every MMA before it
-            if (!mbar_wait_drain(&S.empty[r % NSLOT], (uint32_t)((r / NSLOT) & 1))) atomicOr(a.err, DEVERR_TIMEOUT_DRAIN);
+        if (!issuer_ok && I.grp_committed >= 0) {
+            const long long r = I.grp_committed;   // the last group commit tracks every MMA before it
+            if (!mbar_wait_drain(&S.empty[r % NGRP], (uint32_t)((r / NGRP) & 1))) atomicOr(a.err, DEVERR_TIMEOUT_DRAIN);
         }
     }
 }
