@@ -459,27 +459,36 @@ __device__ void tc_epilogue_item(const TcArgs &a, const TcSmem &S, uint32_t tbas
                         if (lane == 0) mbar_arrive(&acc_empty[buf]);
                     }
                     if (!aborted) {
+                        // two fields per packed FP32x2 operation (even / odd columns
+                        // accumulate separately and are added at the end of the chunk)
+                        const float2 *cs2 = reinterpret_cast<const float2 *>(cs + 16 * ch);
+                        const float2 *cy2 = reinterpret_cast<const float2 *>(cy + 16 * ch);
+                        const float2 *cv2 = reinterpret_cast<const float2 *>(cv + 16 * ch);
+                        float2 sp[8];
                         float sm = -INFINITY;
 #pragma unroll
-                        for (int i = 0; i < 16; ++i) {
-                            sv[i] += cs[16 * ch + i];
-                            sm = fmaxf(sm, sv[i]);
+                        for (int i = 0; i < 8; ++i) {
+                            sp[i] = __fadd2_rn(make_float2(sv[2 * i], sv[2 * i + 1]), cs2[i]);
+                            sm = fmaxf(sm, fmaxf(sp[i].x, sp[i].y));
                         }
                         const float mn = fmaxf(st.m, sm);
                         const float mns = mn == -INFINITY ? 0.0f : mn;
                         const float sc = ex2(st.m - mns);
-                        float s0 = st.s0 * sc, s1 = st.s1 * sc, s2 = st.s2 * sc, s3 = st.s3 * sc;
+                        const float2 nm = make_float2(-mns, -mns), ny = make_float2(-yref, -yref);
+                        float2 s0 = make_float2(st.s0 * sc, 0.0f), s1 = make_float2(st.s1 * sc, 0.0f);
+                        float2 s2 = make_float2(st.s2 * sc, 0.0f), s3 = make_float2(st.s3 * sc, 0.0f);
 #pragma unroll
-                        for (int i = 0; i < 16; ++i) {
-                            const float w = ex2(sv[i] - mns);
-                            const float e = yv[i] + (cy[16 * ch + i] - yref);
-                            const float we = w * e;
-                            s0 += w;
-                            s1 += we;
-                            s2 = fmaf(we, e, s2);
-                            s3 = fmaf(w, cv[16 * ch + i], s3);
+                        for (int i = 0; i < 8; ++i) {
+                            const float2 d = __fadd2_rn(sp[i], nm);
+                            const float2 w = make_float2(ex2(d.x), ex2(d.y));
+                            const float2 e = __fadd2_rn(make_float2(yv[2 * i], yv[2 * i + 1]), __fadd2_rn(cy2[i], ny));
+                            const float2 we = __fmul2_rn(w, e);
+                            s0 = __fadd2_rn(s0, w);
+                            s1 = __fadd2_rn(s1, we);
+                            s2 = __ffma2_rn(we, e, s2);
+                            s3 = __ffma2_rn(w, cv2[i], s3);
                         }
-                        st = Soft{mn, s0, s1, s2, s3};
+                        st = Soft{mn, s0.x + s0.y, s1.x + s1.y, s2.x + s2.y, s3.x + s3.y};
                     }
                 }
                 __syncwarp();
