@@ -222,39 +222,23 @@ int pi_batch_create(const pi_batch_item *items, int n, int precision, pi_batch *
         float *phi = reinterpret_cast<float *>(base + align256(K * T * 4) + align256(K * T * 16));
         double *part = reinterpret_cast<double *>(base + align256(K * T * 4) + align256(K * T * 16) + align256(K * 4));
         RolloutArgs &a = b->h_args[i];
-        a = RolloutArgs{};
-        a.rec = c->d_rec;
-        a.P = c->P;
-        a.stages_per_out = c->spo;
-        a.cost = c->cost;
-        a.dt = c->dt;
+        a = ctx_rollout_args(c);
         a.K = it.K;
         a.T = it.T;
-        a.M = c->opts.M;
-        a.model_noise = c->opts.model_noise == PI_NOISE_SAMPLED ? 1 : 0;
         a.x0 = it.x0;
         a.u_nom = it.u_nominal;
         a.cost_tk = cost;
         a.eps_tk = eps;
         a.phi = phi;
-        a.err = c->d_err;
         TcArgs &t = b->h_targs[i];
-        t = TcArgs{};
-        t.wtiles = c->d_wtiles;
-        t.wconst = c->d_wconst;
-        t.tiles_per_out = c->tiles_per_out;
-        t.cost = c->cost;
-        t.dt = c->dt;
+        t = ctx_tc_args(c);
         t.K = it.K;
         t.T = it.T;
-        t.M = c->opts.M;
-        t.model_noise = a.model_noise;
         t.x0 = it.x0;
         t.u_nom = it.u_nominal;
         t.cost_tk = cost;
         t.eps_tk = eps;
         t.phi = phi;
-        t.err = c->d_err;
         ReduceArgs &r = b->h_rargs[i];
         r = ReduceArgs{cost, phi, eps, it.K, it.T, (double)c->dt, 1.0, it.costs_out, part, it.u_nominal, it.u_out};
         const int nblk = scan_blocks(it.K);
