@@ -110,6 +110,11 @@ struct TcBatchArgs {
 
 cudaError_t launch_rollout_tc(const TcArgs &a, cudaStream_t s);
 cudaError_t launch_rollout_tc_batch(const TcBatchArgs &b, int grid, cudaStream_t s);
+// Non-persistent form of the batch launch: one item per CTA or per cluster of
+// `split` CTAs (outputs split as in the single-controller kernel), one wave.
+// tc_group_split(n) = the split that keeps n items in one wave (1 = none fits).
+int tc_group_split(int n_items);
+cudaError_t launch_rollout_tc_group(const TcBatchArgs &b, int split, cudaStream_t s);
 cudaError_t launch_predict_tc(const TcArgs &a, cudaStream_t s);
 const char *tc_launch_diag();   // resources of the tensor-core kernel (for error messages)
 

@@ -657,14 +657,13 @@ __device__ __forceinline__ void tc_flag_abort(const TcArgs &a, const TcSmem &S, 
     *S.abort_flag = 1;
 }
 
-// Single-controller kernel.  NSPLIT = 1: one CTA per 128-slot block.
-// NSPLIT = 2, 3, 4 (rollouts only): launched in clusters of NSPLIT CTAs that
-// share one slot block and split its 12 outputs (see tc_epilogue_item).
+// One CTA's whole life for the 128-slot block at slot_base: set-up, the
+// three roles, drain, tensor-memory release.  With NSPLIT > 1 the CTA is one
+// of the NSPLIT CTAs of a cluster that share the block and split its outputs.
 template <bool PREDICT, int NSPLIT>
-__global__ void __launch_bounds__(NTHREADS, 1) rollout_tc_kernel(const __grid_constant__ TcArgs a)
+__device__ __forceinline__ void tc_cta(const TcArgs &a, long long slot_base, unsigned char *smem)
 {
     static_assert(NSPLIT == 1 || !PREDICT, "prediction mode is not split");
-    extern __shared__ __align__(1024) unsigned char smem[];
     const TcSmem S = tc_smem(smem);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     constexpr uint32_t ncl = NSPLIT;
@@ -693,7 +692,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) rollout_tc_kernel(const __grid_co
     } else {
         long long g = 0;
         bool aborted = false;
-        tc_epilogue_item<PREDICT, NSPLIT>(a, S, tbase, (long long)(blockIdx.x / ncl) * BM, g, aborted, rank);
+        tc_epilogue_item<PREDICT, NSPLIT>(a, S, tbase, slot_base, g, aborted, rank);
         if (aborted) tc_flag_abort(a, S, DEVERR_TIMEOUT_FULL);
     }
     tc_drain(a, S, P, I, issuer_ok);
@@ -705,6 +704,30 @@ __global__ void __launch_bounds__(NTHREADS, 1) rollout_tc_kernel(const __grid_co
         tmem_dealloc(tbase, TMEM_COLS);
     }
     if (ncl > 1) cluster_sync_all();   // no CTA leaves while another may still write into it
+}
+
+// Single-controller kernel.  NSPLIT = 1: one CTA per 128-slot block.
+// NSPLIT = 2, 3, 4 (rollouts only): launched in clusters of NSPLIT CTAs that
+// share one slot block and split its 12 outputs (see tc_epilogue_item).
+template <bool PREDICT, int NSPLIT>
+__global__ void __launch_bounds__(NTHREADS, 1) rollout_tc_kernel(const __grid_constant__ TcArgs a)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    tc_cta<PREDICT, NSPLIT>(a, (long long)(blockIdx.x / NSPLIT) * BM, smem);
+}
+
+// Group form: one (controller, 128-slot block) item per CTA (NSPLIT = 1) or
+// per cluster of NSPLIT CTAs, all items in one wave; the arguments come from
+// the device table.  Used when a batch's items alone would leave SMs idle.
+template <int NSPLIT>
+__global__ void __launch_bounds__(NTHREADS, 1) rollout_tc_group_kernel(const __grid_constant__ TcBatchArgs b)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ TcArgs s_args;
+    const int2 it = b.items[blockIdx.x / NSPLIT];
+    if (threadIdx.x == 0) s_args = b.args[it.x];
+    __syncthreads();
+    tc_cta<false, NSPLIT>(s_args, (long long)it.y * BM, smem);
 }
 
 // Persistent batched form (see rollout_fp32_batch_kernel): CTAs claim
@@ -852,6 +875,50 @@ cudaError_t launch_split(const TcArgs &a, long long blocks, cudaStream_t s)
     return cudaLaunchKernelEx(&cfg, rollout_tc_kernel<false, NSPLIT>, a);
 }
 
+template <int NSPLIT>
+cudaError_t prepare_group()
+{
+    static bool done = false;
+    if (done) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(rollout_tc_group_kernel<NSPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         SMEM_BYTES);
+    if (e == cudaSuccess) done = true;
+    return e;
+}
+
+template <int NSPLIT>
+bool group_clusters_resident(long long items)
+{
+    if (prepare_group<NSPLIT>() != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    split_config(cfg, at, items, NSPLIT, nullptr);
+    int clusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&clusters, rollout_tc_group_kernel<NSPLIT>, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return clusters >= items;
+}
+
+template <int NSPLIT>
+cudaError_t launch_group(const TcBatchArgs &b, cudaStream_t s)
+{
+    cudaError_t e = prepare_group<NSPLIT>();
+    if (e != cudaSuccess) return e;
+    if (NSPLIT == 1) {
+        rollout_tc_group_kernel<1><<<(unsigned)b.n_items, NTHREADS, SMEM_BYTES, s>>>(b);
+        return cudaGetLastError();
+    }
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    split_config(cfg, at, b.n_items, NSPLIT, s);
+    return cudaLaunchKernelEx(&cfg, rollout_tc_group_kernel<NSPLIT>, b);
+}
+
 cudaError_t check_tc_args(const TcArgs &a)
 {
     return a.cost.n_obs > MAX_OBS || a.tiles_per_out <= 0 ? cudaErrorInvalidValue : cudaSuccess;
@@ -885,6 +952,33 @@ cudaError_t launch_predict_tc(const TcArgs &a, cudaStream_t s)
     if (blocks <= 0 || blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
     rollout_tc_kernel<true, 1><<<(unsigned)blocks, NTHREADS, SMEM_BYTES, s>>>(a);
     return cudaGetLastError();
+}
+
+int tc_group_split(int n_items)
+{
+    if (n_items <= 0) return 1;
+    if (const char *e = getenv("PI2RH_TC_SPLIT")) {
+        const int v = atoi(e);
+        if (v >= 1 && v <= 4) return v;
+    }
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if ((long long)n_items * 4 <= sms && group_clusters_resident<4>(n_items)) return 4;
+    if ((long long)n_items * 3 <= sms && group_clusters_resident<3>(n_items)) return 3;
+    if ((long long)n_items * 2 <= sms && group_clusters_resident<2>(n_items)) return 2;
+    return 1;
+}
+
+cudaError_t launch_rollout_tc_group(const TcBatchArgs &b, int split, cudaStream_t s)
+{
+    if (b.n_items <= 0) return cudaErrorInvalidValue;
+    switch (split) {
+    case 4: return launch_group<4>(b, s);
+    case 3: return launch_group<3>(b, s);
+    case 2: return launch_group<2>(b, s);
+    default: return launch_group<1>(b, s);
+    }
 }
 
 bool g_tc_batch_attr = false;

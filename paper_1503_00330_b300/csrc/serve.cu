@@ -386,7 +386,9 @@ int pi_server::launch(Lane &L)
         if (tc) {
             TcBatchArgs tb{reinterpret_cast<const TcArgs *>(d + lay.args), reinterpret_cast<const int2 *>(d + lay.ritems),
                            nr, d_ctl};
-            e = launch_rollout_tc_batch(tb, grid, s);
+            // a small group runs as one wave of clusters that split each block's outputs
+            const int split = tc_group_split(nr);
+            e = split > 1 ? launch_rollout_tc_group(tb, split, s) : launch_rollout_tc_batch(tb, grid, s);
         } else {
             BatchArgs fb{reinterpret_cast<const RolloutArgs *>(d + lay.args), reinterpret_cast<const int2 *>(d + lay.ritems),
                          nr, d_ctl, d_ctl + 1};

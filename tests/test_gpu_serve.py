@@ -233,3 +233,19 @@ def test_trace_replay():
     srv.drain()
     assert np.array_equal(srv.state_save()["counter"].astype(np.int64), counts)
     srv.close()
+
+
+@pytest.mark.parametrize("split", ["1", "2", "3", "4"])
+def test_served_equals_alone_for_each_group_split(monkeypatch, split):
+    """Small groups run as one wave of clusters that split each block's outputs
+    (split 1: the persistent batched kernel); every split serves the same bits."""
+    monkeypatch.setenv("PI2RH_TC_SPLIT", split)
+    ctl = _controller("tc")
+    srv = _server(ctl, len(AGENTS), max_inflight=2, max_group=3)
+    got = _serve_all(srv, 2)
+    srv.close()
+    for a in range(len(AGENTS)):
+        ref, _ = _alone_sequence(ctl, a, 2)
+        for r in range(2):
+            assert np.array_equal(got[(a, r)][0], ref[r][0]), f"split {split}, agent {a} round {r}"
+            assert np.array_equal(got[(a, r)][1], ref[r][1]), f"split {split}, agent {a} round {r}"
