@@ -177,16 +177,28 @@ def reduce_max(dist, v: float, device):
 
 
 def cpu_baseline(p, k_sample: int):
-    """FP64 oracle on the first k_sample rollouts of one update of the workload."""
+    """FP64 oracle on the first k_sample rollouts of one update of the workload
+    (all host threads), and on a 1/8 sample on one thread."""
     from oracle import oracle as O
     O.build()
     t0 = time.perf_counter()
     O.pi_update(p.model, p.cost, p.x0, p.u_nom, k_sample, p.T, p.lam, p.sigma_u, p.seed, M=p.M,
                 model_noise=p.model_noise)
     el = time.perf_counter() - t0
-    return {"value": k_sample * p.T * p.M / el, "unit": UNIT, "cores": O.max_threads(), "kind": "oracle",
+    cores = O.max_threads()
+    k1 = max(k_sample // 8, 1)
+    O.set_threads(1)
+    try:
+        t1 = time.perf_counter()
+        O.pi_update(p.model, p.cost, p.x0, p.u_nom, k1, p.T, p.lam, p.sigma_u, p.seed, M=p.M,
+                    model_noise=p.model_noise)
+        el1 = time.perf_counter() - t1
+    finally:
+        O.set_threads(cores)
+    return {"value": k_sample * p.T * p.M / el, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"one update of {k_sample} of the {p.K} rollouts (T={p.T}, L={p.model.L}, M={p.M}), "
-                      f"{el:.2f} s"}
+                      f"{el:.2f} s",
+            "single_thread": {"value": k1 * p.T * p.M / el1, "sample": f"{k1} rollouts on 1 thread, {el1:.2f} s"}}
 
 
 def run_reference(args):
@@ -426,8 +438,19 @@ def run_serving(args):
                 "all_ok": bool(np.all(rec["status"] == 0))}
 
     full = run(50.0, args.serve_seconds, seed=1)
-    half_rate = 0.5 * full["requests_per_s"] / n_quad
-    half = run(half_rate, max(args.serve_seconds, 160.0 / (0.5 * full["requests_per_s"])), seed=2)
+    cap = full["requests_per_s"]
+    half_rate = 0.5 * cap / n_quad
+    half = run(half_rate, max(args.serve_seconds, 160.0 / (0.5 * cap)), seed=2)
+    sweep = []
+    for i, frac in enumerate(args.serve_sweep):
+        if frac == 0.5:
+            pt = half
+        else:
+            pt = run(frac * cap / n_quad, max(args.serve_seconds, 120.0 / (frac * cap)), seed=3 + i)
+        sweep.append({"load": frac, "offered_hz_per_quad": pt["offered_hz_per_quad"],
+                      "requests_per_s": pt["requests_per_s"], "latency_ms": pt["latency_ms"],
+                      "queue_ms": pt["queue_ms"], "group_size_mean": pt["group_size"]["mean"],
+                      "rollout_steps_per_s": pt["rollout_steps_per_s"]})
     srv.close()
     line = {"metric": METRIC, "value": full["rollout_steps_per_s"], "unit": UNIT, "n_gpus": 1,
             "steps": full["served"], "warmup": args.warmup, "ms_per_step": 1e3 / full["requests_per_s"],
@@ -442,6 +465,7 @@ def run_serving(args):
                     "note": "requests enter on the host and plans return to pinned host memory inside the span"},
             "gpu_launches": full["gpu_launches"], "roofline": full["roofline"],
             "latency_ms": full["latency_ms"], "at_offered_rate": full, "at_half_capacity": half,
+            "load_sweep": {"capacity_requests_per_s": cap, "points": sweep},
             "clocks": full["clocks"]}
     print(json.dumps(line), flush=True)
 
@@ -565,6 +589,8 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=3.0, help="serving: trace length at the offered rate")
     ap.add_argument("--serve-lanes", type=int, default=2, help="serving: groups on the GPU at once")
     ap.add_argument("--serve-group", type=int, default=64, help="serving: most requests per group")
+    ap.add_argument("--serve-sweep", type=float, nargs="*", default=[0.25, 0.5, 0.75, 0.9],
+                    help="serving: offered loads (fractions of the measured capacity) for the latency sweep")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

@@ -98,6 +98,8 @@ def _load():
                                       _dp, ctypes.c_uint64, ctypes.c_int, _dp, _dp]
         lib.orc_pi_update.restype = ctypes.c_int
         lib.orc_max_threads.restype = ctypes.c_int
+        lib.orc_set_threads.argtypes = [ctypes.c_int]
+        lib.orc_set_threads.restype = None
         _lib = lib
     return _lib
 
@@ -267,3 +269,8 @@ def pi_update(model, cost_params, x0, u_nom, K, T, lam, sigma_u, seed, M=1, mode
 
 def max_threads() -> int:
     return int(_load().orc_max_threads())
+
+
+def set_threads(n: int) -> None:
+    """Threads of the rollout loop from now on (OpenMP)."""
+    _load().orc_set_threads(int(n))

@@ -380,3 +380,14 @@ int orc_max_threads(void)
     return 1;
 #endif
 }
+
+/* Sets the threads of the rollout loop (the single-thread CPU timing). */
+void orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    extern void omp_set_num_threads(int);
+    omp_set_num_threads(n > 0 ? n : 1);
+#else
+    (void)n;
+#endif
+}

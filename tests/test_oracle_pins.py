@@ -481,3 +481,27 @@ def test_golden_tiny_update(oracle):
     u, c = oracle.pi_update(p.model, p.cost, p.x0, p.u_nom, p.K, p.T, p.lam, p.sigma_u, p.seed)
     np.testing.assert_allclose(u, np.array(gold["u_out"]), rtol=1e-12, atol=1e-14)
     np.testing.assert_allclose(c, np.array(gold["costs_out"]), rtol=1e-12)
+
+
+def test_update_converges_as_inverse_sqrt_K(oracle):
+    """Eq. 2 is a self-normalised Monte Carlo estimate over K rollouts: its
+    error against the large-K limit shrinks like K^(-1/2).  The reference is
+    one update with K = 65536; the error at K = 64 ... 4096 is the RMS over 8
+    independent seeds; the fitted log-log slope must be -1/2 within 0.15.
+    Noise shared between rollouts would break the rate; weights that ignored
+    the costs would put the limit at u_nom + E[eps] = 0."""
+    p = W.problem(16, 6, 2, seed=9, n_obs=2)
+    p.u_nom = np.zeros((p.T, 4), np.float32)
+    lam = 0.5
+    ref, _ = oracle.pi_update(p.model, p.cost, p.x0, p.u_nom, 65536, p.T, lam, p.sigma_u, 10_000)
+    Ks = [64, 256, 1024, 4096]
+    rms = []
+    for K in Ks:
+        errs = [oracle.pi_update(p.model, p.cost, p.x0, p.u_nom, K, p.T, lam, p.sigma_u, 100 + s)[0] - ref
+                for s in range(8)]
+        rms.append(np.sqrt(np.mean(np.square(errs))))
+    slope = np.polyfit(np.log(Ks), np.log(rms), 1)[0]
+    assert -0.65 <= slope <= -0.35, (rms, slope)
+    # the limit is not u_nom + E[eps] = 0: the costs move it by many standard
+    # errors of the K = 65536 reference (about rms(4096) * sqrt(4096 / 65536))
+    assert np.abs(ref).max() > 5 * rms[-1] * np.sqrt(4096 / 65536)
