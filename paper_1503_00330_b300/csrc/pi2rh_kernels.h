@@ -1,12 +1,29 @@
 // pi2rh_kernels.h -- host-side launch interface of the kernels (internal).
 #pragma once
 
+#include <atomic>
 #include <cstdint>
 #include <cuda_runtime.h>
 
 #include "pi2rh_device.cuh"
 
 namespace pi2rh {
+
+// Raises a kernel's dynamic shared-memory limit to `bytes` once per device
+// (devices 0-63 are remembered in `done`; concurrent first calls both set the
+// same value, which is harmless).
+template <typename Kernel>
+inline cudaError_t set_smem_once(std::atomic<uint64_t> &done, Kernel *kernel, int bytes)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const uint64_t bit = dev >= 0 && dev < 64 ? 1ull << dev : 0ull;
+    if (bit && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess && bit) done.fetch_or(bit, std::memory_order_release);
+    return e;
+}
 
 // Arguments of the fused rollout kernel (also used in prediction-only mode).
 struct RolloutArgs {

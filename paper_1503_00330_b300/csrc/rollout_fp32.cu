@@ -488,18 +488,14 @@ __global__ void __launch_bounds__(NTHREADS, 1) rollout_fp32_batch_kernel(const _
             if (!mbar_wait_drain(&S.full[r % NSTAGE], (uint32_t)((r / NSTAGE) & 1))) atomicOr(b.err, DEVERR_TIMEOUT_DRAIN);
 }
 
-bool g_attr_set[2] = {false, false};
+std::atomic<uint64_t> g_attr_set[2];
 
 template <bool PREDICT>
 cudaError_t launch_impl(const RolloutArgs &a, cudaStream_t s, long long slots)
 {
     if (a.cost.n_obs > MAX_OBS || a.P <= 0 || a.stages_per_out <= 0) return cudaErrorInvalidValue;
-    if (!g_attr_set[PREDICT]) {
-        cudaError_t e = cudaFuncSetAttribute(rollout_fp32_kernel<PREDICT>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-        if (e != cudaSuccess) return e;
-        g_attr_set[PREDICT] = true;
-    }
+    cudaError_t e = set_smem_once(g_attr_set[PREDICT], rollout_fp32_kernel<PREDICT>, SMEM_BYTES);
+    if (e != cudaSuccess) return e;
     const long long blocks = (slots + SLOTS - 1) / SLOTS;
     if (blocks <= 0 || blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
     // prediction of a few rows (the receding-horizon plant step): one CTA per
@@ -522,16 +518,12 @@ cudaError_t launch_predict_fp32(const RolloutArgs &a, cudaStream_t s)
     return launch_impl<true>(a, s, (long long)a.n_pred);
 }
 
-bool g_batch_attr = false;
+std::atomic<uint64_t> g_batch_attr;
 
 cudaError_t launch_rollout_fp32_batch(const BatchArgs &b, int grid, cudaStream_t s)
 {
-    if (!g_batch_attr) {
-        cudaError_t e = cudaFuncSetAttribute(rollout_fp32_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             SMEM_BYTES);
-        if (e != cudaSuccess) return e;
-        g_batch_attr = true;
-    }
+    cudaError_t e = set_smem_once(g_batch_attr, rollout_fp32_batch_kernel, SMEM_BYTES);
+    if (e != cudaSuccess) return e;
     if (grid <= 0) return cudaErrorInvalidValue;
     rollout_fp32_batch_kernel<<<grid, NTHREADS, SMEM_BYTES, s>>>(b);
     return cudaGetLastError();

@@ -806,11 +806,11 @@ void split_config(cudaLaunchConfig_t &cfg, cudaLaunchAttribute *at, long long bl
 template <bool PREDICT, int NSPLIT>
 cudaError_t prepare_tc()
 {
-    static bool done = false;
-    if (done) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(rollout_tc_kernel<PREDICT, NSPLIT>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    static std::atomic<uint64_t> done;
+    cudaError_t e = set_smem_once(done, rollout_tc_kernel<PREDICT, NSPLIT>, SMEM_BYTES);
     if (e != cudaSuccess) return e;
+    static std::atomic<bool> checked{false};
+    if (checked.load(std::memory_order_acquire)) return cudaSuccess;
     cudaFuncAttributes fa;
     e = cudaFuncGetAttributes(&fa, rollout_tc_kernel<PREDICT, NSPLIT>);
     if (e != cudaSuccess) return e;
@@ -819,7 +819,7 @@ cudaError_t prepare_tc()
              fa.numRegs, fa.maxThreadsPerBlock, SMEM_BYTES, fa.maxDynamicSharedSizeBytes, fa.sharedSizeBytes,
              fa.localSizeBytes);
     if (fa.maxThreadsPerBlock < NTHREADS) return cudaErrorLaunchOutOfResources;
-    done = true;
+    checked.store(true, std::memory_order_release);
     return cudaSuccess;
 }
 
@@ -878,12 +878,8 @@ cudaError_t launch_split(const TcArgs &a, long long blocks, cudaStream_t s)
 template <int NSPLIT>
 cudaError_t prepare_group()
 {
-    static bool done = false;
-    if (done) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(rollout_tc_group_kernel<NSPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         SMEM_BYTES);
-    if (e == cudaSuccess) done = true;
-    return e;
+    static std::atomic<uint64_t> done;
+    return set_smem_once(done, rollout_tc_group_kernel<NSPLIT>, SMEM_BYTES);
 }
 
 template <int NSPLIT>
@@ -981,16 +977,12 @@ cudaError_t launch_rollout_tc_group(const TcBatchArgs &b, int split, cudaStream_
     }
 }
 
-bool g_tc_batch_attr = false;
+std::atomic<uint64_t> g_tc_batch_attr;
 
 cudaError_t launch_rollout_tc_batch(const TcBatchArgs &b, int grid, cudaStream_t s)
 {
-    if (!g_tc_batch_attr) {
-        cudaError_t e = cudaFuncSetAttribute(rollout_tc_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             SMEM_BYTES);
-        if (e != cudaSuccess) return e;
-        g_tc_batch_attr = true;
-    }
+    cudaError_t e = set_smem_once(g_tc_batch_attr, rollout_tc_batch_kernel, SMEM_BYTES);
+    if (e != cudaSuccess) return e;
     if (grid <= 0) return cudaErrorInvalidValue;
     rollout_tc_batch_kernel<<<grid, NTHREADS, SMEM_BYTES, s>>>(b);
     return cudaGetLastError();

@@ -748,9 +748,13 @@ int pi_server_create(pi_ctx *ctx, const pi_server_opts *opts, pi_server **out)
     s->agent_busy.assign(na, 0);
     s->agent_outstanding.assign(na, 0);
     s->mark.assign(na, 0);
-    pi_server *raw = s.release();
-    raw->worker = std::thread([raw] { raw->run(); });
-    *out = raw;
+    try {
+        s->worker = std::thread([srv = s.get()] { srv->run(); });
+    } catch (const std::exception &ex) {
+        free_server(s.get());
+        return sfail(PI_ERR_INTERNAL, std::string("cannot start the scheduler thread: ") + ex.what());
+    }
+    *out = s.release();
     return PI_OK;
 }
 
