@@ -264,6 +264,28 @@ def form_roofline(precision, rollout_ms, K, T, M, L, dev, peaks, workload):
             "rollout_ms_per_launch": statistics.mean(rollout_ms)}
 
 
+def reduction_rooflines(scan_ms, merge_ms, K, T, peaks):
+    """Achieved bandwidth of the cost-to-go/LSE scan and of the merge (memory-bound kernels).
+
+    Bytes are algorithmic: the scan reads cost [T][K] f32 and eps [T][K] float4 and phi [K],
+    writes costs_out [K] and the LSE partials [K/64][T][6] f64; the merge reads the partials
+    and u_nom [T][4] and writes u_out [T][4].  Their inputs were written by the rollout kernel
+    just before (about 20 B per rollout-step), so they are mostly L2-resident: the fraction is
+    given against the measured HBM copy peak, and can exceed what DRAM alone would allow."""
+    nblk = -(-K // 64)
+    scan_b = K * T * 20 + K * 8 + nblk * T * 48
+    merge_b = nblk * T * 48 + T * 32
+    hbm = float(peaks.get("hbm_gbs", 6492.1))
+    out = {}
+    for name, ms, b in (("scan_lse_kernel", scan_ms, scan_b), ("lse_merge_kernel", merge_ms, merge_b)):
+        avg = statistics.mean(ms)
+        gbs = b / (avg / 1e3) / 1e9
+        out[name] = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                     "bytes_per_launch": b, "ms_per_launch": avg,
+                     "data": "inputs written by the rollout kernel just before (L2-resident for this size)"}
+    return out
+
+
 def time_form(precision, p, args, dev):
     """The receding-horizon loop of `p` timed the same way with the other form."""
     import torch
@@ -278,7 +300,7 @@ def time_form(precision, p, args, dev):
     costs = torch.empty(K, dtype=torch.float32, device=dev)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
-    rollout_ms, step_ms = [], []
+    rollout_ms, step_ms, scan_ms, merge_ms = [], [], [], []
     for i in range(args.warmup + args.steps):
         flush.zero_()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -286,10 +308,12 @@ def time_form(precision, p, args, dev):
         ctl.update(x0, ua, K, T, p.lam, p.sigma_u, p.seed + i, u_out=ub, costs_out=costs)
         ctl.rh_advance(x0, ub, ua)
         b.record(stream)
-        r = ctl.stage_times()[0]
+        st = ctl.stage_times()
         b.synchronize()
         if i >= args.warmup:
-            rollout_ms.append(r)
+            rollout_ms.append(st[0])
+            scan_ms.append(st[1])
+            merge_ms.append(st[2])
             step_ms.append(a.elapsed_time(b))
     ctl.sync()
     ctl.close()
@@ -297,7 +321,7 @@ def time_form(precision, p, args, dev):
     roof = form_roofline(precision, rollout_ms, K, T, M, L, dev, measured_peaks(), args.workload)
     roof["rollout_share_of_step"] = sum(rollout_ms) / sum(step_ms)
     return {"value": K * T * M * args.steps / total_s, "ms_per_update": 1e3 * total_s / args.steps,
-            "roofline": roof}
+            "roofline": roof, "reduction": reduction_rooflines(scan_ms, merge_ms, K, T, measured_peaks())}
 
 
 def run_batched(args):
@@ -502,7 +526,7 @@ def run_ours(args):
 
     # ---- device-timed region -------------------------------------------------
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    rollout_ms, step_ms = [], []
+    rollout_ms, step_ms, scan_ms, merge_ms = [], [], [], []
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
@@ -513,7 +537,10 @@ def run_ours(args):
             ev[i][0].record(stream)
             rh_step(args.warmup + i)
             ev[i][1].record(stream)
-            rollout_ms.append(ctl.stage_times()[0])     # waits for this update
+            st = ctl.stage_times()                      # waits for this update
+            rollout_ms.append(st[0])
+            scan_ms.append(st[1])
+            merge_ms.append(st[2])
         torch.cuda.synchronize()
     if dist is not None:
         dist.barrier()
@@ -545,8 +572,9 @@ def run_ours(args):
     peaks = measured_peaks()
     roofline = form_roofline(args.precision, rollout_ms, K, T, M, L, dev, peaks, args.workload)
     roofline["rollout_share_of_step"] = sum(rollout_ms) / sum(step_ms)
+    reduction = reduction_rooflines(scan_ms, merge_ms, K, T, peaks)
     forms = {args.precision: {"value": value, "ms_per_update": 1e3 * total_s / args.steps,
-                              "roofline": roofline}}
+                              "roofline": roofline, "reduction": reduction}}
     if not args.no_compare:
         other = "tc" if args.precision == "fp32" else "fp32"
         forms[other] = time_form(other, p, args, dev)
@@ -563,6 +591,7 @@ def run_ours(args):
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": (12 + T * 4) * 4,
                     "d2h_bytes_per_step": (T * 4 + K) * 4},
             "roofline": roofline,
+            "reduction_kernels": reduction,
             "forms": forms,
             "clocks": clocks.summary()}
     if ws == 1 and not args.no_cpu_baseline:
