@@ -1,14 +1,15 @@
 // reduce.cu -- cost-to-go scan and the per-timestep weighted average (Eq. 2).
 //
 // scan_lse_kernel: one CTA per RS_KC = 64 rollouts.  The timesteps are walked
-// from T-1 down to 0 in chunks of TC: one thread per rollout extends its
-// suffix sum S_{k,i} = phi_k + dt sum_{j>=i} q_{k,j} in FP64 (Sec. 3.1) and
-// parks the chunk in shared memory; then each warp takes whole timesteps of
-// the chunk and forms, over the CTA's 64 rollouts, the log-sum-exp partial
+// from T-1 down to 0 in chunks of TC: one thread per rollout loads the chunk's
+// costs (all loads in flight at once), extends its suffix sum
+// S_{k,i} = phi_k + dt sum_{j>=i} q_{k,j} in FP64 (Sec. 3.1) and parks the
+// chunk in shared memory; then each warp takes whole timesteps of the chunk
+// (their eps loaded up front) and forms, over the CTA's 64 rollouts, the log-sum-exp partial
 //     m_c = min_k S,  Z_c = sum_k 2^((m_c - S) log2(e)/lambda),
 //     V_c = sum_k 2^(...) eps_k
-// (exponent in FP64, exponential and the 2-term lane sums in FP32, warp sums
-// in FP64).  cost and eps are read once, coalesced and vectorised ([T][K]
+// (exponent in FP64; exponential, the 2-term lane sums and the pairwise warp
+// sums in FP32; partials stored in FP64).  cost and eps are read once, coalesced and vectorised ([T][K]
 // layout, eps as float4).  costs_out[k] = S_{k,0}.
 //
 // lse_merge_kernel: one warp per timestep merges the per-CTA partials in a
@@ -37,6 +38,14 @@ __device__ __forceinline__ double warp_sum_d(double v)
     return v;
 }
 
+// Pairwise (5-level butterfly) sum over a warp in FP32: at most 5 roundings.
+__device__ __forceinline__ float warp_sum_f(float v)
+{
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
+}
+
 __device__ __forceinline__ void scan_lse_block(const float *__restrict__ cost_tk, const float *__restrict__ phi,
                                                const float4 *__restrict__ eps_tk, int K, int T, double dt,
                                                double inv_lam_log2e, float *__restrict__ costs_out,
@@ -52,31 +61,60 @@ __device__ __forceinline__ void scan_lse_block(const float *__restrict__ cost_tk
     for (int hi = T; hi > 0; hi -= TC) {
         const int lo = hi > TC ? hi - TC : 0;
         if (tid < KC) {
-            for (int i = hi - 1; i >= lo; --i) {
-                double s = INFINITY;
-                if (k < K) {
-                    acc += (double)cost_tk[(size_t)i * K + k] * dt;
-                    s = acc;
+            // the chunk's costs are loaded first (independent loads in flight),
+            // then summed backwards in FP64 in the same order as ever
+            float cb[TC];
+#pragma unroll
+            for (int r = 0; r < TC; ++r) {
+                const int i = hi - 1 - r;
+                cb[r] = (k < K && i >= lo) ? cost_tk[(size_t)i * K + k] : 0.0f;
+            }
+#pragma unroll
+            for (int r = 0; r < TC; ++r) {
+                const int i = hi - 1 - r;
+                if (i >= lo) {
+                    double s = INFINITY;
+                    if (k < K) {
+                        acc += (double)cb[r] * dt;
+                        s = acc;
+                    }
+                    S_s[i - lo][tid] = s;
                 }
-                S_s[i - lo][tid] = s;
             }
             if (lo == 0 && k < K) costs_out[k] = (float)acc;
         }
         __syncthreads();
-        for (int r = warp; r < hi - lo; r += NT / 32) {
-            const int i = lo + r;
+        // each warp takes timesteps warp, warp + 8, ... of the chunk; the eps of
+        // all of them are loaded before the reductions
+        constexpr int RPW = TC / (NT / 32);
+        float4 ea[RPW], eb[RPW];
+        const int ka = k0 + lane, kb = k0 + lane + 32;
+#pragma unroll
+        for (int u = 0; u < RPW; ++u) {
+            const int r = warp + u * (NT / 32), i = lo + r;
+            const bool ok = r < hi - lo;
+            ea[u] = ok && ka < K ? eps_tk[(size_t)i * K + ka] : make_float4(0.f, 0.f, 0.f, 0.f);
+            eb[u] = ok && kb < K ? eps_tk[(size_t)i * K + kb] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < RPW; ++u) {
+            const int r = warp + u * (NT / 32), i = lo + r;
+            if (r >= hi - lo) break;
             const double sa = S_s[r][lane], sb = S_s[r][lane + 32];
+            // exact FP64 minimum: a rounded shift can put exponents hundreds of
+            // binary orders off when S is large and lambda small
             const double mn = warp_min_d(fmin(sa, sb));
             const float wa = exp2f((float)((mn - sa) * inv_lam_log2e));
             const float wb = exp2f((float)((mn - sb) * inv_lam_log2e));
-            const int ka = k0 + lane, kb = k0 + lane + 32;
-            const float4 ea = ka < K ? eps_tk[(size_t)i * K + ka] : make_float4(0.f, 0.f, 0.f, 0.f);
-            const float4 eb = kb < K ? eps_tk[(size_t)i * K + kb] : make_float4(0.f, 0.f, 0.f, 0.f);
-            double z = warp_sum_d((double)(wa + wb));
-            double v0 = warp_sum_d((double)fmaf(wa, ea.x, wb * eb.x));
-            double v1 = warp_sum_d((double)fmaf(wa, ea.y, wb * eb.y));
-            double v2 = warp_sum_d((double)fmaf(wa, ea.z, wb * eb.z));
-            double v3 = warp_sum_d((double)fmaf(wa, ea.w, wb * eb.w));
+            // the 64 rollouts' FP32 terms are summed by a pairwise warp tree in
+            // FP32 (B300 has little FP64 throughput); the partials are stored
+            // and merged over K in FP64
+            const float4 xa = ea[u], xb = eb[u];
+            const double z = (double)warp_sum_f(wa + wb);
+            const double v0 = (double)warp_sum_f(fmaf(wa, xa.x, wb * xb.x));
+            const double v1 = (double)warp_sum_f(fmaf(wa, xa.y, wb * xb.y));
+            const double v2 = (double)warp_sum_f(fmaf(wa, xa.z, wb * xb.z));
+            const double v3 = (double)warp_sum_f(fmaf(wa, xa.w, wb * xb.w));
             if (lane == 0) {
                 double *p = part + ((size_t)blk * T + i) * 6;
                 p[0] = mn;

@@ -127,6 +127,27 @@ def test_reduce_stage(oracle, K, T, lam):
     assert ec <= 1e-6
 
 
+def test_reduce_stage_large_costs_small_lambda(oracle):
+    """Costs near 1e8 (cost-to-go near 1e8 too) with lambda = 0.01: the shift of the
+    exponents must be the exact minimum, else exp2 over- or underflows; u_out is
+    then essentially the argmin rollout's perturbation, as in the oracle."""
+    K, T, lam = 300, 9, 0.01
+    g = np.random.default_rng(77)
+    cost = (1e8 + g.uniform(0, 2e3, (K, T))).astype(np.float32)
+    phi = g.uniform(0, 10, K).astype(np.float32)
+    eps = g.normal(0, 0.3, (K, T, 4)).astype(np.float32)
+    u_nom = g.normal(0, 0.5, (T, 4)).astype(np.float32)
+    p = W.problem(8, 4, 2, seed=0)
+    ctl = _ctrl(p)
+    u, c = ctl.debug_reduce(cost.T.copy(), phi, np.transpose(eps, (1, 0, 2)).copy(), u_nom, lam)
+    ctl.sync()
+    u = u.cpu().numpy()
+    S = oracle.cost_to_go(cost, phi, float(p.model.dt))
+    uref = oracle.weighted_update(S, eps, u_nom, lam)
+    assert np.all(np.isfinite(u))
+    assert np.all(_u_err(u, uref) <= U_TOL)
+
+
 # ---------------------------------------------------------------------------
 # rollout stage and end to end
 # ---------------------------------------------------------------------------
