@@ -233,7 +233,7 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-TC_FIELDS_PER_TILE = 64
+TC_FIELDS_PER_TILE = 128                      # fields per tensor-core tile (MMA N)
 TC_MMA_FLOPS_PER_FIELD = 3 * 2 * (160 + 16)   # hi*hi + hi*lo + lo*hi over K=160 (S) and K=16 (Y)
 
 
