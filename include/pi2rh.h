@@ -61,7 +61,8 @@ enum {
     PI_ERR_TIMEOUT = 4,     /* a bounded device-side wait expired (see pi_sync)    */
     PI_ERR_INTERNAL = 5,    /* a device-side consistency check failed              */
     PI_ERR_UNSUPPORTED = 6, /* option not available in this build                  */
-    PI_ERR_BUSY = 7         /* the object has work in flight that the call needs finished */
+    PI_ERR_BUSY = 7,        /* the object has work in flight that the call needs finished */
+    PI_ERR_CANCELLED = 8    /* a serving request was cancelled before it reached the GPU */
 };
 
 /* PI_PRECISION_FP32: receptive fields evaluated on the FP32 FMA pipe.
@@ -326,7 +327,8 @@ typedef struct {
 typedef struct {
     uint64_t ticket;
     int agent, K, T;
-    int status;         /* PI_OK, or PI_ERR_TIMEOUT / PI_ERR_INTERNAL / PI_ERR_CUDA           */
+    int status;         /* PI_OK, or PI_ERR_TIMEOUT / PI_ERR_INTERNAL / PI_ERR_CUDA, or
+                           PI_ERR_CANCELLED (t_launch_ns is then 0)                         */
     int group_size;     /* requests in the launch that carried this one                      */
     int64_t t_submit_ns, t_launch_ns, t_result_ns;
 } pi_serve_done;
@@ -365,6 +367,12 @@ int pi_server_set_agent(pi_server *s, int agent, const float *x0, const float *u
  * ticket.  Errors: INVALID_ARG (sizes, parameters, or a request whose scratch
  * exceeds the whole pool). */
 int pi_server_submit(pi_server *s, const pi_serve_request *req, uint64_t *ticket);
+
+/* Cancels a request that is still queued: it never reaches the GPU, its
+ * agent's state and counter are untouched, and a completion record with status
+ * PI_ERR_CANCELLED is queued for it.  PI_ERR_BUSY if the request is already on
+ * the GPU or finished; PI_ERR_INVALID_ARG for an unknown ticket. */
+int pi_server_cancel(pi_server *s, uint64_t ticket);
 
 /* Moves up to max completion records into out (oldest first), waiting up to
  * timeout_us microseconds for the first one (0 = do not wait); *n_out = count. */

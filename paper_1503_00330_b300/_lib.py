@@ -14,9 +14,9 @@ LIB_PATH = os.path.join(PKG, "lib", "libpi2rh.so")
 HEADER = os.path.join(os.path.dirname(PKG), "include", "pi2rh.h")
 
 (PI_OK, PI_ERR_INVALID_ARG, PI_ERR_OOM, PI_ERR_CUDA, PI_ERR_TIMEOUT, PI_ERR_INTERNAL, PI_ERR_UNSUPPORTED,
- PI_ERR_BUSY) = range(8)
+ PI_ERR_BUSY, PI_ERR_CANCELLED) = range(9)
 ERR_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "TIMEOUT", 5: "INTERNAL", 6: "UNSUPPORTED",
-             7: "BUSY"}
+             7: "BUSY", 8: "CANCELLED"}
 
 _fp = ctypes.POINTER(ctypes.c_float)
 _vp = ctypes.c_void_p
@@ -114,6 +114,7 @@ _SIGS = {
     "pi_server_create": (ctypes.c_int, [_vp, ctypes.POINTER(ServerOptsC), ctypes.POINTER(_vp)]),
     "pi_server_set_agent": (ctypes.c_int, [_vp, ctypes.c_int, _fp, _fp, ctypes.c_uint64]),
     "pi_server_submit": (ctypes.c_int, [_vp, ctypes.POINTER(ServeRequestC), ctypes.POINTER(ctypes.c_uint64)]),
+    "pi_server_cancel": (ctypes.c_int, [_vp, ctypes.c_uint64]),
     "pi_server_poll": (ctypes.c_int, [_vp, ctypes.POINTER(ServeDoneC), ctypes.c_int, ctypes.c_int64,
                                       ctypes.POINTER(ctypes.c_int)]),
     "pi_server_result": (ctypes.c_int, [_vp, ctypes.c_uint64, _fp, _fp]),

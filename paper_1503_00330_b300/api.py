@@ -336,6 +336,14 @@ class Server:
         check(self._lib.pi_server_submit(self._h, ctypes.byref(q), ctypes.byref(t)))
         return int(t.value)
 
+    def cancel(self, ticket: int) -> bool:
+        """Cancels a queued request; False if it is already on the GPU or finished."""
+        rc = self._lib.pi_server_cancel(self._h, int(ticket))
+        if rc == _lib.PI_ERR_BUSY:
+            return False
+        check(rc)
+        return True
+
     def poll(self, max_n: int = 1024, timeout_us: int = 0) -> np.ndarray:
         buf = (_lib.ServeDoneC * max_n)()
         n = ctypes.c_int()

@@ -139,6 +139,7 @@ TcArgs tc_args(const pi_ctx *c) { return ctx_tc_args(c); }
 int launch_rollouts(pi_ctx *c, const float *x0, const float *u_nom, int K, int T,
                     const float *sigma_u, uint64_t seed, float *cost, float4 *eps, float *phi)
 {
+    NvtxRange nv("pi2rh rollout");
     if (c->opts.precision == PI_PRECISION_TC_FP16X3) {
         TcArgs t = tc_args(c);
         t.K = K;
@@ -178,6 +179,7 @@ int launch_rollouts(pi_ctx *c, const float *x0, const float *u_nom, int K, int T
 int launch_reduce(pi_ctx *c, const float *cost, const float *phi, const float4 *eps,
                   const float *u_nom, int K, int T, float lambda, float *u_out, float *costs_out)
 {
+    NvtxRange nv("pi2rh cost-to-go + weighted average");
     const double inv_lam_log2e = 1.4426950408889634074 / (double)lambda;
     PI_CUDA(launch_scan_lse(cost, phi, eps, K, T, c->dt, inv_lam_log2e, costs_out, c->d_part,
                             c->stream),
@@ -445,6 +447,7 @@ int pi_update(pi_ctx *c, const float *x0, const float *u_nom, int K, int T, floa
     PI_TRY(check_sizes(K, T, c->opts.M));
     PI_TRY(check_update_args(nullptr, lambda, sigma_u));
     PI_TRY(injected_fault());
+    NvtxRange nv("pi_update");
     DeviceGuard dg(c->device);
     PI_CUDA(dg.err, "cudaSetDevice");
     PI_TRY(ensure_scratch(c, K, T));
@@ -462,6 +465,7 @@ int pi_rh_advance(pi_ctx *c, float *x0, const float *u_out, int T, float *u_next
     if (!x0 || !u_out || !u_next || T < 1) return fail(PI_ERR_INVALID_ARG, "bad argument");
     if (u_next < u_out + (size_t)T * NU && u_out < u_next + (size_t)T * NU)
         return fail(PI_ERR_INVALID_ARG, "u_nom_next must not overlap u_out");
+    NvtxRange nv("pi_rh_advance");
     DeviceGuard dg(c->device);
     PI_CUDA(dg.err, "cudaSetDevice");
     if (!c->d_rh) PI_CUDA(cudaMallocAsync((void **)&c->d_rh, 40 * sizeof(float), c->stream), "rh scratch");

@@ -307,6 +307,7 @@ int pi_batch_update(pi_batch *b, const float *lambda, const float *sigma_u, cons
             if (!std::isfinite(sigma_u[4 * i + j]) || sigma_u[4 * i + j] < 0.0f)
                 return bfail(PI_ERR_INVALID_ARG, "sigma_u of item " + std::to_string(i) + " must be >= 0");
     }
+    NvtxRange nv("pi_batch_update");
     int prev = -1;
     cudaGetDevice(&prev);
     if (prev != b->device && cudaSetDevice(b->device) != cudaSuccess) return bfail(PI_ERR_CUDA, "cudaSetDevice");

@@ -4,6 +4,7 @@
 
 #include <cstdint>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "pi2rh.h"
 #include "pi2rh_device.cuh"
@@ -37,6 +38,15 @@ struct pi_ctx {
     bool timing = false;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     uint64_t launches = 0;
+};
+
+// Scoped NVTX range on the calling host thread (shown by profilers that attach
+// to NVTX; a few nanoseconds otherwise).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
 };
 
 // Records msg as the calling thread's last error (pi_last_error) and returns code.

@@ -295,6 +295,7 @@ int status_of(int err_word)
 // Fills the lane's tables for its group and enqueues the whole group update.
 int pi_server::launch(Lane &L)
 {
+    NvtxRange nv("pi_server group launch");
     const int n = (int)L.group.size();
     const bool tc = form == PI_PRECISION_TC_FP16X3;
     const int spb = tc ? TC_SLOTS : RF_SLOTS;
@@ -797,6 +798,31 @@ int pi_server_submit(pi_server *s, const pi_serve_request *req, uint64_t *ticket
     s->enqueue_locked(std::move(r));
     if (ticket) *ticket = s->next_ticket;
     return PI_OK;
+}
+
+int pi_server_cancel(pi_server *s, uint64_t ticket)
+{
+    if (!s) return sfail(PI_ERR_INVALID_ARG, "server is NULL");
+    std::lock_guard<std::mutex> lk(s->mu);
+    for (auto it = s->pending.begin(); it != s->pending.end(); ++it) {
+        if (it->ticket != ticket) continue;
+        pi_serve_done dn{};
+        dn.ticket = it->ticket;
+        dn.agent = it->q.agent;
+        dn.K = it->q.K;
+        dn.T = it->q.T;
+        dn.status = PI_ERR_CANCELLED;
+        dn.t_submit_ns = it->t_submit;
+        dn.t_result_ns = now_ns();
+        s->agent_outstanding[it->q.agent] -= 1;
+        s->pending.erase(it);
+        s->done_q.push_back(dn);
+        s->st.completed += 1;
+        s->cv_done.notify_all();
+        return PI_OK;
+    }
+    if (ticket == 0 || ticket > s->next_ticket) return sfail(PI_ERR_INVALID_ARG, "unknown ticket");
+    return sfail(PI_ERR_BUSY, "the request is on the GPU or finished");
 }
 
 int pi_server_poll(pi_server *s, pi_serve_done *out, int max, int64_t timeout_us, int *n_out)

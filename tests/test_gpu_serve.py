@@ -249,3 +249,39 @@ def test_served_equals_alone_for_each_group_split(monkeypatch, split):
         for r in range(2):
             assert np.array_equal(got[(a, r)][0], ref[r][0]), f"split {split}, agent {a} round {r}"
             assert np.array_equal(got[(a, r)][1], ref[r][1]), f"split {split}, agent {a} round {r}"
+
+
+def test_cancelled_requests_leave_the_rest_unchanged():
+    """Queued requests cancelled on the host never reach the GPU: every other
+    request is served exactly as alone, and an agent whose request was cancelled
+    continues its own sequence as if the request had never been made."""
+    from paper_1503_00330_b300._lib import PI_ERR_CANCELLED, PiError
+    ctl = _controller("fp32")
+    srv = _server(ctl, len(AGENTS), max_inflight=1, max_group=1)   # a long queue
+    tickets = {}
+    for r in range(3):
+        for a in range(len(AGENTS)):
+            K, T = AGENTS[a]
+            tickets[srv.submit(a, K, T, LAM, SU)] = (a, r)
+    victims = [t for t, ar in tickets.items() if ar in ((2, 1), (5, 2))]
+    cancelled = {t for t in victims if srv.cancel(t)}
+    assert max(victims) in cancelled            # the last request submitted was still queued
+    done = srv.wait(tickets)
+    served = {a: [] for a in range(len(AGENTS))}
+    for t in sorted(tickets):                   # ticket order is each agent's round order
+        a, r = tickets[t]
+        if t in cancelled:
+            assert done[t]["status"] == PI_ERR_CANCELLED and done[t]["t_launch_ns"] == 0
+            continue
+        assert done[t]["status"] == 0
+        K, T = AGENTS[a]
+        served[a].append(srv.result(t, T, K))
+    for a in range(len(AGENTS)):
+        ref, _ = _alone_sequence(ctl, a, len(served[a]))
+        for n, (u, c) in enumerate(served[a]):
+            assert np.array_equal(u, ref[n][0]) and np.array_equal(c, ref[n][1]), f"agent {a} request {n}"
+    assert srv.cancel(max(victims)) is False     # finished: nothing to cancel
+    with pytest.raises(PiError):
+        srv.cancel(10 ** 9)                     # never issued
+    assert int(srv.state_save()["counter"][5]) == 2
+    srv.close()
