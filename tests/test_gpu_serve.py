@@ -283,5 +283,6 @@ def test_cancelled_requests_leave_the_rest_unchanged():
     assert srv.cancel(max(victims)) is False     # finished: nothing to cancel
     with pytest.raises(PiError):
         srv.cancel(10 ** 9)                     # never issued
+    srv.drain()
     assert int(srv.state_save()["counter"][5]) == 2
     srv.close()
