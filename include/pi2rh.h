@@ -411,6 +411,13 @@ int pi_server_get_stats(const pi_server *s, pi_server_stats *out);
  * and frees the server.  NULL is accepted. */
 void pi_server_destroy(pi_server *s);
 
+/* Host-only ABI check (no GPU): writes, for the public structs in this order
+ * -- pi_lwpr_params, pi_cost_params, pi_opts, pi_batch_item, pi_server_opts,
+ * pi_serve_request, pi_serve_done, pi_serve_arrival, pi_server_stats -- their
+ * sizeof followed by the byte offset of each member in declaration order, into
+ * out [max]; *n = entries written.  INVALID_ARG if max is too small. */
+int pi_debug_struct_layout(size_t *out, int max, int *n);
+
 /* Host-only check of the server's pool allocator (no GPU): runs n operations
  * on a pool of `capacity` bytes -- op[i] = 1 allocates size[i] bytes, op[i] = 0
  * frees the block allocated by operation size[i] -- and writes each

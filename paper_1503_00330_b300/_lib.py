@@ -128,6 +128,8 @@ _SIGS = {
                                             ctypes.POINTER(ctypes.c_uint64)]),
     "pi_server_get_stats": (ctypes.c_int, [_vp, ctypes.POINTER(ServerStatsC)]),
     "pi_server_destroy": (None, [_vp]),
+    "pi_debug_struct_layout": (ctypes.c_int, [ctypes.POINTER(ctypes.c_size_t), ctypes.c_int,
+                                              ctypes.POINTER(ctypes.c_int)]),
     "pi_debug_pool": (ctypes.c_int, [ctypes.c_size_t, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_size_t),
                                      ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int)]),
     "pi_debug_noise": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp]),

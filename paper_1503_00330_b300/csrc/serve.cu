@@ -986,6 +986,52 @@ void pi_server_destroy(pi_server *s)
     delete s;
 }
 
+int pi_debug_struct_layout(size_t *out, int max, int *n)
+{
+    if (!out || !n || max < 0) return sfail(PI_ERR_INVALID_ARG, "bad argument");
+#define PI_L(T, ...) sizeof(T), __VA_ARGS__
+    const size_t v[] = {
+        PI_L(pi_lwpr_params, offsetof(pi_lwpr_params, n_in), offsetof(pi_lwpr_params, n_out),
+             offsetof(pi_lwpr_params, L), offsetof(pi_lwpr_params, dt), offsetof(pi_lwpr_params, c),
+             offsetof(pi_lwpr_params, D), offsetof(pi_lwpr_params, beta), offsetof(pi_lwpr_params, b),
+             offsetof(pi_lwpr_params, sigma)),
+        PI_L(pi_cost_params, offsetof(pi_cost_params, goal), offsetof(pi_cost_params, Q_pos),
+             offsetof(pi_cost_params, Q_vel), offsetof(pi_cost_params, Q_ang), offsetof(pi_cost_params, w_obs),
+             offsetof(pi_cost_params, obs_sharp), offsetof(pi_cost_params, radius), offsetof(pi_cost_params, w_crash),
+             offsetof(pi_cost_params, w_var), offsetof(pi_cost_params, w_T), offsetof(pi_cost_params, obs_kind),
+             offsetof(pi_cost_params, n_obs), offsetof(pi_cost_params, obs_xy)),
+        PI_L(pi_opts, offsetof(pi_opts, precision), offsetof(pi_opts, model_noise), offsetof(pi_opts, M),
+             offsetof(pi_opts, device)),
+        PI_L(pi_batch_item, offsetof(pi_batch_item, ctx), offsetof(pi_batch_item, K), offsetof(pi_batch_item, T),
+             offsetof(pi_batch_item, x0), offsetof(pi_batch_item, u_nominal), offsetof(pi_batch_item, u_out),
+             offsetof(pi_batch_item, costs_out)),
+        PI_L(pi_server_opts, offsetof(pi_server_opts, n_agents), offsetof(pi_server_opts, K_max),
+             offsetof(pi_server_opts, T_max), offsetof(pi_server_opts, max_inflight),
+             offsetof(pi_server_opts, max_group), offsetof(pi_server_opts, hbm_budget),
+             offsetof(pi_server_opts, want_costs)),
+        PI_L(pi_serve_request, offsetof(pi_serve_request, agent), offsetof(pi_serve_request, K),
+             offsetof(pi_serve_request, T), offsetof(pi_serve_request, lambda), offsetof(pi_serve_request, sigma_u),
+             offsetof(pi_serve_request, x0), offsetof(pi_serve_request, keep_result)),
+        PI_L(pi_serve_done, offsetof(pi_serve_done, ticket), offsetof(pi_serve_done, agent),
+             offsetof(pi_serve_done, K), offsetof(pi_serve_done, T), offsetof(pi_serve_done, status),
+             offsetof(pi_serve_done, group_size), offsetof(pi_serve_done, t_submit_ns),
+             offsetof(pi_serve_done, t_launch_ns), offsetof(pi_serve_done, t_result_ns)),
+        PI_L(pi_serve_arrival, offsetof(pi_serve_arrival, t_ns), offsetof(pi_serve_arrival, agent),
+             offsetof(pi_serve_arrival, K), offsetof(pi_serve_arrival, T)),
+        PI_L(pi_server_stats, offsetof(pi_server_stats, submitted), offsetof(pi_server_stats, completed),
+             offsetof(pi_server_stats, groups), offsetof(pi_server_stats, launches),
+             offsetof(pi_server_stats, memory_waits), offsetof(pi_server_stats, pool_bytes),
+             offsetof(pi_server_stats, pool_peak_bytes), offsetof(pi_server_stats, peak_inflight_requests),
+             offsetof(pi_server_stats, peak_group_size)),
+    };
+#undef PI_L
+    const int cnt = (int)(sizeof v / sizeof v[0]);
+    if (max < cnt) return sfail(PI_ERR_INVALID_ARG, "out is too small");
+    for (int i = 0; i < cnt; ++i) out[i] = v[i];
+    *n = cnt;
+    return PI_OK;
+}
+
 int pi_debug_pool(size_t capacity, const int *op, const size_t *size, int n, int64_t *offset, int *free_extents)
 {
     if (n < 0 || (n > 0 && (!op || !size || !offset)) || !free_extents)

@@ -72,3 +72,34 @@ def test_null_context_rejected(lib):
 def test_debug_noise_rejects_sizes(lib):
     assert lib.pi_debug_noise(0, 0, 5, 0, None, None) == _lib.PI_ERR_INVALID_ARG
     assert lib.pi_debug_noise(0, 5, 5, 0, None, None) == _lib.PI_ERR_INVALID_ARG
+
+
+def test_ctypes_structs_match_the_c_layout():
+    """Every struct the binding passes across the boundary has the C compiler's
+    size and member offsets (a drifted field would corrupt data silently)."""
+    import ctypes
+    from paper_1503_00330_b300 import _lib
+    lib = _lib.load()
+    buf = (ctypes.c_size_t * 128)()
+    n = ctypes.c_int()
+    _lib.check(lib.pi_debug_struct_layout(buf, 128, ctypes.byref(n)))
+    c_side = list(buf[:n.value])
+    names = {"LwprParamsC": ["n_in", "n_out", "L", "dt", "c", "D", "beta", "b", "sigma"],
+             "CostParamsC": ["goal", "Q_pos", "Q_vel", "Q_ang", "w_obs", "obs_sharp", "radius", "w_crash", "w_var",
+                             "w_T", "obs_kind", "n_obs", "obs_xy"],
+             "OptsC": ["precision", "model_noise", "M", "device"],
+             "BatchItemC": ["ctx", "K", "T", "x0", "u_nominal", "u_out", "costs_out"],
+             "ServerOptsC": ["n_agents", "K_max", "T_max", "max_inflight", "max_group", "hbm_budget", "want_costs"],
+             "ServeRequestC": ["agent", "K", "T", "lam", "sigma_u", "x0", "keep_result"],
+             "ServeDoneC": ["ticket", "agent", "K", "T", "status", "group_size", "t_submit_ns", "t_launch_ns",
+                            "t_result_ns"],
+             "ServeArrivalC": ["t_ns", "agent", "K", "T"],
+             "ServerStatsC": ["submitted", "completed", "groups", "launches", "memory_waits", "pool_bytes",
+                              "pool_peak_bytes", "peak_inflight_requests", "peak_group_size"]}
+    py_side = []
+    for cls, fields in names.items():
+        st = getattr(_lib, cls)
+        assert [f for f, _ in st._fields_] == fields, cls
+        py_side.append(ctypes.sizeof(st))
+        py_side += [getattr(st, f).offset for f in fields]
+    assert py_side == c_side
