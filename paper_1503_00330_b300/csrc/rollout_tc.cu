@@ -18,18 +18,23 @@
 // Roles (one CTA per SM, 128 slots, 320 threads):
 //   warp 0 lane 0: producer -- 1-D bulk copies (TMA) of the pre-packed
 //                  coefficient chunks (8 KB: the hi and lo coefficient blocks
-//                  of one K step for 128 fields) into a ring of NSLOT chunk
-//                  slots, and of the per-field constants (cs, cy, sigma^2)
-//                  into a 4-deep constant ring;
+//                  of one K step for 128 fields) in groups of CPG chunks (one
+//                  copy per contiguous run, one barrier pair per group) into a
+//                  ring of NSLOT chunk slots, and of the per-field constants
+//                  (cs, cy, sigma^2) into a 4-deep constant ring;
 //   warp 1 lane 0: MMA issuer -- per tile of 128 fields, 33 MMAs (M=128,
-//                  N=128, K=16; S: 10 K steps x 3 split products, Y: 1 x 3),
-//                  releasing each chunk slot as soon as its MMAs complete,
-//                  into one of two TMEM accumulator buffers;
+//                  N=128, K=16; S: 10 K steps x 3 split products, Y: 1 x 3)
+//                  into one of two TMEM accumulator buffers, releasing each
+//                  chunk group as soon as its MMAs complete;
 //   warps 2-9:     epilogue -- tcgen05.ld of S and Y, online base-2 softmax
-//                  per output (chunks of 16 fields, one rescale per chunk),
-//                  merge of the two column halves, then the dynamics step
-//                  (cost, Euler step, Philox noise) and the feature tile of
-//                  the next step.
+//                  per output on packed FP32x2 operations (chunks of 16
+//                  fields, one rescale per chunk), merge of the two column
+//                  halves, then the dynamics step (cost, Euler step, Philox
+//                  noise) and the feature tile of the next step.
+// Launch forms: one CTA per 128-slot block; clusters of 2-4 CTAs that split a
+// block's 12 outputs when the blocks alone would leave SMs idle (means and
+// variances exchanged through distributed shared memory); a persistent
+// work-list form and a one-wave group form for batches.
 // Every wait is bounded; on expiry the kernel flags the device error word,
 // drains its copies and MMAs, frees its tensor memory and returns.
 #include <cstdio>
