@@ -36,6 +36,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "LWPR rollout-steps/s (ms per PI^2 update alongside)"
+PAPER_CONTEXT = ("paper (context only, other hardware and a ~1000x smaller model): one PI^2 iteration of "
+                 "1000 rollouts x 50 steps in ~6.5 ms on a GTX 780 Ti (~7.7e6 rollout-steps/s), 18 ms with 32 "
+                 "sub-rollouts, for an LWPR model of 3 outputs x 15-24 fields over 4 inputs")
 UNIT = "rollout-steps/s"
 FLOPS_PER_FIELD = 360          # 16 sub + 136 FMA + 16 FMA + 16 FMA + 4 FMA (x2 flops per FMA)
 FP32_LANES_PER_SM = 128
@@ -593,6 +596,7 @@ def run_ours(args):
             "roofline": roofline,
             "reduction_kernels": reduction,
             "forms": forms,
+            "paper_context": PAPER_CONTEXT,
             "clocks": clocks.summary()}
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(p, args.cpu_sample)
