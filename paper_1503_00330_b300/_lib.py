@@ -105,6 +105,7 @@ _SIGS = {
     "pi_debug_wait_timeout": (ctypes.c_int, [_vp, ctypes.c_int64]),
     "pi_batch_create": (ctypes.c_int, [ctypes.POINTER(BatchItemC), ctypes.c_int, ctypes.c_int, ctypes.POINTER(_vp)]),
     "pi_batch_set_schedule": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
+    "pi_batch_set_tile": (ctypes.c_int, [_vp, ctypes.c_int]),
     "pi_batch_set_stream": (ctypes.c_int, [_vp, _vp]),
     "pi_batch_update": (ctypes.c_int, [_vp, _fp, _fp, ctypes.POINTER(ctypes.c_uint64)]),
     "pi_batch_sync": (ctypes.c_int, [_vp]),

@@ -238,6 +238,10 @@ class Batch:
     def set_schedule(self, order: str = "longest_first", grid: int = 0):
         check(self._lib.pi_batch_set_schedule(self._h, self.ORDERS[order], int(grid)))
 
+    def set_tile(self, split: int = 0):
+        """Tensor-core tile shape: 0 persistent work list; 1..4 CTAs per 128-slot item (outputs split)."""
+        check(self._lib.pi_batch_set_tile(self._h, int(split)))
+
     def update(self, lam, sigma_u, seeds):
         s = torch.cuda.current_stream(self.device).cuda_stream
         if s != self._stream:

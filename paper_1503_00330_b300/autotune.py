@@ -1,12 +1,14 @@
 """Schedule autotuner for the batched (multi-controller) update.
 
-For a set of controllers it times every candidate schedule of the persistent
-batched launch -- precision form (FP32 or tensor-core) x work-list order
-(controller order, longest block first, round robin) -- on the device, keeps
-the fastest, and stores it in a JSON cache keyed by the batch's shape
-signature (per controller: K, T, L, M) and the device name, so later runs
-with the same shapes skip the search.  Both forms meet the same accuracy
-target, so the choice is by time alone.
+For a set of controllers it times every candidate schedule of the batched
+launch -- precision form (FP32 or tensor-core) x work-list order (controller
+order, longest block first, round robin) x, for the tensor-core form, the
+tile shape (persistent CTAs over 128-slot x 12-output items, or one item per
+CTA, or per pair of CTAs that split its outputs) -- on the device, keeps the
+fastest, and stores it in a JSON cache keyed by the batch's shape signature
+(per controller: K, T, L, M) and the device name, so later runs with the same
+shapes skip the search.  Both forms meet the same accuracy target, so the
+choice is by time alone.
 """
 from __future__ import annotations
 
@@ -22,7 +24,8 @@ from .api import Batch, Controller
 DEFAULT_CACHE = os.environ.get("PI2RH_AUTOTUNE_CACHE",
                                os.path.join(os.path.expanduser("~"), ".cache", "pi2rh", "autotune.json"))
 ORDERS = ("as_given", "longest_first", "round_robin")
-VERSION = 1
+TC_TILES = (0, 1, 2)     # persistent work list; one item per CTA; outputs split over 2 CTAs
+VERSION = 2
 
 
 def signature(problems, device: int = 0) -> str:
@@ -67,8 +70,8 @@ def time_batch(batch: Batch, problems, reps: int = 2, warmup: int = 1) -> float:
 
 
 def tune(problems, forms=("fp32", "tc"), orders=ORDERS, reps: int = 2, cache_path: str = DEFAULT_CACHE,
-         use_cache: bool = True, device: int = 0, log=None) -> dict:
-    """Returns {"form", "order", "ms", "candidates": {...}, "cached": bool}."""
+         use_cache: bool = True, device: int = 0, log=None, tc_tiles=TC_TILES) -> dict:
+    """Returns {"form", "order", "tile", "ms", "candidates": {...}, "cached": bool}."""
     key = signature(problems, device)
     cache = _load(cache_path) if use_cache else {}
     if use_cache and key in cache:
@@ -83,17 +86,20 @@ def tune(problems, forms=("fp32", "tc"), orders=ORDERS, reps: int = 2, cache_pat
                       x0=[p.x0 for p in problems], u_nom=[p.u_nom for p in problems])
         for order in orders:
             batch.set_schedule(order)
-            t0 = time.perf_counter()
-            ms = time_batch(batch, problems, reps=reps)
-            results[f"{form}/{order}"] = ms
-            if log:
-                log(f"autotune {form}/{order}: {ms:.2f} ms per update ({time.perf_counter() - t0:.1f} s)")
+            for tile in (tc_tiles if form == "tc" else (0,)):
+                batch.set_tile(tile)
+                t0 = time.perf_counter()
+                ms = time_batch(batch, problems, reps=reps)
+                results[f"{form}/{order}/{tile}"] = ms
+                if log:
+                    log(f"autotune {form}/{order}/tile {tile}: {ms:.2f} ms per update "
+                        f"({time.perf_counter() - t0:.1f} s)")
         batch.close()
         for c in ctls:
             c.close()
     best = min(results, key=results.get)
-    form, order = best.split("/")
-    out = {"form": form, "order": order, "ms": results[best], "candidates": results}
+    form, order, tile = best.split("/")
+    out = {"form": form, "order": order, "tile": int(tile), "ms": results[best], "candidates": results}
     if use_cache:
         cache[key] = out
         _store(cache_path, cache)

@@ -26,6 +26,7 @@ struct pi_batch {
     int form = PI_PRECISION_FP32;
     int order = PI_BATCH_ORDER_LONGEST_FIRST;
     int grid = 0;
+    int split = 0;                          // tensor-core tile shape: 0 persistent, 1..4 outputs split
     cudaStream_t user_stream = nullptr;
     cudaStream_t stream = nullptr;          // private stream used for capture and replay
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
@@ -115,7 +116,8 @@ int capture(pi_batch *b)
     if (e == cudaSuccess) {
         if (b->form == PI_PRECISION_TC_FP16X3) {
             TcBatchArgs tb{static_cast<const TcArgs *>(b->d_args), b->d_ritems, b->n_ritems, b->d_counter};
-            e = launch_rollout_tc_batch(tb, b->grid, b->stream);
+            e = b->split > 0 ? launch_rollout_tc_group(tb, b->split, b->stream)
+                             : launch_rollout_tc_batch(tb, b->grid, b->stream);
         } else {
             BatchArgs fb{static_cast<const RolloutArgs *>(b->d_args), b->d_ritems, b->n_ritems, b->d_counter,
                          b->items[0].ctx->d_err};
@@ -287,6 +289,26 @@ int pi_batch_set_schedule(pi_batch *b, int order, int grid)
     }
     if (prev >= 0 && prev != b->device) cudaSetDevice(prev);
     return rc;
+}
+
+int pi_batch_set_tile(pi_batch *b, int split)
+{
+    if (!b) return bfail(PI_ERR_INVALID_ARG, "batch is NULL");
+    if (split < 0 || split > 4)
+        return bfail(PI_ERR_INVALID_ARG, "split must be 0..4");
+    if (split != 0 && b->form != PI_PRECISION_TC_FP16X3)
+        return bfail(PI_ERR_INVALID_ARG, "only tensor-core batches take a split tile shape");
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != b->device) cudaSetDevice(b->device);
+    cudaStreamSynchronize(b->stream);
+    b->split = split;
+    if (b->exec) {
+        cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
+    }
+    if (prev >= 0 && prev != b->device) cudaSetDevice(prev);
+    return PI_OK;
 }
 
 int pi_batch_set_stream(pi_batch *b, void *stream)
