@@ -346,6 +346,8 @@ def run_batched(args):
         ctls = [Controller(p.model, p.cost, M=p.M, model_noise=p.model_noise, precision=form) for p in probs]
         batch = Batch(ctls, [p.K for p in probs], [p.T for p in probs], precision=form,
                       x0=[p.x0 for p in probs], u_nom=[p.u_nom for p in probs])
+        if form == "tc":
+            batch.set_tile(args.batch_tile)
         lam = [p.lam for p in probs]
         su = [p.sigma_u for p in probs]
         for i in range(args.warmup):
@@ -394,6 +396,7 @@ def run_batched(args):
                                    "L ~ logU[128, 2048], one persistent launch under a CUDA graph",
                        "controllers": len(probs), "rollout_steps_per_update": rs_total,
                        "precision": args.precision, "schedule": "longest_first",
+                       "tc_tile": args.batch_tile,
                        "l2": "flushed between timed steps (256 MiB write outside the event window)"},
             "gpu_launches": main["gpu_launches"], "roofline": main["roofline"], "forms": forms,
             "clocks": main["clocks"]}
@@ -619,6 +622,8 @@ def main():
     ap.add_argument("--precision", choices=["fp32", "tc"], default="fp32",
                     help="form of the headline line (the other form is timed too and reported under 'forms')")
     ap.add_argument("--no-compare", action="store_true", help="skip timing the other form")
+    ap.add_argument("--batch-tile", type=int, default=0,
+                    help="batched: tensor-core tile shape (0 persistent work list, 1..4 CTAs per item)")
     ap.add_argument("--serve-seconds", type=float, default=3.0, help="serving: trace length at the offered rate")
     ap.add_argument("--serve-lanes", type=int, default=2, help="serving: groups on the GPU at once")
     ap.add_argument("--serve-group", type=int, default=64, help="serving: most requests per group")
