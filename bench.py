@@ -330,7 +330,8 @@ def time_form(precision, p, args, dev):
 def run_batched(args):
     """64 independent controllers (K ~ logU[1024, 32768], T ~ U{30..150},
     L ~ logU[128, 2048], own model/obstacles/seed each) updated by one
-    persistent launch under a CUDA graph; both forms timed."""
+    batched launch under a CUDA graph; both forms timed, each with the
+    work-list order and (tensor cores) tile shape the autotuner picks."""
     import torch
     from paper_1503_00330_b300 import build
     from paper_1503_00330_b300 import workloads as W
@@ -338,6 +339,18 @@ def run_batched(args):
     build.build()
     dev = torch.device("cuda", 0)
     probs = W.batched(64, seed=0)
+    # schedule per form from the autotuner (JSON-cached by batch shape), unless fixed on the command line
+    sched = {"fp32": ("longest_first", 0), "tc": ("longest_first", args.batch_tile)}
+    tuned = None
+    if args.batch_tile < 0:
+        from paper_1503_00330_b300 import autotune
+        tuned = autotune.tune(probs, reps=2)
+        best = {}
+        for key, ms in tuned["candidates"].items():   # "form/order/tile" -> ms per update
+            f, o, t = key.split("/")
+            if f not in best or ms < best[f][2]:
+                best[f] = (o, int(t), ms)
+        sched = {f: (o, t) for f, (o, t, _) in best.items()}
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
     forms = {}
@@ -346,8 +359,9 @@ def run_batched(args):
         ctls = [Controller(p.model, p.cost, M=p.M, model_noise=p.model_noise, precision=form) for p in probs]
         batch = Batch(ctls, [p.K for p in probs], [p.T for p in probs], precision=form,
                       x0=[p.x0 for p in probs], u_nom=[p.u_nom for p in probs])
+        batch.set_schedule(sched[form][0])
         if form == "tc":
-            batch.set_tile(args.batch_tile)
+            batch.set_tile(sched[form][1])
         lam = [p.lam for p in probs]
         su = [p.sigma_u for p in probs]
         for i in range(args.warmup):
@@ -368,6 +382,7 @@ def run_batched(args):
         rs = batch.rollout_steps()
         useful = sum(p.K * p.T * p.M * 12 * p.model.L for p in probs) * FLOPS_PER_FIELD
         entry = {"value": rs * args.steps / (sum(ms) / 1e3), "ms_per_update": statistics.mean(ms),
+                 "schedule": {"order": sched[form][0], "tile": sched[form][1]},
                  "gpu_launches": batch.launch_count() - launches0, "clocks": clocks.summary()}
         if form == "fp32":
             peak = torch.cuda.get_device_properties(dev).multi_processor_count * FP32_LANES_PER_SM * 2 * \
@@ -395,10 +410,12 @@ def run_batched(args):
             "config": {"workload": "batched: 64 controllers, K ~ logU[1024, 32768], T ~ U{30..150}, "
                                    "L ~ logU[128, 2048], one persistent launch under a CUDA graph",
                        "controllers": len(probs), "rollout_steps_per_update": rs_total,
-                       "precision": args.precision, "schedule": "longest_first",
-                       "tc_tile": args.batch_tile,
+                       "precision": args.precision,
+                       "schedule": "per form, from the autotuner" if tuned else "fixed on the command line",
                        "l2": "flushed between timed steps (256 MiB write outside the event window)"},
             "gpu_launches": main["gpu_launches"], "roofline": main["roofline"], "forms": forms,
+            "autotune": None if tuned is None else {"best": {k: tuned[k] for k in ("form", "order", "tile", "ms")},
+                                                    "cached": tuned["cached"], "candidates_ms": tuned["candidates"]},
             "clocks": main["clocks"]}
     print(json.dumps(line), flush=True)
 
@@ -622,8 +639,9 @@ def main():
     ap.add_argument("--precision", choices=["fp32", "tc"], default="fp32",
                     help="form of the headline line (the other form is timed too and reported under 'forms')")
     ap.add_argument("--no-compare", action="store_true", help="skip timing the other form")
-    ap.add_argument("--batch-tile", type=int, default=0,
-                    help="batched: tensor-core tile shape (0 persistent work list, 1..4 CTAs per item)")
+    ap.add_argument("--batch-tile", type=int, default=-1,
+                    help="batched: tensor-core tile shape (0 persistent work list, 1..4 CTAs per item; "
+                         "-1 = pick order and tile per form with the autotuner)")
     ap.add_argument("--serve-seconds", type=float, default=3.0, help="serving: trace length at the offered rate")
     ap.add_argument("--serve-lanes", type=int, default=2, help="serving: groups on the GPU at once")
     ap.add_argument("--serve-group", type=int, default=64, help="serving: most requests per group")
