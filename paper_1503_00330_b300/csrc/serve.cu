@@ -14,8 +14,8 @@
 //      skipped without holding back later ones; a request whose scratch does
 //      not fit the pool ends the pass (first come, first served on memory);
 //   3. launches the group on the free lane: table upload, seed/state prologue,
-//      one persistent batched rollout launch over all (request, slot block)
-//      items in longest-first order, the batched cost-to-go and merge
+//      one batched rollout launch over all (request, slot block) items in
+//      longest-first order, the batched cost-to-go and merge
 //      launches, the copy of the plans to the host, and the receding-horizon
 //      advance of every agent of the group (plant step on the LWPR mean,
 //      shifted warm start, counter + 1).
@@ -387,9 +387,10 @@ int pi_server::launch(Lane &L)
         if (tc) {
             TcBatchArgs tb{reinterpret_cast<const TcArgs *>(d + lay.args), reinterpret_cast<const int2 *>(d + lay.ritems),
                            nr, d_ctl};
-            // a small group runs as one wave of clusters that split each block's outputs
-            const int split = tc_group_split(nr);
-            e = split > 1 ? launch_rollout_tc_group(tb, split, s) : launch_rollout_tc_batch(tb, grid, s);
+            // one item per CTA (a plain launch: the block scheduler fills SMs as
+            // items finish, also across lanes); a small group as one wave of
+            // clusters that split each block's outputs
+            e = launch_rollout_tc_group(tb, tc_group_split(nr), s);
         } else {
             BatchArgs fb{reinterpret_cast<const RolloutArgs *>(d + lay.args), reinterpret_cast<const int2 *>(d + lay.ritems),
                          nr, d_ctl, d_ctl + 1};
