@@ -256,12 +256,13 @@ int pi_batch_create(const pi_batch_item *items, int n, int precision, pi_batch *
  * persistent CTAs (0 = one per SM).  Re-captures the graph on the next update. */
 int pi_batch_set_schedule(pi_batch *b, int order, int grid);
 
-/* Tile shape of a tensor-core batch (used by the autotuner).  split = 0
- * (default): the persistent work list above, one CTA per item of 128 slots x
- * 12 outputs.  split = 1..4: a launch with one item per CTA (1) or per cluster
- * of `split` CTAs, each CTA evaluating 12/split of the item's outputs for its
- * 128 slots (the same results, bitwise).  FP32 batches accept only 0
- * (INVALID_ARG otherwise).  Re-captures the graph on the next update. */
+/* Tile shape of the batch (used by the autotuner).  split = 0 (default): the
+ * persistent work list above, one CTA per item (128 slots x 12 outputs with
+ * tensor cores, 64 slots x 12 outputs in FP32).  split = 1: a plain launch
+ * with one item per CTA.  split = 2..4 (tensor cores only): one item per
+ * cluster of `split` CTAs, each evaluating 12/split of the item's outputs for
+ * its 128 slots.  Every shape gives the same results, bitwise.  INVALID_ARG
+ * for split > 1 on an FP32 batch.  Re-captures the graph on the next update. */
 int pi_batch_set_tile(pi_batch *b, int split);
 
 /* Stream the batch's work is ordered after (and that waits for it); NULL = legacy default stream. */

@@ -3,8 +3,8 @@
 For a set of controllers it times every candidate schedule of the batched
 launch -- precision form (FP32 or tensor-core) x work-list order (controller
 order, longest block first, round robin) x, for the tensor-core form, the
-tile shape (persistent CTAs over 128-slot x 12-output items, or one item per
-CTA, or per pair of CTAs that split its outputs) -- on the device, keeps the
+tile shape (persistent CTAs over the slot-block items, or one item per CTA,
+or, with tensor cores, per pair of CTAs that split its outputs) -- on the device, keeps the
 fastest, and stores it in a JSON cache keyed by the batch's shape signature
 (per controller: K, T, L, M) and the device name, so later runs with the same
 shapes skip the search.  Both forms meet the same accuracy target, so the
@@ -25,7 +25,8 @@ DEFAULT_CACHE = os.environ.get("PI2RH_AUTOTUNE_CACHE",
                                os.path.join(os.path.expanduser("~"), ".cache", "pi2rh", "autotune.json"))
 ORDERS = ("as_given", "longest_first", "round_robin")
 TC_TILES = (0, 1, 2)     # persistent work list; one item per CTA; outputs split over 2 CTAs
-VERSION = 2
+FP32_TILES = (0, 1)      # persistent work list; one item per CTA
+VERSION = 3
 
 
 def signature(problems, device: int = 0) -> str:
@@ -86,7 +87,7 @@ def tune(problems, forms=("fp32", "tc"), orders=ORDERS, reps: int = 2, cache_pat
                       x0=[p.x0 for p in problems], u_nom=[p.u_nom for p in problems])
         for order in orders:
             batch.set_schedule(order)
-            for tile in (tc_tiles if form == "tc" else (0,)):
+            for tile in (tc_tiles if form == "tc" else FP32_TILES):
                 batch.set_tile(tile)
                 t0 = time.perf_counter()
                 ms = time_batch(batch, problems, reps=reps)

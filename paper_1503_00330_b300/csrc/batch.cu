@@ -121,7 +121,7 @@ int capture(pi_batch *b)
         } else {
             BatchArgs fb{static_cast<const RolloutArgs *>(b->d_args), b->d_ritems, b->n_ritems, b->d_counter,
                          b->items[0].ctx->d_err};
-            e = launch_rollout_fp32_batch(fb, b->grid, b->stream);
+            e = b->split > 0 ? launch_rollout_fp32_group(fb, b->stream) : launch_rollout_fp32_batch(fb, b->grid, b->stream);
         }
     }
     if (e == cudaSuccess) e = launch_scan_lse_batch(b->d_rargs, b->d_sitems, b->n_sitems, b->stream);
@@ -296,8 +296,8 @@ int pi_batch_set_tile(pi_batch *b, int split)
     if (!b) return bfail(PI_ERR_INVALID_ARG, "batch is NULL");
     if (split < 0 || split > 4)
         return bfail(PI_ERR_INVALID_ARG, "split must be 0..4");
-    if (split != 0 && b->form != PI_PRECISION_TC_FP16X3)
-        return bfail(PI_ERR_INVALID_ARG, "only tensor-core batches take a split tile shape");
+    if (split > 1 && b->form != PI_PRECISION_TC_FP16X3)
+        return bfail(PI_ERR_INVALID_ARG, "FP32 batches take tile shape 0 or 1 (outputs are not split)");
     int prev = -1;
     cudaGetDevice(&prev);
     if (prev != b->device) cudaSetDevice(b->device);

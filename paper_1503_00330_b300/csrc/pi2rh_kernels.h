@@ -64,6 +64,8 @@ struct BatchArgs {
 
 cudaError_t launch_rollout_fp32(const RolloutArgs &a, cudaStream_t s);
 cudaError_t launch_rollout_fp32_batch(const BatchArgs &b, int grid, cudaStream_t s);
+// Plain-launch form of the batch: one item per CTA (b.counter unused).
+cudaError_t launch_rollout_fp32_group(const BatchArgs &b, cudaStream_t s);
 cudaError_t launch_predict_fp32(const RolloutArgs &a, cudaStream_t s);
 
 // ---------------------------------------------------------------------------

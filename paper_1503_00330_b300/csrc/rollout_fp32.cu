@@ -488,6 +488,37 @@ __global__ void __launch_bounds__(NTHREADS, 1) rollout_fp32_batch_kernel(const _
             if (!mbar_wait_drain(&S.full[r % NSTAGE], (uint32_t)((r / NSTAGE) & 1))) atomicOr(b.err, DEVERR_TIMEOUT_DRAIN);
 }
 
+// One (controller, 64-slot block) item per CTA, arguments from the device
+// table (the plain-launch form of the batch: the block scheduler fills SMs as
+// items finish).
+__global__ void __launch_bounds__(NTHREADS, 1) rollout_fp32_group_kernel(const __grid_constant__ BatchArgs b)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ RolloutArgs s_args;
+    const Fp32Smem S = fp32_smem(smem);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int2 it = b.items[blockIdx.x];
+    if (tid == 0) {
+        s_args = b.args[it.x];
+        fp32_init_barriers(S);
+    }
+    __syncthreads();
+    const RolloutArgs &a = s_args;
+    for (int i = tid; i < a.cost.n_obs; i += NTHREADS) S.obs_s[i] = a.cost.obs[i];
+    __syncthreads();
+    if (warp == CW) {
+        if (lane != 0) return;
+        long long issued = 0;
+        fp32_producer<false>(a, S, 0, issued);
+        for (long long g = (issued > NSTAGE ? issued - NSTAGE : 0); g < issued; ++g)
+            if (!mbar_wait_drain(&S.full[g % NSTAGE], (uint32_t)((g / NSTAGE) & 1))) atomicOr(a.err, DEVERR_TIMEOUT_DRAIN);
+        return;
+    }
+    long long g = 0;
+    bool aborted = false;
+    fp32_consumer<false>(a, S, (long long)it.y * SLOTS, g, aborted);
+}
+
 std::atomic<uint64_t> g_attr_set[2];
 
 template <bool PREDICT>
@@ -518,7 +549,7 @@ cudaError_t launch_predict_fp32(const RolloutArgs &a, cudaStream_t s)
     return launch_impl<true>(a, s, (long long)a.n_pred);
 }
 
-std::atomic<uint64_t> g_batch_attr;
+std::atomic<uint64_t> g_batch_attr, g_group_attr;
 
 cudaError_t launch_rollout_fp32_batch(const BatchArgs &b, int grid, cudaStream_t s)
 {
@@ -526,6 +557,15 @@ cudaError_t launch_rollout_fp32_batch(const BatchArgs &b, int grid, cudaStream_t
     if (e != cudaSuccess) return e;
     if (grid <= 0) return cudaErrorInvalidValue;
     rollout_fp32_batch_kernel<<<grid, NTHREADS, SMEM_BYTES, s>>>(b);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rollout_fp32_group(const BatchArgs &b, cudaStream_t s)
+{
+    cudaError_t e = set_smem_once(g_group_attr, rollout_fp32_group_kernel, SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    if (b.n_items <= 0) return cudaErrorInvalidValue;
+    rollout_fp32_group_kernel<<<b.n_items, NTHREADS, SMEM_BYTES, s>>>(b);
     return cudaGetLastError();
 }
 

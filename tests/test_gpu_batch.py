@@ -76,8 +76,8 @@ def test_autotuner_picks_and_caches(tmp_path):
     cache = str(tmp_path / "tune.json")
     r1 = autotune.tune(probs, reps=1, cache_path=cache)
     assert r1["form"] in ("fp32", "tc") and r1["order"] in autotune.ORDERS and not r1["cached"]
-    assert r1["tile"] in autotune.TC_TILES and (r1["form"] == "tc" or r1["tile"] == 0)
-    assert len(r1["candidates"]) == len(autotune.ORDERS) * (1 + len(autotune.TC_TILES))
+    assert r1["tile"] in (autotune.TC_TILES if r1["form"] == "tc" else autotune.FP32_TILES)
+    assert len(r1["candidates"]) == len(autotune.ORDERS) * (len(autotune.FP32_TILES) + len(autotune.TC_TILES))
     r2 = autotune.tune(probs, reps=1, cache_path=cache)
     assert r2["cached"] and (r2["form"], r2["order"], r2["tile"]) == (r1["form"], r1["order"], r1["tile"])
 
@@ -104,5 +104,21 @@ def test_batch_tile_shapes_equal_single_updates(split):
     fctl = [Controller(probs[0].model, probs[0].cost)]
     fb = Batch(fctl, [probs[0].K], [probs[0].T], precision="fp32")
     with pytest.raises(PiError):
-        fb.set_tile(2)                    # the FP32 form has one tile shape
+        fb.set_tile(2)                    # FP32 items are not split over CTAs
     fb.close()
+
+
+def test_fp32_batch_plain_launch_equals_single_updates():
+    from paper_1503_00330_b300.api import Batch, Controller
+    probs = _problems()
+    ctls = [Controller(p.model, p.cost, M=p.M) for p in probs]
+    batch = Batch(ctls, [p.K for p in probs], [p.T for p in probs], precision="fp32",
+                  x0=[p.x0 for p in probs], u_nom=[p.u_nom for p in probs])
+    batch.set_tile(1)
+    seeds = [p.seed + 5 for p in probs]
+    u_b, c_b = batch.update([p.lam for p in probs], [p.sigma_u for p in probs], seeds)
+    batch.sync()
+    for i, (p, c) in enumerate(zip(probs, ctls)):
+        u, cs = c.update(p.x0, p.u_nom, p.K, p.T, p.lam, p.sigma_u, seeds[i])
+        c.sync()
+        assert torch.equal(u_b[i], u) and torch.equal(c_b[i], cs), f"controller {i}"
