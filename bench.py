@@ -340,7 +340,7 @@ def run_batched(args):
     dev = torch.device("cuda", 0)
     probs = W.batched(64, seed=0)
     # schedule per form from the autotuner (JSON-cached by batch shape), unless fixed on the command line
-    sched = {"fp32": ("longest_first", 0), "tc": ("longest_first", args.batch_tile)}
+    sched = {"fp32": ("longest_first", min(args.batch_tile, 1)), "tc": ("longest_first", args.batch_tile)}
     tuned = None
     if args.batch_tile < 0:
         from paper_1503_00330_b300 import autotune
@@ -360,8 +360,7 @@ def run_batched(args):
         batch = Batch(ctls, [p.K for p in probs], [p.T for p in probs], precision=form,
                       x0=[p.x0 for p in probs], u_nom=[p.u_nom for p in probs])
         batch.set_schedule(sched[form][0])
-        if form == "tc":
-            batch.set_tile(sched[form][1])
+        batch.set_tile(sched[form][1])
         lam = [p.lam for p in probs]
         su = [p.sigma_u for p in probs]
         for i in range(args.warmup):
@@ -640,8 +639,8 @@ def main():
                     help="form of the headline line (the other form is timed too and reported under 'forms')")
     ap.add_argument("--no-compare", action="store_true", help="skip timing the other form")
     ap.add_argument("--batch-tile", type=int, default=-1,
-                    help="batched: tensor-core tile shape (0 persistent work list, 1..4 CTAs per item; "
-                         "-1 = pick order and tile per form with the autotuner)")
+                    help="batched: tile shape (0 persistent work list, 1 one item per CTA, 2..4 tensor-core "
+                         "outputs split over CTAs; -1 = pick order and tile per form with the autotuner)")
     ap.add_argument("--serve-seconds", type=float, default=3.0, help="serving: trace length at the offered rate")
     ap.add_argument("--serve-lanes", type=int, default=2, help="serving: groups on the GPU at once")
     ap.add_argument("--serve-group", type=int, default=64, help="serving: most requests per group")
