@@ -828,41 +828,59 @@ cudaError_t prepare_tc()
     return cudaSuccess;
 }
 
+// CTAs of the single-controller kernel with clusters of NSPLIT that can be
+// resident at once (0 if the cluster shape cannot be launched).
 template <int NSPLIT>
-bool all_clusters_resident(long long blocks)
+long long resident_ctas()
 {
     if (prepare_tc<false, NSPLIT>() != cudaSuccess) {
         cudaGetLastError();
-        return false;
+        return 0;
     }
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (NSPLIT == 1) return sms;
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute at[1];
-    split_config(cfg, at, blocks, NSPLIT, nullptr);
+    split_config(cfg, at, sms, NSPLIT, nullptr);
     int clusters = 0;
     if (cudaOccupancyMaxActiveClusters(&clusters, rollout_tc_kernel<false, NSPLIT>, &cfg) != cudaSuccess) {
         cudaGetLastError();
-        return false;
+        return 0;
     }
-    return clusters >= blocks;
+    return (long long)clusters * NSPLIT;
 }
 
-// Output split of the single-controller rollout launch: the largest of 4, 3, 2
-// CTAs per slot block such that every cluster is resident at once (one wave);
-// 1 when the slot blocks alone fill the GPU.  PI2RH_TC_SPLIT = 1..4 forces a
-// value (the results are bitwise the same for every split).
+// Relative time of `items` 128-slot items whose outputs are split over s CTAs
+// when `resident` CTAs run at once: whole waves of CTAs that each carry 1/s of
+// an item's work, times the split's own cost (a CTA repeats the dynamics step
+// and exchanges its outputs).  The overheads are the ones measured on this
+// kernel (12 outputs, L = 2048): +3 % for 2 CTAs, +13 % for 3, +19 % for 4.
+double split_cost(long long items, int s, long long resident)
+{
+    static const double overhead[5] = {0.0, 0.0, 0.03, 0.13, 0.19};
+    if (resident <= 0) return 1e300;
+    const long long waves = (items * s + resident - 1) / resident;
+    return (double)waves / s * (1.0 + overhead[s]);
+}
+
+// Output split of the single-controller rollout launch: the split of least
+// split_cost (ties to the smaller split).  Small K spreads each block over a
+// cluster so that the SMs fill up; a few waves of blocks use pairs to shorten
+// the last, partly empty wave.  PI2RH_TC_SPLIT = 1..4 forces a value (the
+// results are bitwise the same for every split).
 int choose_split(long long blocks)
 {
     if (const char *e = getenv("PI2RH_TC_SPLIT")) {
         const int v = atoi(e);
         if (v >= 1 && v <= 4) return v;
     }
-    int dev = 0, sms = 148;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (blocks * 4 <= sms && all_clusters_resident<4>(blocks)) return 4;
-    if (blocks * 3 <= sms && all_clusters_resident<3>(blocks)) return 3;
-    if (blocks * 2 <= sms && all_clusters_resident<2>(blocks)) return 2;
-    return 1;
+    const long long res[5] = {0, resident_ctas<1>(), resident_ctas<2>(), resident_ctas<3>(), resident_ctas<4>()};
+    int best = 1;
+    for (int sp = 2; sp <= 4; ++sp)
+        if (split_cost(blocks, sp, res[sp]) < split_cost(blocks, best, res[best])) best = sp;
+    return best;
 }
 
 template <int NSPLIT>
