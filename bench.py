@@ -143,6 +143,11 @@ def workload(name: str, seed: int):
         return W.small(seed), "small: K=256, T=50, L=64 x 12 outputs, 4 obstacles"
     if name == "precision":
         return W.precision(seed), "precision: K=65536, T=100, L=2048 x 12 outputs, cond(D) logU[1,1e3]"
+    if name == "subrollouts":
+        # the paper's largest model-uncertainty setting (1000 rollouts x 32 sub-rollouts x 50 steps)
+        # on the realtime model; a rollout-step here counts every sub-rollout step
+        p = W.problem(1024, 50, 512, seed, n_obs=16, M=32)
+        return p, "subrollouts: K=1024 rollouts x M=32 sub-rollouts, T=50, L=512 x 12 outputs, 16 obstacles"
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -631,7 +636,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=["realtime", "realtime_short", "small", "precision", "precision_short", "batched",
-                                                   "serving"], default="realtime")
+                                                   "serving", "subrollouts"], default="realtime")
     ap.add_argument("--cpu-sample", type=int, default=256, help="rollouts in the CPU-baseline sample")
     ap.add_argument("--ref-sample", type=int, default=64, help="rollouts per reference-arm step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
