@@ -185,10 +185,11 @@ def reduce_max(dist, v: float, device):
 
 
 def cpu_baseline(p, k_sample: int):
-    """FP64 oracle on the first k_sample rollouts of one update of the workload
-    (all host threads), and on a 1/8 sample on one thread."""
+    """FP64 oracle on the first k_sample / M rollouts of one update of the
+    workload (all host threads), and on a 1/8 sample on one thread."""
     from oracle import oracle as O
     O.build()
+    k_sample = max(1, k_sample // max(p.M, 1))
     t0 = time.perf_counter()
     O.pi_update(p.model, p.cost, p.x0, p.u_nom, k_sample, p.T, p.lam, p.sigma_u, p.seed, M=p.M,
                 model_noise=p.model_noise)
