@@ -599,6 +599,8 @@ def run_ours(args):
 
     peaks = measured_peaks()
     roofline = form_roofline(args.precision, rollout_ms, K, T, M, L, dev, peaks, args.workload)
+    from paper_1503_00330_b300.api import pipe_rates
+    rates = pipe_rates(local)   # measured pipe rates: context beside the unit-count FP32 peak
     roofline["rollout_share_of_step"] = sum(rollout_ms) / sum(step_ms)
     reduction = reduction_rooflines(scan_ms, merge_ms, K, T, peaks)
     forms = {args.precision: {"value": value, "ms_per_update": 1e3 * total_s / args.steps,
@@ -620,6 +622,8 @@ def run_ours(args):
                     "d2h_bytes_per_step": (T * 4 + K) * 4},
             "roofline": roofline,
             "reduction_kernels": reduction,
+            "measured_pipe_rates": {**rates, "note": "FFMA2 / MUFU ex2 chains on every SM, event-timed; "
+                                                     "the FP32 roofline keeps the unit-count peak"},
             "forms": forms,
             "paper_context": PAPER_CONTEXT,
             "clocks": clocks.summary()}

@@ -420,6 +420,12 @@ int pi_server_get_stats(const pi_server *s, pi_server_stats *out);
  * and frees the server.  NULL is accepted. */
 void pi_server_destroy(pi_server *s);
 
+/* Measured issue rates of the pipes the FP32 form leans on, on `device`: packed
+ * FP32 FMA (FFMA2) in TFLOP/s and the MUFU base-2 exponential in results/s.
+ * Independent dependency chains on every SM, CUDA-event timed; synchronous.
+ * Context for the roofline (the paper has no counterpart). */
+int pi_debug_pipe_rates(int device, double *ffma_tflops, double *ex2_per_s);
+
 /* Host-only ABI check (no GPU): writes, for the public structs in this order
  * -- pi_lwpr_params, pi_cost_params, pi_opts, pi_batch_item, pi_server_opts,
  * pi_serve_request, pi_serve_done, pi_serve_arrival, pi_server_stats -- their

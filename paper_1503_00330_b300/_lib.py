@@ -131,6 +131,8 @@ _SIGS = {
     "pi_server_destroy": (None, [_vp]),
     "pi_debug_struct_layout": (ctypes.c_int, [ctypes.POINTER(ctypes.c_size_t), ctypes.c_int,
                                               ctypes.POINTER(ctypes.c_int)]),
+    "pi_debug_pipe_rates": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                           ctypes.POINTER(ctypes.c_double)]),
     "pi_debug_pool": (ctypes.c_int, [ctypes.c_size_t, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_size_t),
                                      ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int)]),
     "pi_debug_noise": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp]),

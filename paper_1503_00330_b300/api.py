@@ -430,6 +430,14 @@ class Server:
             pass
 
 
+def pipe_rates(device: int = 0) -> dict:
+    """Measured FFMA2 TFLOP/s and MUFU ex2 results/s of the device (see pi_debug_pipe_rates)."""
+    lib = _lib.load()
+    f, e = ctypes.c_double(), ctypes.c_double()
+    check(lib.pi_debug_pipe_rates(int(device), ctypes.byref(f), ctypes.byref(e)))
+    return {"ffma_tflops": f.value, "ex2_per_s": e.value}
+
+
 def debug_pool(capacity: int, ops):
     """Runs the serving pool allocator on the host: ops = [("alloc", nbytes) | ("free", op_index)].
 
