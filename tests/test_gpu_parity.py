@@ -355,3 +355,20 @@ def test_precision_workload_sampled(oracle):
     print("precision K=128: u err", eu, "cost err", ec)
     assert np.all(eu <= U_TOL)
     assert ec <= S_TOL
+
+
+@pytest.mark.parametrize("form", ["fp32", "tc"])
+def test_u_out_may_alias_u_nominal(form):
+    """The header lets u_out alias u_nominal (an in-place plan update): the
+    result equals the one written to a separate buffer, bitwise."""
+    from paper_1503_00330_b300.api import Controller
+    p = W.problem(300, 17, 40, seed=8, n_obs=3)
+    p.u_nom = np.random.default_rng(1).normal(0, 0.2, (p.T, 4)).astype(np.float32)
+    ctl = Controller(p.model, p.cost, precision=form)
+    u_sep, c_sep = ctl.update(p.x0, p.u_nom, p.K, p.T, p.lam, p.sigma_u, p.seed)
+    ctl.sync()
+    plan = torch.as_tensor(p.u_nom, device="cuda").clone()
+    u_in, c_in = ctl.update(p.x0, plan, p.K, p.T, p.lam, p.sigma_u, p.seed, u_out=plan)
+    ctl.sync()
+    assert u_in.data_ptr() == plan.data_ptr()
+    assert torch.equal(plan, u_sep) and torch.equal(c_in, c_sep)
