@@ -382,7 +382,6 @@ int pi_server::launch(Lane &L)
                                     reinterpret_cast<const float *>(d + lay.x0), d_x0, d_seed, d_ctr);
         e = cudaGetLastError();
     }
-    const int grid = std::min(sms, nr);
     if (e == cudaSuccess) {
         if (tc) {
             TcBatchArgs tb{reinterpret_cast<const TcArgs *>(d + lay.args), reinterpret_cast<const int2 *>(d + lay.ritems),
@@ -394,7 +393,7 @@ int pi_server::launch(Lane &L)
         } else {
             BatchArgs fb{reinterpret_cast<const RolloutArgs *>(d + lay.args), reinterpret_cast<const int2 *>(d + lay.ritems),
                          nr, d_ctl, d_ctl + 1};
-            e = launch_rollout_fp32_batch(fb, grid, s);
+            e = launch_rollout_fp32_group(fb, s);   // one item per CTA
         }
     }
     const ReduceArgs *d_rargs = reinterpret_cast<const ReduceArgs *>(d + lay.rargs);
