@@ -22,7 +22,8 @@
 //                  copy per contiguous run, one barrier pair per group) into a
 //                  ring of NSLOT chunk slots, and of the per-field constants
 //                  (cs, cy, sigma^2) into a 4-deep constant ring;
-//   warp 1 lane 0: MMA issuer -- per tile of 128 fields, 33 MMAs (M=128,
+//   warp 1:        MMA issuer (the whole warp runs the loop, one elected
+//                  lane issues) -- per tile of 128 fields, 33 MMAs (M=128,
 //                  N=128, K=16; S: 10 K steps x 3 split products, Y: 1 x 3)
 //                  into one of two TMEM accumulator buffers, releasing each
 //                  chunk group as soon as its MMAs complete;
@@ -285,9 +286,13 @@ __device__ bool tc_producer_item(const TcArgs &a, const TcSmem &S, TcProducer &P
     return ok;
 }
 
-// MMA issuer (lane 0 of warp 1) for one work item; false after a timeout.
-// Waits once per chunk group and releases the group's slots with one commit
-// after its last MMA; the group's chunk c sits in ring slot group * CPG + c.
+// MMA issuer (all of warp 1) for one work item; false after a timeout.
+// The whole warp runs the loop, so every counter and descriptor is
+// warp-uniform, and the lane elect.sync picks issues the MMAs and commits.  (A
+// lone lane of a diverged warp issued them about 1.4x slower whenever the
+// epilogue warps sharing its sub-partition were busy.)  Waits once per chunk
+// group and releases the group's slots with one commit after its last MMA;
+// the group's chunk c sits in ring slot group * CPG + c.
 template <bool PREDICT>
 __device__ bool tc_issuer_item(const TcArgs &a, const TcSmem &S, uint32_t tbase, TcIssuer &I, int n_out)
 {
@@ -300,16 +305,12 @@ __device__ bool tc_issuer_item(const TcArgs &a, const TcSmem &S, uint32_t tbase,
     const long long nchunk = (long long)G * nsteps * NCH;
     long long &g = I.g, &ts = I.ts;
     const uint32_t idesc = idesc_f16_f32(BM, TNF);
-    const uint32_t phi_hi = smem_u32(smem + OFF_PHI_HI), phi_lo = smem_u32(smem + OFF_PHI_LO);
-    // descriptors: A = feature tile K step j (rows 2560 B apart), B = a
-    // chunk half (128 rows x 16 K, rows 256 B apart); slot/half offsets
-    // are added to the 14-bit start field (addresses stay < 256 KB).
-    uint64_t ah[KF / 16], al[KF / 16];
-#pragma unroll
-    for (int j = 0; j < KF / 16; ++j) {
-        ah[j] = smem_desc_kmajor(phi_hi + j * 256, 128, 16 * KF);
-        al[j] = smem_desc_kmajor(phi_lo + j * 256, 128, 16 * KF);
-    }
+    // descriptors: A = feature tile K step j (rows 2560 B apart; step j at
+    // +256 B), B = a chunk half (128 rows x 16 K, rows 256 B apart); step,
+    // slot and half offsets are added to the 14-bit start field (>> 4; the
+    // addresses stay < 256 KB).
+    const uint64_t a_hi = smem_desc_kmajor(smem_u32(smem + OFF_PHI_HI), 128, 16 * KF);
+    const uint64_t a_lo = smem_desc_kmajor(smem_u32(smem + OFF_PHI_LO), 128, 16 * KF);
     const uint64_t b0 = smem_desc_kmajor(smem_u32(smem + OFF_RING), 128, 256);
     // group state: counter, ring group, its phase, chunk within it
     long long grp = I.grp;
@@ -318,37 +319,34 @@ __device__ bool tc_issuer_item(const TcArgs &a, const TcSmem &S, uint32_t tbase,
     long long ci = 0;   // chunks of this item consumed
     bool ok = true;
     for (int t = 0; t < nsteps && ok; ++t, ++ts) {
-        ok = mbar_wait_bounded(phi_ready, (uint32_t)(ts & 1), abort_flag);
+        ok = __all_sync(0xffffffffu, mbar_wait_bounded(phi_ready, (uint32_t)(ts & 1), abort_flag));
         tc_fence_after();
         for (int jt = 0; jt < G && ok; ++jt, ++g) {
             const int buf = (int)(g & 1);
-            if (g >= 2) ok = mbar_wait_bounded(&acc_empty[buf], (uint32_t)(((g >> 1) - 1) & 1), abort_flag);
+            if (g >= 2)
+                ok = __all_sync(0xffffffffu,
+                                mbar_wait_bounded(&acc_empty[buf], (uint32_t)(((g >> 1) - 1) & 1), abort_flag));
             if (!ok) break;
             tc_fence_after();
             const uint32_t dS = tbase + buf * 256, dY = dS + 128;
 #pragma unroll
             for (int j = 0; j < NCH; ++j) {
                 if (cg == 0 && ok) {
-                    ok = mbar_wait_bounded(&full[gs], gph, abort_flag);
+                    ok = __all_sync(0xffffffffu, mbar_wait_bounded(&full[gs], gph, abort_flag));
                     tc_fence_after();
                 }
                 if (ok) {
                     const uint64_t bh = b0 + (uint64_t)((gs * CPG + cg) * (TC_CHUNK_BYTES >> 4));
                     const uint64_t bl = bh + (uint64_t)(TC_HALF_CHUNK >> 4);
-                    if (j < NCH - 1) {
-                        mma_f16(dS, ah[j], bh, idesc, j > 0);
-                        mma_f16(dS, ah[j], bl, idesc, true);
-                        mma_f16(dS, al[j], bh, idesc, true);
-                    } else {
-                        mma_f16(dY, ah[0], bh, idesc, false);
-                        mma_f16(dY, ah[0], bl, idesc, true);
-                        mma_f16(dY, al[0], bh, idesc, true);
-                    }
+                    if (j < NCH - 1)
+                        mma3_elect(dS, a_hi + (uint64_t)(j * 16), a_lo + (uint64_t)(j * 16), bh, bl, idesc, j > 0);
+                    else
+                        mma3_elect(dY, a_hi, a_lo, bh, bl, idesc, 0u);
                 }
                 ++ci;
                 if (++cg == CPG || ci == nchunk) {
                     if (ok) {
-                        mma_commit(&empty[gs]);
+                        commit_elect(&empty[gs]);
                         I.grp_committed = grp;
                     }
                     cg = 0;
@@ -359,7 +357,7 @@ __device__ bool tc_issuer_item(const TcArgs &a, const TcSmem &S, uint32_t tbase,
                     }
                 }
             }
-            if (ok) mma_commit(&acc_full[buf]);
+            if (ok) commit_elect(&acc_full[buf]);
         }
     }
     I.grp = grp;
@@ -689,10 +687,8 @@ __device__ __forceinline__ void tc_cta(const TcArgs &a, long long slot_base, uns
         if (lane == 0 && !tc_producer_item<PREDICT>(a, S, P, o_begin, n_out)) tc_flag_abort(a, S, DEVERR_TIMEOUT_EMPTY);
         __syncwarp();
     } else if (warp == 1) {
-        if (lane == 0) {
-            issuer_ok = tc_issuer_item<PREDICT>(a, S, tbase, I, n_out);
-            if (!issuer_ok) tc_flag_abort(a, S, DEVERR_TIMEOUT_FULL);
-        }
+        issuer_ok = tc_issuer_item<PREDICT>(a, S, tbase, I, n_out);
+        if (!issuer_ok && lane == 0) tc_flag_abort(a, S, DEVERR_TIMEOUT_FULL);
         __syncwarp();
     } else {
         long long g = 0;
@@ -770,9 +766,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) rollout_tc_batch_kernel(const __g
             if (lane == 0 && !tc_producer_item<false>(a, S, P, 0, NY)) tc_flag_abort(a, S, DEVERR_TIMEOUT_EMPTY);
             __syncwarp();
         } else if (warp == 1) {
-            if (lane == 0 && issuer_ok) {
+            if (issuer_ok) {
                 issuer_ok = tc_issuer_item<false>(a, S, tbase, I, NY);
-                if (!issuer_ok) tc_flag_abort(a, S, DEVERR_TIMEOUT_FULL);
+                if (!issuer_ok && lane == 0) tc_flag_abort(a, S, DEVERR_TIMEOUT_FULL);
             }
             __syncwarp();
         } else {

@@ -82,6 +82,37 @@ __device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a_desc, uint64
         : "memory");
 }
 
+// The three MMAs of one K step of the split-precision product,
+//   D (+)= A_hi B_hi + A_hi B_lo + A_lo B_hi,
+// executed by a whole converged warp and issued by the one lane that
+// elect.sync picks (the same lane on every call with all lanes active).  The
+// first MMA overwrites D when acc_first is 0.
+__device__ __forceinline__ void mma3_elect(uint32_t d_tmem, uint64_t a_hi, uint64_t a_lo, uint64_t b_hi,
+                                           uint64_t b_lo, uint32_t idesc, uint32_t acc_first)
+{
+    asm volatile(
+        "{\n\t.reg .pred p, t, e;\n\t"
+        "elect.sync _|e, 0xffffffff;\n\t"
+        "setp.ne.u32 p, %6, 0;\n\t"
+        "setp.eq.u32 t, %6, %6;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %3, %5, p;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %4, %5, t;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %2, %3, %5, t;\n\t}" ::"r"(d_tmem),
+        "l"(a_hi), "l"(a_lo), "l"(b_hi), "l"(b_lo), "r"(idesc), "r"(acc_first)
+        : "memory");
+}
+
+// tcgen05.commit from the lane elect.sync picks (the lane that issued the
+// MMAs of mma3_elect): arrives on the mbarrier once they complete.
+__device__ __forceinline__ void commit_elect(uint64_t *bar)
+{
+    asm volatile(
+        "{\n\t.reg .pred e;\n\t"
+        "elect.sync _|e, 0xffffffff;\n\t"
+        "@e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n\t}" ::"r"(smem_u32(bar))
+        : "memory");
+}
+
 // Arrives on an mbarrier once all prior tcgen05 async operations of this thread complete.
 __device__ __forceinline__ void mma_commit(uint64_t *bar)
 {
