@@ -210,14 +210,18 @@ namespace {
 // Packs the model for the tensor-core form: per output and tile of 128
 // fields, 11 chunks of [hi | lo] fp16 coefficient blocks in the K-major
 // core-matrix layout the MMAs read (chunk j < 10: the S coefficients of K step
-// j; chunk 10: the Y coefficients), and the fp32 per-field constants (see
-// rollout_tc.cu for the algebra).
+// j, with cs_j as the weight of the constant feature 152; chunk 10: the Y
+// coefficients), and the fp32 per-field constants cy_j and sigma_j^2 (see
+// rollout_tc.cu for the algebra).  The constant feature is 1 + 2^-14 as
+// hi + lo, so its weight's lo part is cs_lo - 2^-14 cs_hi; a padding field of
+// a ragged last tile has the weight -inf (hi; lo 0) and all other weights 0,
+// so its exponent is exactly -inf and its softmax weight 0.
 void pack_tc(const pi_lwpr_params *lw, int tiles, std::vector<unsigned char> &wt, std::vector<float> &wc)
 {
     const int L = lw->L, TF = TC_TILE_FIELDS;
     const double kap = 0.72134752044448170368;   // log2(e) / 2
     wt.assign((size_t)NY * tiles * TC_TILE_BYTES, 0);
-    wc.assign((size_t)NY * tiles * 3 * TF, 0.0f);
+    wc.assign((size_t)NY * tiles * 2 * TF, 0.0f);
     auto put = [&](unsigned char *tile, int chunk, int row, int kin, double v) {
         const __half hi = __float2half_rn((float)v);
         const __half lo = __float2half_rn((float)(v - (double)__half2float(hi)));
@@ -229,11 +233,14 @@ void pack_tc(const pi_lwpr_params *lw, int tiles, std::vector<unsigned char> &wt
     for (int o = 0; o < NY; ++o)
         for (int tt = 0; tt < tiles; ++tt) {
             unsigned char *tile = wt.data() + ((size_t)o * tiles + tt) * TC_TILE_BYTES;
-            float *cst = wc.data() + ((size_t)o * tiles + tt) * 3 * TF;
+            float *cst = wc.data() + ((size_t)o * tiles + tt) * 2 * TF;
             for (int i = 0; i < TF; ++i) {
                 const int j = tt * TF + i;
                 if (j >= L) {
-                    cst[i] = -INFINITY;          // padding field: zero weight
+                    // padding field: exponent -inf, zero weight
+                    unsigned char *base = tile + (size_t)(TC_CONST_FEATURE / 16) * TC_CHUNK_BYTES;
+                    const uint32_t o16 = kmajor_offset(i, TC_CONST_FEATURE % 16, 16);
+                    *reinterpret_cast<__half *>(base + o16) = __ushort_as_half((unsigned short)0xFC00u);
                     continue;
                 }
                 const size_t f = (size_t)o * L + j;
@@ -257,14 +264,25 @@ void pack_tc(const pi_lwpr_params *lw, int tiles, std::vector<unsigned char> &wt
                         const int ra = tc_feat_row(k), cb = tc_feat_col(k);
                         v = ra == cb ? -kap * (double)D[ra * NZ + ra]
                                      : -kap * ((double)D[ra * NZ + cb] + (double)D[cb * NZ + ra]);
+                    } else if (k == TC_CONST_FEATURE) {
+                        // cs_j against the constant feature 1 + 2^-14 (hi + lo):
+                        // hi*hi + hi*lo + lo*hi = cs_hi + (cs_lo - 2^-14 cs_hi) + 2^-14 cs_hi
+                        const double cs = -kap * cDc;
+                        const __half hi = __float2half_rn((float)cs);
+                        const double hd = (double)__half2float(hi);
+                        const __half lo = __float2half_rn((float)(cs - hd - 0x1p-14 * hd));
+                        unsigned char *base = tile + (size_t)(k / 16) * TC_CHUNK_BYTES;
+                        const uint32_t o16 = kmajor_offset(i, k % 16, 16);
+                        *reinterpret_cast<__half *>(base + o16) = hi;
+                        *reinterpret_cast<__half *>(base + TC_HALF_CHUNK + o16) = lo;
+                        continue;
                     }
                     put(tile, k / 16, i, k % 16, v);
                 }
                 for (int k = 0; k < 16; ++k) put(tile, TC_KF / 16, i, k, (double)beta[k]);
-                cst[i] = (float)(-kap * cDc);
-                cst[TF + i] = (float)((double)lw->b[f] - bc);
+                cst[i] = (float)((double)lw->b[f] - bc);
                 const double sg = (double)lw->sigma[f];
-                cst[2 * TF + i] = (float)(sg * sg);
+                cst[TF + i] = (float)(sg * sg);
             }
         }
 }

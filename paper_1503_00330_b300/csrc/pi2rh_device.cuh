@@ -240,6 +240,18 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
     }
 }
 
+// True in the one lane of a converged warp that elect.sync picks.
+__device__ __forceinline__ bool elect_one()
+{
+    uint32_t e;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "elect.sync _|p, 0xffffffff;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(e));
+    return e != 0;
+}
+
 // Bounded wait with no abort check (used to drain copies at exit).
 __device__ __forceinline__ bool mbar_wait_drain(uint64_t *bar, uint32_t parity)
 {

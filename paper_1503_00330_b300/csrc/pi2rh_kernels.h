@@ -73,16 +73,17 @@ cudaError_t launch_predict_fp32(const RolloutArgs &a, cudaStream_t s);
 // creation as 11 chunks of 8 KB in the exact shared-memory image the MMAs
 // read (fp16, K-major core-matrix layout, 128 rows x 16 K per half-chunk):
 // chunk j < 10 = [S hi | S lo] of K step j, chunk 10 = [Y hi | Y lo]; the
-// per-field constants (cs, cy, sigma^2; 3 x 128 floats) are packed separately.
+// per-field constants (cy, sigma^2; 2 x 128 floats) are packed separately.
 // ---------------------------------------------------------------------------
 constexpr int TC_SLOTS = 128;           // rollout slots per CTA (MMA M)
 constexpr int TC_TILE_FIELDS = 128;     // fields per tile (MMA N)
-constexpr int TC_KF = 160;              // feature columns: z (16), z_a z_b (136), 0 (8)
+constexpr int TC_KF = 160;              // feature columns: z (16), z_a z_b (136), 1, 0 (7)
 constexpr int TC_HALF_CHUNK = TC_TILE_FIELDS * 16 * 2;                 // 4 KB
 constexpr int TC_CHUNK_BYTES = 2 * TC_HALF_CHUNK;                      // 8 KB
 constexpr int TC_CHUNKS_PER_TILE = TC_KF / 16 + 1;                     // 11
 constexpr int TC_TILE_BYTES = TC_CHUNKS_PER_TILE * TC_CHUNK_BYTES;     // 90,112
-constexpr int TC_CONST_BYTES = 3 * TC_TILE_FIELDS * 4;                 // 1,536
+constexpr int TC_CONST_BYTES = 2 * TC_TILE_FIELDS * 4;                 // 1,024
+constexpr int TC_CONST_FEATURE = 152;   // feature column holding the constant 1 (+ 2^-14 in the lo part)
 
 // Quadratic feature k (16 <= k < 152) is z_a z_b with (a, b) the (k-16)-th
 // entry of the row-major upper triangle; features k < 16 are z_k.

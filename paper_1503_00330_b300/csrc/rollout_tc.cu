@@ -3,25 +3,31 @@
 // The receptive-field exponents and local predictions (Sec. 2, Eq. 1) of all
 // 12 L fields are evaluated for 128 rollout slots at a time as two GEMMs on
 // the 5th-generation tensor cores:
-//   s_j = -(1/2) log2(e) (z - c_j)^T D_j (z - c_j)
-//       = phi(z) . w_j + cs_j,   phi(z) = [z_a (16), z_a z_b (a <= b, 136), 0 (8)]
+//   s_j = -(1/2) log2(e) (z - c_j)^T D_j (z - c_j) = phi(z) . w_j,
+//         phi(z) = [z_a (16), z_a z_b (a <= b, 136), 1, 0 (7)]
 //   y_j = b_j + beta_j . (z - c_j) = z . beta_j + cy_j
-// with w_j = [2k (D_s c_j)_a, -k D'_ab, 0], k = log2(e)/2, D_s = (D + D^T)/2,
-// D'_aa = D_aa, D'_ab = D_ab + D_ba; the constants cs_j = -k c_j^T D_s c_j and
-// cy_j = b_j - beta_j . c_j are added in FP32 in the epilogue.
+// with w_j = [2k (D_s c_j)_a, -k D'_ab, cs_j, 0], k = log2(e)/2,
+// D_s = (D + D^T)/2, D'_aa = D_aa, D'_ab = D_ab + D_ba and the constant
+// cs_j = -k c_j^T D_s c_j (the weight of the constant feature); the constant
+// cy_j = b_j - beta_j . c_j is added in FP32 in the epilogue.  A padding field
+// of a ragged last tile has the weight -inf on the constant feature and 0
+// elsewhere, so its exponent is -inf and its softmax weight 0.
 //
 // Precision: operands are split into fp16 hi + lo parts and each product is
 // formed as hi*hi + hi*lo + lo*hi (three tcgen05.mma kind::f16 per K step,
 // fp32 accumulation in tensor memory); the dropped lo*lo term is ~2^-22
-// relative, so the exponents carry FP32-level accuracy.
+// relative, so the exponents carry FP32-level accuracy.  The constant feature
+// is split as 1 + 2^-14 (its weight's lo part compensates), so that the
+// lo*hi product of a padding field is 2^-14 * -inf, never 0 * -inf.
 //
 // Roles (one CTA per SM, 128 slots, 320 threads):
-//   warp 0 lane 0: producer -- 1-D bulk copies (TMA) of the pre-packed
-//                  coefficient chunks (8 KB: the hi and lo coefficient blocks
-//                  of one K step for 128 fields) in groups of CPG chunks (one
+//   warp 0:        producer (one elected lane issues) -- 1-D bulk copies
+//                  (TMA) of the pre-packed coefficient chunks (8 KB: the hi
+//                  and lo coefficient blocks of one K step for 128 fields)
+//                  in groups of CPG chunks (one
 //                  copy per contiguous run, one barrier pair per group) into a
 //                  ring of NSLOT chunk slots, and of the per-field constants
-//                  (cs, cy, sigma^2) into a 4-deep constant ring;
+//                  (cy, sigma^2) into a 4-deep constant ring;
 //   warp 1:        MMA issuer (the whole warp runs the loop, one elected
 //                  lane issues) -- per tile of 128 fields, 33 MMAs (M=128,
 //                  N=128, K=16; S: 10 K steps x 3 split products, Y: 1 x 3)
@@ -29,9 +35,10 @@
 //                  chunk group as soon as its MMAs complete;
 //   warps 2-9:     epilogue -- tcgen05.ld of S and Y, online base-2 softmax
 //                  per output on packed FP32x2 operations (chunks of 16
-//                  fields, one rescale per chunk), merge of the two column
-//                  halves, then the dynamics step (cost, Euler step, Philox
-//                  noise) and the feature tile of the next step.
+//                  fields, one rescale per chunk; running sums of w, w e and
+//                  w (e^2 + sigma^2)), merge of the two column halves, then
+//                  the dynamics step (cost, Euler step, Philox noise) and
+//                  the feature tile of the next step.
 // Launch forms: one CTA per 128-slot block; clusters of 2-4 CTAs that split a
 // block's 12 outputs when the blocks alone would leave SMs idle (means and
 // variances exchanged through distributed shared memory); a persistent
@@ -70,8 +77,9 @@ constexpr int OFF_PHI_HI = 0;
 constexpr int OFF_PHI_LO = OFF_PHI_HI + PHI_BYTES;
 constexpr int OFF_RING = OFF_PHI_LO + PHI_BYTES;
 constexpr int OFF_CONST = OFF_RING + NSLOT * TC_CHUNK_BYTES;
-constexpr int OFF_PART = OFF_CONST + NCONST * TC_CONST_BYTES;   // [2][5][BM]
-constexpr int OFF_Z = OFF_PART + 2 * 5 * BM * 4;                // [NZ][BM]
+constexpr int NSUM = 4;                 // softmax state: max, sums of w, w e, w (e^2 + sigma^2)
+constexpr int OFF_PART = OFF_CONST + NCONST * TC_CONST_BYTES;   // [2][NSUM][BM]
+constexpr int OFF_Z = OFF_PART + 2 * NSUM * BM * 4;             // [NZ][BM]
 constexpr int OFF_X = OFF_Z + NZ * BM * 4;                      // [NX][BM]
 constexpr int OFF_Y = OFF_X + NX * BM * 4;                      // [NY][BM]
 constexpr int OFF_V = OFF_Y + NY * BM * 4;
@@ -90,12 +98,16 @@ static_assert(SMEM_BYTES <= 232448, "shared memory budget");
 
 constexpr uint32_t TMEM_COLS = 512;     // 2 buffers x (S 128 + Y 128)
 
-// Feature k of phi: k < 16 -> z_k * 1; 16 <= k < 152 -> z_a z_b; k >= 152 -> 0.
+// Feature k of phi: k < 16 -> z_k * 1; 16 <= k < 152 -> z_a z_b; 152 -> 1
+// (split as 1 + 2^-14 by split_pair); k > 152 -> 0.
 __host__ __device__ constexpr int feat_a(int k) { return k < 16 ? k : tc_feat_row(k); }
 __host__ __device__ constexpr int feat_b(int k) { return k < 16 ? 16 : tc_feat_col(k); }
 
+// Online softmax state of one output for one slot: the running maximum m of
+// the exponents and, relative to 2^m, the sums of w, w e and w (e^2 +
+// sigma^2), e = y_j - y_ref.
 struct Soft {
-    float m, s0, s1, s2, s3;
+    float m, s0, s1, s2;
 };
 
 __device__ __forceinline__ void merge_into(Soft &a, const Soft &b)
@@ -106,8 +118,45 @@ __device__ __forceinline__ void merge_into(Soft &a, const Soft &b)
     a.s0 = fmaf(a.s0, ca, b.s0 * cb);
     a.s1 = fmaf(a.s1, ca, b.s1 * cb);
     a.s2 = fmaf(a.s2, ca, b.s2 * cb);
-    a.s3 = fmaf(a.s3, ca, b.s3 * cb);
     a.m = M;
+}
+
+__device__ __forceinline__ float max3(float a, float b, float c)
+{
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
+// Folds the 16 fields of one chunk (exponents sv, local predictions without
+// their constant yv) into the softmax state, two fields per packed FP32x2
+// operation (even and odd columns accumulate separately and are added at the
+// end).
+__device__ __forceinline__ void soft_chunk(Soft &st, const float (&sv)[16], const float (&yv)[16],
+                                           const float2 *cy2, const float2 *cv2, float yref)
+{
+    float2 sp[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) sp[i] = make_float2(sv[2 * i], sv[2 * i + 1]);
+    const float m0 = max3(sp[0].x, sp[0].y, sp[1].x), m1 = max3(sp[1].y, sp[2].x, sp[2].y);
+    const float m2 = max3(sp[3].x, sp[3].y, sp[4].x), m3 = max3(sp[4].y, sp[5].x, sp[5].y);
+    const float m4 = max3(sp[6].x, sp[6].y, sp[7].x);
+    const float mn = max3(max3(m0, m1, m2), max3(m3, m4, sp[7].y), st.m);
+    const float mns = mn == -INFINITY ? 0.0f : mn;
+    const float sc = ex2(st.m - mns);
+    const float2 nm = make_float2(-mns, -mns), ny = make_float2(-yref, -yref);
+    float2 s0 = make_float2(st.s0 * sc, 0.0f), s1 = make_float2(st.s1 * sc, 0.0f);
+    float2 s2 = make_float2(st.s2 * sc, 0.0f);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const float2 d = __fadd2_rn(sp[i], nm);
+        const float2 w = make_float2(ex2(d.x), ex2(d.y));
+        const float2 e = __fadd2_rn(make_float2(yv[2 * i], yv[2 * i + 1]), __fadd2_rn(cy2[i], ny));
+        s0 = __fadd2_rn(s0, w);
+        s1 = __ffma2_rn(w, e, s1);
+        s2 = __ffma2_rn(w, __ffma2_rn(e, e, cv2[i]), s2);
+    }
+    st = Soft{mn, s0.x + s0.y, s1.x + s1.y, s2.x + s2.y};
 }
 
 __device__ __forceinline__ uint32_t pack_h2(__half lo, __half hi)
@@ -121,6 +170,8 @@ __device__ __forceinline__ float feature(const float (&zext)[17])
     if constexpr (K < 152) {
         constexpr int fa = feat_a(K), fb = feat_b(K);
         return zext[fa] * zext[fb];
+    } else if constexpr (K == TC_CONST_FEATURE) {
+        return 1.0f;
     } else {
         return 0.0f;
     }
@@ -132,7 +183,10 @@ __device__ __forceinline__ void split_pair(const float (&zext)[17], uint32_t &hw
     const float f0 = feature<K>(zext), f1 = feature<K + 1>(zext);
     const __half h0 = __float2half_rn(f0), h1 = __float2half_rn(f1);
     hw = pack_h2(h0, h1);
-    lw = pack_h2(__float2half_rn(f0 - __half2float(h0)), __float2half_rn(f1 - __half2float(h1)));
+    if constexpr (K == TC_CONST_FEATURE)
+        lw = pack_h2(__ushort_as_half((unsigned short)0x0400u), __float2half_rn(f1 - __half2float(h1)));   // 2^-14
+    else
+        lw = pack_h2(__float2half_rn(f0 - __half2float(h0)), __float2half_rn(f1 - __half2float(h1)));
 }
 
 // Writes the hi/lo fp16 feature rows of slot r from z (zext[16] == 1), one
@@ -231,8 +285,9 @@ struct TcIssuer {
     long long g = 0, grp = 0, grp_committed = -1, ts = 0;
 };
 
-// Producer (lane 0 of warp 0) for one work item -- the tiles of outputs
-// o_begin .. o_begin + n_out - 1 -- ; false after a timeout.
+// Producer (all of warp 0; one elected lane issues the copies) for one work
+// item -- the tiles of outputs o_begin .. o_begin + n_out - 1 -- ; false
+// after a timeout.
 //
 // The coefficient chunks of a step are one contiguous run of global memory
 // (tiles of consecutive outputs are adjacent), and a bulk copy costs about the
@@ -261,26 +316,37 @@ __device__ bool tc_producer_item(const TcArgs &a, const TcSmem &S, TcProducer &P
         for (; next_tile <= last_tile; ++next_tile) {
             const long long gt = P.g;
             const int c = (int)(gt & 3);
-            if (gt >= 4) ok = mbar_wait_bounded(&const_empty[c], (uint32_t)(((gt >> 2) - 1) & 1), abort_flag);
+            if (gt >= 4)
+                ok = __all_sync(0xffffffffu,
+                                mbar_wait_bounded(&const_empty[c], (uint32_t)(((gt >> 2) - 1) & 1), abort_flag));
             if (!ok) break;
             const long long tile = tile0 + next_tile % G;
-            mbar_arrive_expect_tx(&const_full[c], TC_CONST_BYTES);
-            bulk_g2s(smem + OFF_CONST + c * TC_CONST_BYTES, a.wconst + tile * TC_CONST_BYTES, TC_CONST_BYTES,
-                     &const_full[c]);
+            if (elect_one()) {
+                mbar_arrive_expect_tx(&const_full[c], TC_CONST_BYTES);
+                bulk_g2s(smem + OFF_CONST + c * TC_CONST_BYTES, a.wconst + tile * TC_CONST_BYTES, TC_CONST_BYTES,
+                         &const_full[c]);
+            }
+            __syncwarp();
             P.g = gt + 1;
             P.issued_tiles = P.g;
         }
         if (!ok) break;
         const long long grp = P.grp;
         const int gs = (int)(grp % NGRP);
-        if (grp >= NGRP) ok = mbar_wait_bounded(&empty[gs], (uint32_t)(((grp / NGRP) - 1) & 1), abort_flag);
+        if (grp >= NGRP)
+            ok = __all_sync(0xffffffffu,
+                            mbar_wait_bounded(&empty[gs], (uint32_t)(((grp / NGRP) - 1) & 1), abort_flag));
         if (!ok) break;
         unsigned char *dst = smem + OFF_RING + gs * CPG * TC_CHUNK_BYTES;
         const long long i0 = c0 % step_chunks;
         const int n1 = (int)(step_chunks - i0 < n ? step_chunks - i0 : n);
-        mbar_arrive_expect_tx(&full[gs], (uint32_t)(n * TC_CHUNK_BYTES));
-        bulk_g2s(dst, step_src + i0 * TC_CHUNK_BYTES, (uint32_t)(n1 * TC_CHUNK_BYTES), &full[gs]);
-        if (n1 < n) bulk_g2s(dst + n1 * TC_CHUNK_BYTES, step_src, (uint32_t)((n - n1) * TC_CHUNK_BYTES), &full[gs]);
+        if (elect_one()) {
+            mbar_arrive_expect_tx(&full[gs], (uint32_t)(n * TC_CHUNK_BYTES));
+            bulk_g2s(dst, step_src + i0 * TC_CHUNK_BYTES, (uint32_t)(n1 * TC_CHUNK_BYTES), &full[gs]);
+            if (n1 < n)
+                bulk_g2s(dst + n1 * TC_CHUNK_BYTES, step_src, (uint32_t)((n - n1) * TC_CHUNK_BYTES), &full[gs]);
+        }
+        __syncwarp();
         P.grp = grp + 1;
     }
     return ok;
@@ -437,7 +503,7 @@ __device__ void tc_epilogue_item(const TcArgs &a, const TcSmem &S, uint32_t tbas
     for (int t = 0; t < nsteps; ++t) {
         for (int o = o_begin; o < o_begin + n_out; ++o) {
             const float yref = yrbuf[o * BM + r];
-            Soft st{-INFINITY, 0.f, 0.f, 0.f, 0.f};
+            Soft st{-INFINITY, 0.f, 0.f, 0.f};
             for (int j = 0; j < ntiles; ++j, ++g) {
                 const int buf = (int)(g & 1), c = (int)(g & 3);
                 if (!aborted && !mbar_wait_bounded(&acc_full[buf], (uint32_t)((g >> 1) & 1), abort_flag))
@@ -447,9 +513,8 @@ __device__ void tc_epilogue_item(const TcArgs &a, const TcSmem &S, uint32_t tbas
                 if (!aborted && !mbar_wait_bounded(&const_full[c], (uint32_t)((g >> 2) & 1), abort_flag))
                     aborted = true;
                 aborted = __any_sync(0xffffffffu, aborted);
-                const float *cs = reinterpret_cast<const float *>(smem + OFF_CONST + c * TC_CONST_BYTES) + h * HALF;
-                const float *cy = cs + TNF;
-                const float *cv = cs + 2 * TNF;
+                const float *cy = reinterpret_cast<const float *>(smem + OFF_CONST + c * TC_CONST_BYTES) + h * HALF;
+                const float *cv = cy + TNF;
                 const uint32_t base = tbase + lane_off + buf * 256 + h * HALF;
 #pragma unroll
                 for (int ch = 0; ch < HALF / 16; ++ch) {
@@ -462,58 +527,31 @@ __device__ void tc_epilogue_item(const TcArgs &a, const TcSmem &S, uint32_t tbas
                         if (lane == 0) mbar_arrive(&acc_empty[buf]);
                     }
                     if (!aborted) {
-                        // two fields per packed FP32x2 operation (even / odd columns
-                        // accumulate separately and are added at the end of the chunk)
-                        const float2 *cs2 = reinterpret_cast<const float2 *>(cs + 16 * ch);
                         const float2 *cy2 = reinterpret_cast<const float2 *>(cy + 16 * ch);
                         const float2 *cv2 = reinterpret_cast<const float2 *>(cv + 16 * ch);
-                        float2 sp[8];
-                        float sm = -INFINITY;
-#pragma unroll
-                        for (int i = 0; i < 8; ++i) {
-                            sp[i] = __fadd2_rn(make_float2(sv[2 * i], sv[2 * i + 1]), cs2[i]);
-                            sm = fmaxf(sm, fmaxf(sp[i].x, sp[i].y));
-                        }
-                        const float mn = fmaxf(st.m, sm);
-                        const float mns = mn == -INFINITY ? 0.0f : mn;
-                        const float sc = ex2(st.m - mns);
-                        const float2 nm = make_float2(-mns, -mns), ny = make_float2(-yref, -yref);
-                        float2 s0 = make_float2(st.s0 * sc, 0.0f), s1 = make_float2(st.s1 * sc, 0.0f);
-                        float2 s2 = make_float2(st.s2 * sc, 0.0f), s3 = make_float2(st.s3 * sc, 0.0f);
-#pragma unroll
-                        for (int i = 0; i < 8; ++i) {
-                            const float2 d = __fadd2_rn(sp[i], nm);
-                            const float2 w = make_float2(ex2(d.x), ex2(d.y));
-                            const float2 e = __fadd2_rn(make_float2(yv[2 * i], yv[2 * i + 1]), __fadd2_rn(cy2[i], ny));
-                            const float2 we = __fmul2_rn(w, e);
-                            s0 = __fadd2_rn(s0, w);
-                            s1 = __fadd2_rn(s1, we);
-                            s2 = __ffma2_rn(we, e, s2);
-                            s3 = __ffma2_rn(w, cv2[i], s3);
-                        }
-                        st = Soft{mn, s0.x + s0.y, s1.x + s1.y, s2.x + s2.y, s3.x + s3.y};
+                        soft_chunk(st, sv, yv, cy2, cv2, yref);
                     }
                 }
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&const_empty[c]);
             }
             // merge the two column halves of this output
-            float *pb = part + (o & 1) * 5 * BM;
+            float *pp = part + (o & 1) * NSUM * BM;
             if (!owner) {
-                pb[0 * BM + r] = st.m;
-                pb[1 * BM + r] = st.s0;
-                pb[2 * BM + r] = st.s1;
-                pb[3 * BM + r] = st.s2;
-                pb[4 * BM + r] = st.s3;
+                pp[0 * BM + r] = st.m;
+                pp[1 * BM + r] = st.s0;
+                pp[2 * BM + r] = st.s1;
+                pp[3 * BM + r] = st.s2;
             }
             named_bar_sync(1, NE);
             if (owner) {
-                const Soft other{pb[0 * BM + r], pb[1 * BM + r], pb[2 * BM + r], pb[3 * BM + r], pb[4 * BM + r]};
+                const Soft other{pp[0 * BM + r], pp[1 * BM + r], pp[2 * BM + r], pp[3 * BM + r]};
                 merge_into(st, other);
+                // mean y_ref + E[e]; variance E[e^2 + sigma^2] - E[e]^2
                 const float inv = 1.0f / st.s0;
                 const float me = st.s1 * inv;
                 ybuf[o * BM + r] = yref + me;
-                vbuf[o * BM + r] = fmaxf(fmaf(-me, me, st.s2 * inv), 0.0f) + st.s3 * inv;
+                vbuf[o * BM + r] = fmaxf(fmaf(-me, me, st.s2 * inv), 0.0f);
             }
         }
 
@@ -684,7 +722,8 @@ __device__ __forceinline__ void tc_cta(const TcArgs &a, long long slot_base, uns
     TcIssuer I;
     bool issuer_ok = true;
     if (warp == 0) {
-        if (lane == 0 && !tc_producer_item<PREDICT>(a, S, P, o_begin, n_out)) tc_flag_abort(a, S, DEVERR_TIMEOUT_EMPTY);
+        const bool pok = tc_producer_item<PREDICT>(a, S, P, o_begin, n_out);
+        if (!pok && lane == 0) tc_flag_abort(a, S, DEVERR_TIMEOUT_EMPTY);
         __syncwarp();
     } else if (warp == 1) {
         issuer_ok = tc_issuer_item<PREDICT>(a, S, tbase, I, n_out);
@@ -763,7 +802,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) rollout_tc_batch_kernel(const __g
         for (int i = tid; i < a.cost.n_obs; i += NTHREADS) S.obs_s[i] = a.cost.obs[i];
         __syncthreads();
         if (warp == 0) {
-            if (lane == 0 && !tc_producer_item<false>(a, S, P, 0, NY)) tc_flag_abort(a, S, DEVERR_TIMEOUT_EMPTY);
+            const bool pok = tc_producer_item<false>(a, S, P, 0, NY);
+            if (!pok && lane == 0) tc_flag_abort(a, S, DEVERR_TIMEOUT_EMPTY);
             __syncwarp();
         } else if (warp == 1) {
             if (issuer_ok) {
