@@ -208,27 +208,45 @@ void free_ctx_memory(pi_ctx *c)
 namespace {
 
 // Packs the model for the tensor-core form: per output and tile of 128
-// fields, 11 chunks of [hi | lo] fp16 coefficient blocks in the K-major
-// core-matrix layout the MMAs read (chunk j < 10: the S coefficients of K step
-// j, with cs_j as the weight of the constant feature 152; chunk 10: the Y
-// coefficients), and the fp32 per-field constants cy_j and sigma_j^2 (see
-// rollout_tc.cu for the algebra).  The constant feature is 1 + 2^-14 as
-// hi + lo, so its weight's lo part is cs_lo - 2^-14 cs_hi; a padding field of
-// a ragged last tile has the weight -inf (hi; lo 0) and all other weights 0,
-// so its exponent is exactly -inf and its softmax weight 0.
+// fields, 11 chunks of 8 KB of fp16 coefficient blocks (128 rows x 16 K,
+// K-major core-matrix layout, as the MMAs read them):
+//   chunk 0 = [S hi of K step 0 | Y hi],  chunk 1 = [S lo of K step 0 | Y lo]
+//     (K step 0 and the Y GEMM share the A operand z, so each pair of blocks
+//     is one 256-row B operand of an N=256 MMA);
+//   chunk j + 1 = [S hi | S lo] of K step j, j = 1..9;
+// with cs_j the weight of the constant feature 152 (see rollout_tc.cu for
+// the algebra), and the fp32 per-field constants cy_j and sigma_j^2.  The
+// constant feature is 1 + 2^-14 as hi + lo, so its weight's lo part is
+// cs_lo - 2^-14 cs_hi; a padding field of a ragged last tile has the weight
+// -inf (hi; lo 0) and all other weights 0, so its exponent is exactly -inf and
+// its softmax weight 0.
 void pack_tc(const pi_lwpr_params *lw, int tiles, std::vector<unsigned char> &wt, std::vector<float> &wc)
 {
     const int L = lw->L, TF = TC_TILE_FIELDS;
     const double kap = 0.72134752044448170368;   // log2(e) / 2
     wt.assign((size_t)NY * tiles * TC_TILE_BYTES, 0);
     wc.assign((size_t)NY * tiles * 2 * TF, 0.0f);
-    auto put = [&](unsigned char *tile, int chunk, int row, int kin, double v) {
+    // byte offsets (within a tile) of the hi and lo halves of coefficient
+    // (field row i, feature k) of the S GEMM, and of coefficient k of the Y GEMM
+    auto s_off = [](int i, int k, size_t &hi, size_t &lo) {
+        const uint32_t o = kmajor_offset(i, k % 16, 16);
+        if (k < 16) {
+            hi = o;
+            lo = (size_t)TC_CHUNK_BYTES + o;
+        } else {
+            hi = (size_t)(k / 16 + 1) * TC_CHUNK_BYTES + o;
+            lo = hi + TC_HALF_CHUNK;
+        }
+    };
+    auto y_off = [](int i, int k, size_t &hi, size_t &lo) {
+        hi = (size_t)TC_HALF_CHUNK + kmajor_offset(i, k, 16);
+        lo = (size_t)TC_CHUNK_BYTES + hi;
+    };
+    auto put = [](unsigned char *tile, size_t hi_off, size_t lo_off, double v) {
         const __half hi = __float2half_rn((float)v);
         const __half lo = __float2half_rn((float)(v - (double)__half2float(hi)));
-        unsigned char *base = tile + (size_t)chunk * TC_CHUNK_BYTES;
-        const uint32_t o = kmajor_offset(row, kin, 16);
-        *reinterpret_cast<__half *>(base + o) = hi;
-        *reinterpret_cast<__half *>(base + TC_HALF_CHUNK + o) = lo;
+        *reinterpret_cast<__half *>(tile + hi_off) = hi;
+        *reinterpret_cast<__half *>(tile + lo_off) = lo;
     };
     for (int o = 0; o < NY; ++o)
         for (int tt = 0; tt < tiles; ++tt) {
@@ -236,11 +254,11 @@ void pack_tc(const pi_lwpr_params *lw, int tiles, std::vector<unsigned char> &wt
             float *cst = wc.data() + ((size_t)o * tiles + tt) * 2 * TF;
             for (int i = 0; i < TF; ++i) {
                 const int j = tt * TF + i;
+                size_t ho, lo_o;
                 if (j >= L) {
                     // padding field: exponent -inf, zero weight
-                    unsigned char *base = tile + (size_t)(TC_CONST_FEATURE / 16) * TC_CHUNK_BYTES;
-                    const uint32_t o16 = kmajor_offset(i, TC_CONST_FEATURE % 16, 16);
-                    *reinterpret_cast<__half *>(base + o16) = __ushort_as_half((unsigned short)0xFC00u);
+                    s_off(i, TC_CONST_FEATURE, ho, lo_o);
+                    *reinterpret_cast<__half *>(tile + ho) = __ushort_as_half((unsigned short)0xFC00u);
                     continue;
                 }
                 const size_t f = (size_t)o * L + j;
@@ -257,6 +275,7 @@ void pack_tc(const pi_lwpr_params *lw, int tiles, std::vector<unsigned char> &wt
                     bc += (double)beta[a2] * (double)c[a2];
                 }
                 for (int k = 0; k < TC_KF; ++k) {
+                    s_off(i, k, ho, lo_o);
                     double v = 0.0;
                     if (k < 16) {
                         v = 2.0 * kap * Dsc[k];
@@ -271,15 +290,16 @@ void pack_tc(const pi_lwpr_params *lw, int tiles, std::vector<unsigned char> &wt
                         const __half hi = __float2half_rn((float)cs);
                         const double hd = (double)__half2float(hi);
                         const __half lo = __float2half_rn((float)(cs - hd - 0x1p-14 * hd));
-                        unsigned char *base = tile + (size_t)(k / 16) * TC_CHUNK_BYTES;
-                        const uint32_t o16 = kmajor_offset(i, k % 16, 16);
-                        *reinterpret_cast<__half *>(base + o16) = hi;
-                        *reinterpret_cast<__half *>(base + TC_HALF_CHUNK + o16) = lo;
+                        *reinterpret_cast<__half *>(tile + ho) = hi;
+                        *reinterpret_cast<__half *>(tile + lo_o) = lo;
                         continue;
                     }
-                    put(tile, k / 16, i, k % 16, v);
+                    put(tile, ho, lo_o, v);
                 }
-                for (int k = 0; k < 16; ++k) put(tile, TC_KF / 16, i, k, (double)beta[k]);
+                for (int k = 0; k < 16; ++k) {
+                    y_off(i, k, ho, lo_o);
+                    put(tile, ho, lo_o, (double)beta[k]);
+                }
                 cst[i] = (float)((double)lw->b[f] - bc);
                 const double sg = (double)lw->sigma[f];
                 cst[TF + i] = (float)(sg * sg);

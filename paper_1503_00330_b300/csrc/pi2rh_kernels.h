@@ -72,7 +72,9 @@ cudaError_t launch_predict_fp32(const RolloutArgs &a, cudaStream_t s);
 // Tensor-core form.  Coefficient tiles of 128 fields are pre-packed at context
 // creation as 11 chunks of 8 KB in the exact shared-memory image the MMAs
 // read (fp16, K-major core-matrix layout, 128 rows x 16 K per half-chunk):
-// chunk j < 10 = [S hi | S lo] of K step j, chunk 10 = [Y hi | Y lo]; the
+// chunk 0 = [S hi of K step 0 | Y hi], chunk 1 = [S lo of K step 0 | Y lo]
+// (one N = 256 MMA serves K step 0 of S and the whole Y GEMM, which share
+// the A operand z), chunk j + 1 = [S hi | S lo] of K step j = 1..9; the
 // per-field constants (cy, sigma^2; 2 x 128 floats) are packed separately.
 // ---------------------------------------------------------------------------
 constexpr int TC_SLOTS = 128;           // rollout slots per CTA (MMA M)

@@ -22,17 +22,17 @@
 //
 // Roles (one CTA per SM, 128 slots, 320 threads):
 //   warp 0:        producer (one elected lane issues) -- 1-D bulk copies
-//                  (TMA) of the pre-packed coefficient chunks (8 KB: the hi
-//                  and lo coefficient blocks of one K step for 128 fields)
-//                  in groups of CPG chunks (one
-//                  copy per contiguous run, one barrier pair per group) into a
-//                  ring of NSLOT chunk slots, and of the per-field constants
-//                  (cy, sigma^2) into a 4-deep constant ring;
+//                  (TMA) of the pre-packed coefficient chunks (8 KB each,
+//                  11 per tile of 128 fields) in groups of CPG chunks (one
+//                  copy per contiguous run, one barrier pair per group) into
+//                  a ring of NSLOT chunk slots, and of the per-field
+//                  constants (cy, sigma^2) into a 4-deep constant ring;
 //   warp 1:        MMA issuer (the whole warp runs the loop, one elected
-//                  lane issues) -- per tile of 128 fields, 33 MMAs (M=128,
-//                  N=128, K=16; S: 10 K steps x 3 split products, Y: 1 x 3)
-//                  into one of two TMEM accumulator buffers, releasing each
-//                  chunk group as soon as its MMAs complete;
+//                  lane issues) -- per tile of 128 fields, 30 MMAs (M=128,
+//                  K=16, 3 split products per K step: K step 0 of S and the
+//                  Y GEMM as one N=256 MMA, K steps 1-9 with N=128) into one
+//                  of two TMEM accumulator buffers, releasing each chunk
+//                  group as soon as its MMAs complete;
 //   warps 2-9:     epilogue -- tcgen05.ld of S and Y, online base-2 softmax
 //                  per output on packed FP32x2 operations (chunks of 16
 //                  fields, one rescale per chunk; running sums of w, w e and
@@ -356,9 +356,13 @@ __device__ bool tc_producer_item(const TcArgs &a, const TcSmem &S, TcProducer &P
 // The whole warp runs the loop, so every counter and descriptor is
 // warp-uniform, and the lane elect.sync picks issues the MMAs and commits.  (A
 // lone lane of a diverged warp issued them about 1.4x slower whenever the
-// epilogue warps sharing its sub-partition were busy.)  Waits once per chunk
-// group and releases the group's slots with one commit after its last MMA;
-// the group's chunk c sits in ring slot group * CPG + c.
+// epilogue warps sharing its sub-partition were busy.)  Per tile: chunks 0
+// and 1 feed one N = 256 MMA triple (K step 0 of S into accumulator columns
+// 0-127 and the Y GEMM into 128-255), chunks 2..10 one N = 128 triple each
+// (K steps 1..9 of S) -- 30 MMAs.  Waits once per chunk group and releases
+// the group's slots with one commit after the MMAs that read it (a group
+// ending at chunk 0 is released after the triple issued at chunk 1); the
+// group's chunk c sits in ring slot group * CPG + c.
 template <bool PREDICT>
 __device__ bool tc_issuer_item(const TcArgs &a, const TcSmem &S, uint32_t tbase, TcIssuer &I, int n_out)
 {
@@ -370,11 +374,11 @@ __device__ bool tc_issuer_item(const TcArgs &a, const TcSmem &S, uint32_t tbase,
     const int nsteps = PREDICT ? 2 : a.T;
     const long long nchunk = (long long)G * nsteps * NCH;
     long long &g = I.g, &ts = I.ts;
-    const uint32_t idesc = idesc_f16_f32(BM, TNF);
+    const uint32_t idesc = idesc_f16_f32(BM, TNF), idesc_wide = idesc_f16_f32(BM, 2 * TNF);
     // descriptors: A = feature tile K step j (rows 2560 B apart; step j at
-    // +256 B), B = a chunk half (128 rows x 16 K, rows 256 B apart); step,
-    // slot and half offsets are added to the 14-bit start field (>> 4; the
-    // addresses stay < 256 KB).
+    // +256 B), B = a chunk half (128 rows x 16 K, rows 256 B apart; 256 rows
+    // for the whole first two chunks); step, slot and half offsets are added
+    // to the 14-bit start field (>> 4; the addresses stay < 256 KB).
     const uint64_t a_hi = smem_desc_kmajor(smem_u32(smem + OFF_PHI_HI), 128, 16 * KF);
     const uint64_t a_lo = smem_desc_kmajor(smem_u32(smem + OFF_PHI_LO), 128, 16 * KF);
     const uint64_t b0 = smem_desc_kmajor(smem_u32(smem + OFF_RING), 128, 256);
@@ -394,24 +398,38 @@ __device__ bool tc_issuer_item(const TcArgs &a, const TcSmem &S, uint32_t tbase,
                                 mbar_wait_bounded(&acc_empty[buf], (uint32_t)(((g >> 1) - 1) & 1), abort_flag));
             if (!ok) break;
             tc_fence_after();
-            const uint32_t dS = tbase + buf * 256, dY = dS + 128;
+            const uint32_t dS = tbase + buf * 256;   // S: columns 0-127, Y: 128-255
 #pragma unroll
             for (int j = 0; j < NCH; ++j) {
                 if (cg == 0 && ok) {
                     ok = __all_sync(0xffffffffu, mbar_wait_bounded(&full[gs], gph, abort_flag));
                     tc_fence_after();
                 }
-                if (ok) {
-                    const uint64_t bh = b0 + (uint64_t)((gs * CPG + cg) * (TC_CHUNK_BYTES >> 4));
-                    const uint64_t bl = bh + (uint64_t)(TC_HALF_CHUNK >> 4);
-                    if (j < NCH - 1)
-                        mma3_elect(dS, a_hi + (uint64_t)(j * 16), a_lo + (uint64_t)(j * 16), bh, bl, idesc, j > 0);
-                    else
-                        mma3_elect(dY, a_hi, a_lo, bh, bl, idesc, 0u);
+                if (ok && j > 0) {
+                    const uint32_t slot = gs * CPG + cg;
+                    const uint64_t bc = b0 + (uint64_t)(slot * (TC_CHUNK_BYTES >> 4));
+                    if (j == 1) {
+                        // chunk 0 sits in the ring slot before this one (the last
+                        // slot of the previous group when this chunk opens a group)
+                        const uint32_t pslot = cg > 0 ? slot - 1 : (gs == 0 ? NGRP : gs) * CPG - 1;
+                        const uint64_t bp = b0 + (uint64_t)(pslot * (TC_CHUNK_BYTES >> 4));
+                        mma3_elect(dS, a_hi, a_lo, bp, bc, idesc_wide, 0u);
+                        if (cg == 0) {
+                            // chunk 0 closed the previous group: release it now
+                            const uint32_t pg = gs == 0 ? NGRP - 1 : gs - 1;
+                            commit_elect(&empty[pg]);
+                            I.grp_committed = grp - 1;
+                        }
+                    } else {
+                        mma3_elect(dS, a_hi + (uint64_t)((j - 1) * 16), a_lo + (uint64_t)((j - 1) * 16), bc,
+                                   bc + (uint64_t)(TC_HALF_CHUNK >> 4), idesc, 1u);
+                    }
                 }
                 ++ci;
                 if (++cg == CPG || ci == nchunk) {
-                    if (ok) {
+                    // chunk 0 is read by the MMAs issued at chunk 1: a group it
+                    // closes is released there
+                    if (ok && j > 0) {
                         commit_elect(&empty[gs]);
                         I.grp_committed = grp;
                     }
@@ -425,6 +443,13 @@ __device__ bool tc_issuer_item(const TcArgs &a, const TcSmem &S, uint32_t tbase,
             }
             if (ok) commit_elect(&acc_full[buf]);
         }
+    }
+    // after a timeout, one more commit (on the current group's barrier, whose
+    // phase nothing else completes) covers every MMA issued; the drain waits
+    // for it
+    if (!ok) {
+        commit_elect(&empty[gs]);
+        I.grp_committed = grp;
     }
     I.grp = grp;
     return ok;
@@ -681,12 +706,14 @@ __device__ __forceinline__ void tc_drain(const TcArgs &a, const TcSmem &S, const
             if (!mbar_wait_drain(&S.const_full[g & 3], (uint32_t)((g >> 2) & 1))) atomicOr(a.err, DEVERR_TIMEOUT_DRAIN);
     }
     if (warp == 1 && lane == 0) {
-        // every MMA issued must complete before the tensor memory is freed
+        // every MMA issued must complete before the tensor memory is freed:
+        // normally the last tile's accumulator commit covers them all, after a
+        // timeout the issuer's final group commit does
         if (issuer_ok && I.g > 0 &&
             !mbar_wait_drain(&S.acc_full[(I.g - 1) & 1], (uint32_t)(((I.g - 1) >> 1) & 1)))
             atomicOr(a.err, DEVERR_TIMEOUT_DRAIN);
         if (!issuer_ok && I.grp_committed >= 0) {
-            const long long r = I.grp_committed;   // the last group commit tracks every MMA before it
+            const long long r = I.grp_committed;
             if (!mbar_wait_drain(&S.empty[r % NGRP], (uint32_t)((r / NGRP) & 1))) atomicOr(a.err, DEVERR_TIMEOUT_DRAIN);
         }
     }
