@@ -273,6 +273,13 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
         : "memory");
 }
 
+// Arrival (without waiting) at named barrier `id`, whose instance counts
+// `count` threads in all (those that arrive and those that sync).
+__device__ __forceinline__ void named_bar_arrive(int id, int count)
+{
+    asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
 // Named barrier over `count` threads (multiple of 32), id 1..15.
 __device__ __forceinline__ void named_bar_sync(int id, int count)
 {

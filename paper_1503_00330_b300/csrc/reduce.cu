@@ -1,16 +1,24 @@
 // reduce.cu -- cost-to-go scan and the per-timestep weighted average (Eq. 2).
 //
 // scan_lse_kernel: one CTA per RS_KC = 64 rollouts.  The timesteps are walked
-// from T-1 down to 0 in chunks of TC: one thread per rollout loads the chunk's
-// costs (all loads in flight at once), extends its suffix sum
-// S_{k,i} = phi_k + dt sum_{j>=i} q_{k,j} in FP64 (Sec. 3.1) and parks the
-// chunk in shared memory; then each warp takes whole timesteps of the chunk
-// (their eps loaded up front) and forms, over the CTA's 64 rollouts, the log-sum-exp partial
+// from T-1 down to 0 in chunks of TC, through a two-deep shared-memory buffer:
+// - producer warps 0-1, one thread per rollout, prefetch the next chunk's
+//   costs and extend the suffix sum S_{k,i} = phi_k + dt sum_{j>=i} q_{k,j}
+//   in FP64 (Sec. 3.1), serially from T-1 down;
+// - consumer warps 2-7 take whole timesteps of the previous chunk (their eps
+//   loaded before they wait) and form, over the CTA's 64 rollouts, the
+//   log-sum-exp partial
 //     m_c = min_k S,  Z_c = sum_k 2^((m_c - S) log2(e)/lambda),
 //     V_c = sum_k 2^(...) eps_k
 // (exponent in FP64; exponential, the 2-term lane sums and the pairwise warp
-// sums in FP32; partials stored in FP64).  cost and eps are read once, coalesced and vectorised ([T][K]
-// layout, eps as float4).  costs_out[k] = S_{k,0}.
+// sums in FP32; partials stored in FP64).  The halves hand chunks over through
+// named barriers (full / empty per buffer).  cost and eps are read once,
+// coalesced and vectorised ([T][K] layout, eps as float4).  costs_out[k] = S_{k,0}.
+// B300 runs FP64 at about 2 lanes per clock per SM, 1/64 of FP32, so the
+// kernel keeps FP64 to the suffix sum (convert + FMA) and the exponent
+// (subtract, multiply, convert) -- five FP64-pipe instructions per
+// rollout-step: the exact minimum over the rollouts is taken on integer keys
+// of the doubles (warp redux), and only lane 0 converts the sums it stores.
 //
 // lse_merge_kernel: one warp per timestep merges the per-CTA partials in a
 // fixed order (deterministic) in FP64 and writes u_out = u_nom + V / Z.
@@ -31,6 +39,30 @@ __device__ __forceinline__ double warp_min_d(double v)
     return v;
 }
 
+// Order-preserving unsigned key of a double (not NaN): the smaller key is the
+// smaller value, so a minimum over keys is the exact minimum of the values.
+__device__ __forceinline__ unsigned long long dkey(double d)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+
+__device__ __forceinline__ double dkey_value(unsigned long long k)
+{
+    const unsigned long long b = (k >> 63) ? (k & 0x7FFFFFFFFFFFFFFFull) : ~k;
+    return __longlong_as_double((long long)b);
+}
+
+// Exact minimum over a warp of one key per lane: the minimum high word, then
+// the minimum low word among the lanes holding it (integer warp reductions).
+__device__ __forceinline__ double warp_min_key(unsigned long long k)
+{
+    const unsigned hi = (unsigned)(k >> 32), lo = (unsigned)k;
+    const unsigned mhi = __reduce_min_sync(0xffffffffu, hi);
+    const unsigned mlo = __reduce_min_sync(0xffffffffu, hi == mhi ? lo : 0xffffffffu);
+    return dkey_value(((unsigned long long)mhi << 32) | mlo);
+}
+
 __device__ __forceinline__ double warp_sum_d(double v)
 {
 #pragma unroll
@@ -46,86 +78,128 @@ __device__ __forceinline__ float warp_sum_f(float v)
     return v;
 }
 
+// Named barriers of the scan's two-deep buffer (compile-time ids): full[b]
+// (producers arrive, consumers wait) and empty[b] (the other way round).
+__device__ __forceinline__ void scan_full_arrive(int b)
+{
+    if (b) named_bar_arrive(2, NT);
+    else named_bar_arrive(1, NT);
+}
+__device__ __forceinline__ void scan_full_wait(int b)
+{
+    if (b) named_bar_sync(2, NT);
+    else named_bar_sync(1, NT);
+}
+__device__ __forceinline__ void scan_empty_arrive(int b)
+{
+    if (b) named_bar_arrive(4, NT);
+    else named_bar_arrive(3, NT);
+}
+__device__ __forceinline__ void scan_empty_wait(int b)
+{
+    if (b) named_bar_sync(4, NT);
+    else named_bar_sync(3, NT);
+}
+
 __device__ __forceinline__ void scan_lse_block(const float *__restrict__ cost_tk, const float *__restrict__ phi,
                                                const float4 *__restrict__ eps_tk, int K, int T, double dt,
                                                double inv_lam_log2e, float *__restrict__ costs_out,
                                                double *__restrict__ part, int blk)
 {
-    __shared__ double S_s[TC][KC];
+    constexpr int NPROD = KC;                 // producer threads (warps 0-1)
+    constexpr int NCW = (NT - NPROD) / 32;    // consumer warps
+    __shared__ double S_s[2][TC][KC];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int k0 = blk * KC;
-    const int k = k0 + tid;
-    double acc = 0.0;
-    if (tid < KC && k < K) acc = (double)phi[k];
-
-    for (int hi = T; hi > 0; hi -= TC) {
-        const int lo = hi > TC ? hi - TC : 0;
-        if (tid < KC) {
-            // the chunk's costs are loaded first (independent loads in flight),
-            // then summed backwards in FP64 in the same order as ever
-            float cb[TC];
+    const int nchunk = (T + TC - 1) / TC;     // chunk c covers [max(T - (c+1) TC, 0), T - c TC)
+    if (tid < NPROD) {
+        const int k = k0 + tid;
+        double acc = k < K ? (double)phi[k] : 0.0;
+        float cb[TC];
+        auto load_chunk = [&](int c) {
+            const int hi = T - c * TC, lo = hi > TC ? hi - TC : 0;
 #pragma unroll
             for (int r = 0; r < TC; ++r) {
                 const int i = hi - 1 - r;
                 cb[r] = (k < K && i >= lo) ? cost_tk[(size_t)i * K + k] : 0.0f;
             }
+        };
+        load_chunk(0);
+        for (int c = 0; c < nchunk; ++c) {
+            const int b = c & 1;
+            const int hi = T - c * TC, lo = hi > TC ? hi - TC : 0;
+            float cur[TC];
+#pragma unroll
+            for (int r = 0; r < TC; ++r) cur[r] = cb[r];
+            if (c + 1 < nchunk) load_chunk(c + 1);   // in flight while this chunk is summed
+            if (c >= 2) scan_empty_wait(b);   // the consumers are done with buffer b
+            // the chunk's costs, summed backwards in FP64 in the same order as ever
 #pragma unroll
             for (int r = 0; r < TC; ++r) {
                 const int i = hi - 1 - r;
                 if (i >= lo) {
                     double s = INFINITY;
                     if (k < K) {
-                        acc += (double)cb[r] * dt;
+                        acc += (double)cur[r] * dt;
                         s = acc;
                     }
-                    S_s[i - lo][tid] = s;
+                    S_s[b][i - lo][tid] = s;
                 }
             }
             if (lo == 0 && k < K) costs_out[k] = (float)acc;
+            scan_full_arrive(b);
         }
-        __syncthreads();
-        // each warp takes timesteps warp, warp + 8, ... of the chunk; the eps of
-        // all of them are loaded before the reductions
-        constexpr int RPW = TC / (NT / 32);
+        // the last one or two buffers: wait for their consumers before leaving
+        for (int c = nchunk > 2 ? nchunk - 2 : 0; c < nchunk; ++c) scan_empty_wait(c & 1);
+        return;
+    }
+    const int cw = warp - NPROD / 32;          // consumer warp 0..NCW-1
+    constexpr int RPW = (TC + NCW - 1) / NCW;  // rows per consumer warp and chunk
+    const int ka = k0 + lane, kb = k0 + lane + 32;
+    for (int c = 0; c < nchunk; ++c) {
+        const int b = c & 1;
+        const int hi = T - c * TC, lo = hi > TC ? hi - TC : 0;
+        // this warp's timesteps of the chunk: rows cw, cw + NCW, ...; their eps first
         float4 ea[RPW], eb[RPW];
-        const int ka = k0 + lane, kb = k0 + lane + 32;
 #pragma unroll
         for (int u = 0; u < RPW; ++u) {
-            const int r = warp + u * (NT / 32), i = lo + r;
+            const int r = cw + u * NCW, i = lo + r;
             const bool ok = r < hi - lo;
             ea[u] = ok && ka < K ? eps_tk[(size_t)i * K + ka] : make_float4(0.f, 0.f, 0.f, 0.f);
             eb[u] = ok && kb < K ? eps_tk[(size_t)i * K + kb] : make_float4(0.f, 0.f, 0.f, 0.f);
         }
+        scan_full_wait(b);
 #pragma unroll
         for (int u = 0; u < RPW; ++u) {
-            const int r = warp + u * (NT / 32), i = lo + r;
+            const int r = cw + u * NCW, i = lo + r;
             if (r >= hi - lo) break;
-            const double sa = S_s[r][lane], sb = S_s[r][lane + 32];
-            // exact FP64 minimum: a rounded shift can put exponents hundreds of
-            // binary orders off when S is large and lambda small
-            const double mn = warp_min_d(fmin(sa, sb));
+            const double sa = S_s[b][r][lane], sb = S_s[b][r][lane + 32];
+            // exact minimum (a rounded shift can put exponents hundreds of
+            // binary orders off when S is large and lambda small), on keys
+            const unsigned long long ka2 = dkey(sa), kb2 = dkey(sb);
+            const double mn = warp_min_key(ka2 < kb2 ? ka2 : kb2);
             const float wa = exp2f((float)((mn - sa) * inv_lam_log2e));
             const float wb = exp2f((float)((mn - sb) * inv_lam_log2e));
             // the 64 rollouts' FP32 terms are summed by a pairwise warp tree in
             // FP32 (B300 has little FP64 throughput); the partials are stored
             // and merged over K in FP64
             const float4 xa = ea[u], xb = eb[u];
-            const double z = (double)warp_sum_f(wa + wb);
-            const double v0 = (double)warp_sum_f(fmaf(wa, xa.x, wb * xb.x));
-            const double v1 = (double)warp_sum_f(fmaf(wa, xa.y, wb * xb.y));
-            const double v2 = (double)warp_sum_f(fmaf(wa, xa.z, wb * xb.z));
-            const double v3 = (double)warp_sum_f(fmaf(wa, xa.w, wb * xb.w));
+            const float z = warp_sum_f(wa + wb);
+            const float v0 = warp_sum_f(fmaf(wa, xa.x, wb * xb.x));
+            const float v1 = warp_sum_f(fmaf(wa, xa.y, wb * xb.y));
+            const float v2 = warp_sum_f(fmaf(wa, xa.z, wb * xb.z));
+            const float v3 = warp_sum_f(fmaf(wa, xa.w, wb * xb.w));
             if (lane == 0) {
                 double *p = part + ((size_t)blk * T + i) * 6;
                 p[0] = mn;
-                p[1] = z;
-                p[2] = v0;
-                p[3] = v1;
-                p[4] = v2;
-                p[5] = v3;
+                p[1] = (double)z;
+                p[2] = (double)v0;
+                p[3] = (double)v1;
+                p[4] = (double)v2;
+                p[5] = (double)v3;
             }
         }
-        __syncthreads();
+        scan_empty_arrive(b);
     }
 }
 
