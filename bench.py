@@ -273,14 +273,32 @@ def form_roofline(precision, rollout_ms, K, T, M, L, dev, peaks, workload):
             "rollout_ms_per_launch": statistics.mean(rollout_ms)}
 
 
-def reduction_rooflines(scan_ms, merge_ms, K, T, peaks):
-    """Achieved bandwidth of the cost-to-go/LSE scan and of the merge (memory-bound kernels).
+# FP64-pipe instructions per rollout-step in the scan (lane level): convert and
+# FMA for the suffix sum, subtract, multiply and convert for the exponent.
+SCAN_FP64_PER_ROLLOUT_STEP = 5
+_FP64_RATE = {}
 
-    Bytes are algorithmic: the scan reads cost [T][K] f32 and eps [T][K] float4 and phi [K],
-    writes costs_out [K] and the LSE partials [K/64][T][6] f64; the merge reads the partials
-    and u_nom [T][4] and writes u_out [T][4].  Their inputs were written by the rollout kernel
-    just before (about 20 B per rollout-step), so they are mostly L2-resident: the fraction is
-    given against the measured HBM copy peak, and can exceed what DRAM alone would allow."""
+
+def fp64_peak(device: int) -> float:
+    """Measured FP64 FMA lane results/s of the device (probed once per process)."""
+    if device not in _FP64_RATE:
+        from paper_1503_00330_b300.api import fp64_rate
+        _FP64_RATE[device] = fp64_rate(device)
+    return _FP64_RATE[device]
+
+
+def reduction_rooflines(scan_ms, merge_ms, K, T, peaks, device=0):
+    """Rooflines of the cost-to-go/LSE scan and of the merge.
+
+    The scan is bound by B300's FP64 pipe (ncu: FP64 pipe busy ~62 % of active cycles, DRAM
+    ~9 %): its roofline counts SCAN_FP64_PER_ROLLOUT_STEP FP64 instructions per rollout-step
+    against the measured DFMA rate, with its bandwidth beside it.  The merge is a small,
+    latency-bound launch; its bandwidth is given.  Bytes are algorithmic: the scan reads cost
+    [T][K] f32 and eps [T][K] float4 and phi [K], writes costs_out [K] and the LSE partials
+    [K/64][T][6] f64; the merge reads the partials and u_nom [T][4] and writes u_out [T][4].
+    Their inputs were written by the rollout kernel just before (about 20 B per
+    rollout-step), so they are mostly L2-resident: the bandwidth fraction is given against the
+    measured HBM copy peak, and can exceed what DRAM alone would allow."""
     nblk = -(-K // 64)
     scan_b = K * T * 20 + K * 8 + nblk * T * 48
     merge_b = nblk * T * 48 + T * 32
@@ -289,9 +307,21 @@ def reduction_rooflines(scan_ms, merge_ms, K, T, peaks):
     for name, ms, b in (("scan_lse_kernel", scan_ms, scan_b), ("lse_merge_kernel", merge_ms, merge_b)):
         avg = statistics.mean(ms)
         gbs = b / (avg / 1e3) / 1e9
-        out[name] = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
-                     "bytes_per_launch": b, "ms_per_launch": avg,
-                     "data": "inputs written by the rollout kernel just before (L2-resident for this size)"}
+        bw = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+              "bytes_per_launch": b, "ms_per_launch": avg,
+              "data": "inputs written by the rollout kernel just before (L2-resident for this size)"}
+        if name == "scan_lse_kernel":
+            ops = SCAN_FP64_PER_ROLLOUT_STEP * K * T
+            rate = fp64_peak(device)
+            achieved = ops / (avg / 1e3)
+            out[name] = {"bound": "fp64", "achieved": achieved / 1e9, "peak": rate / 1e9,
+                         "unit": "G FP64 instr/s", "frac": achieved / rate, "fp64_instr_per_launch": ops,
+                         "ms_per_launch": avg,
+                         "peak_basis": "measured DFMA lane rate (pi_debug_fp64_rate); "
+                                       f"{SCAN_FP64_PER_ROLLOUT_STEP} FP64 instructions per rollout-step",
+                         "hbm_view": bw}
+        else:
+            out[name] = bw
     return out
 
 
@@ -330,7 +360,7 @@ def time_form(precision, p, args, dev):
     roof = form_roofline(precision, rollout_ms, K, T, M, L, dev, measured_peaks(), args.workload)
     roof["rollout_share_of_step"] = sum(rollout_ms) / sum(step_ms)
     return {"value": K * T * M * args.steps / total_s, "ms_per_update": 1e3 * total_s / args.steps,
-            "roofline": roof, "reduction": reduction_rooflines(scan_ms, merge_ms, K, T, measured_peaks())}
+            "roofline": roof, "reduction": reduction_rooflines(scan_ms, merge_ms, K, T, measured_peaks(), dev.index or 0)}
 
 
 def run_batched(args):
@@ -602,7 +632,7 @@ def run_ours(args):
     from paper_1503_00330_b300.api import pipe_rates
     rates = pipe_rates(local)   # measured pipe rates: context beside the unit-count FP32 peak
     roofline["rollout_share_of_step"] = sum(rollout_ms) / sum(step_ms)
-    reduction = reduction_rooflines(scan_ms, merge_ms, K, T, peaks)
+    reduction = reduction_rooflines(scan_ms, merge_ms, K, T, peaks, local)
     forms = {args.precision: {"value": value, "ms_per_update": 1e3 * total_s / args.steps,
                               "roofline": roofline, "reduction": reduction}}
     if not args.no_compare:
@@ -622,8 +652,9 @@ def run_ours(args):
                     "d2h_bytes_per_step": (T * 4 + K) * 4},
             "roofline": roofline,
             "reduction_kernels": reduction,
-            "measured_pipe_rates": {**rates, "note": "FFMA2 / MUFU ex2 chains on every SM, event-timed; "
-                                                     "the FP32 roofline keeps the unit-count peak"},
+            "measured_pipe_rates": {**rates, "dfma_per_s": fp64_peak(local),
+                                    "note": "FFMA2 / MUFU ex2 / DFMA chains on every SM, event-timed; "
+                                            "the FP32 roofline keeps the unit-count peak"},
             "forms": forms,
             "paper_context": PAPER_CONTEXT,
             "clocks": clocks.summary()}

@@ -426,6 +426,12 @@ void pi_server_destroy(pi_server *s);
  * Context for the roofline (the paper has no counterpart). */
 int pi_debug_pipe_rates(int device, double *ffma_tflops, double *ex2_per_s);
 
+/* Measured FP64 FMA rate of `device` in lane results per second (each is 2
+ * flop): independent DFMA chains on every SM, CUDA-event timed; synchronous.
+ * The denominator of the cost-to-go scan's roofline, which B300's low FP64
+ * throughput bounds. */
+int pi_debug_fp64_rate(int device, double *dfma_per_s);
+
 /* Host-only ABI check (no GPU): writes, for the public structs in this order
  * -- pi_lwpr_params, pi_cost_params, pi_opts, pi_batch_item, pi_server_opts,
  * pi_serve_request, pi_serve_done, pi_serve_arrival, pi_server_stats -- their

@@ -133,6 +133,7 @@ _SIGS = {
                                               ctypes.POINTER(ctypes.c_int)]),
     "pi_debug_pipe_rates": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                            ctypes.POINTER(ctypes.c_double)]),
+    "pi_debug_fp64_rate": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "pi_debug_pool": (ctypes.c_int, [ctypes.c_size_t, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_size_t),
                                      ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int)]),
     "pi_debug_noise": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp]),
@@ -173,4 +174,4 @@ def declared_functions() -> list[str]:
     with open(HEADER) as f:
         src = f.read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(pi_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(pi_[a-z0-9_]+)\s*\(", src)))

@@ -438,6 +438,14 @@ def pipe_rates(device: int = 0) -> dict:
     return {"ffma_tflops": f.value, "ex2_per_s": e.value}
 
 
+def fp64_rate(device: int = 0) -> float:
+    """Measured FP64 FMA lane results per second of the device (see pi_debug_fp64_rate)."""
+    lib = _lib.load()
+    r = ctypes.c_double()
+    check(lib.pi_debug_fp64_rate(int(device), ctypes.byref(r)))
+    return r.value
+
+
 def debug_pool(capacity: int, ops):
     """Runs the serving pool allocator on the host: ops = [("alloc", nbytes) | ("free", op_index)].
 
