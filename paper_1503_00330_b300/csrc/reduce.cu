@@ -20,8 +20,9 @@
 // rollout-step: the exact minimum over the rollouts is taken on integer keys
 // of the doubles (warp redux), and only lane 0 converts the sums it stores.
 //
-// lse_merge_kernel: one warp per timestep merges the per-CTA partials in a
-// fixed order (deterministic) in FP64 and writes u_out = u_nom + V / Z.
+// lse_merge_kernel: one warp per timestep (one warp per CTA, so that the FP64
+// exponentials spread over T SMs) merges the per-CTA partials in a fixed order
+// (deterministic) in FP64 and writes u_out = u_nom + V / Z.
 #include "pi2rh_kernels.h"
 
 namespace pi2rh {
@@ -321,7 +322,8 @@ cudaError_t launch_scan_lse(const float *cost_tk, const float *phi, const float4
 cudaError_t launch_lse_merge(const double *part, int nblk, int T, double inv_lam_log2e,
                              const float *u_nom, float *u_out, cudaStream_t s)
 {
-    lse_merge_kernel<<<(T + 7) / 8, 256, 0, s>>>(part, nblk, T, inv_lam_log2e, u_nom, u_out);
+    // one warp per CTA: the FP64 exponentials of the merge spread over T SMs
+    lse_merge_kernel<<<T, 32, 0, s>>>(part, nblk, T, inv_lam_log2e, u_nom, u_out);
     return cudaGetLastError();
 }
 
