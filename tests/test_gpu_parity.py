@@ -127,6 +127,37 @@ def test_reduce_stage(oracle, K, T, lam):
     assert ec <= 1e-6
 
 
+def test_reduce_stage_negative_costs(oracle):
+    """Costs of either sign (a cost with negative weights): the exact minimum over
+    the rollouts is taken on order-preserving integer keys of the doubles, whose
+    negative branch this exercises (S spans zero)."""
+    K, T, lam = 333, 40, 0.7
+    g = np.random.default_rng(5)
+    cost = g.uniform(-40, 40, (K, T)).astype(np.float32)
+    phi = g.uniform(-10, 10, K).astype(np.float32)
+    eps = g.normal(0, 0.3, (K, T, 4)).astype(np.float32)
+    u_nom = g.normal(0, 0.5, (T, 4)).astype(np.float32)
+    p = W.problem(8, 4, 2, seed=0)
+    ctl = _ctrl(p)
+    u, c = ctl.debug_reduce(cost.T.copy(), phi, np.transpose(eps, (1, 0, 2)).copy(), u_nom, lam)
+    ctl.sync()
+    S = oracle.cost_to_go(cost, phi, float(p.model.dt))
+    assert S.min() < 0 < S.max()
+    uref = oracle.weighted_update(S, eps, u_nom, lam)
+    assert np.all(_u_err(u.cpu().numpy(), uref) <= U_TOL)
+    assert np.max(np.abs(c.cpu().numpy() - S[:, 0]) / (np.abs(S[:, 0]) + 1.0)) <= 1e-6
+
+
+def test_pipe_rate_probes():
+    """The measured pipe rates behind the rooflines are positive and of the size a
+    B300 can have (FFMA2 10-200 TFLOP/s, MUFU ex2 1e11-1e14/s, DFMA 1e10-1e13/s)."""
+    from paper_1503_00330_b300.api import fp64_rate, pipe_rates
+    r = pipe_rates(0)
+    assert 10.0 < r["ffma_tflops"] < 200.0
+    assert 1e11 < r["ex2_per_s"] < 1e14
+    assert 1e10 < fp64_rate(0) < 1e13
+
+
 def test_reduce_stage_large_costs_small_lambda(oracle):
     """Costs near 1e8 (cost-to-go near 1e8 too) with lambda = 0.01: the shift of the
     exponents must be the exact minimum, else exp2 over- or underflows; u_out is
