@@ -360,6 +360,7 @@ def time_form(precision, p, args, dev):
     roof = form_roofline(precision, rollout_ms, K, T, M, L, dev, measured_peaks(), args.workload)
     roof["rollout_share_of_step"] = sum(rollout_ms) / sum(step_ms)
     return {"value": K * T * M * args.steps / total_s, "ms_per_update": 1e3 * total_s / args.steps,
+            "ms_per_update_stats": {"best": min(step_ms), "median": statistics.median(step_ms), "n": len(step_ms)},
             "roofline": roof, "reduction": reduction_rooflines(scan_ms, merge_ms, K, T, measured_peaks(), dev.index or 0)}
 
 
@@ -647,6 +648,8 @@ def run_ours(args):
                        "l2": "flushed between timed steps (256 MiB write outside the event window); "
                              "per-update working set ~21 MB"},
             "ms_per_update": 1e3 * total_s / args.steps,
+            "ms_per_update_stats": {"best": min(step_ms), "median": statistics.median(step_ms),
+                                    "n": len(step_ms), "note": "this rank's timed updates (CUDA events)"},
             "gpu_launches": launches,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": (12 + T * 4) * 4,
                     "d2h_bytes_per_step": (T * 4 + K) * 4},
