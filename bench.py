@@ -273,6 +273,35 @@ def form_roofline(precision, rollout_ms, K, T, M, L, dev, peaks, workload):
             "rollout_ms_per_launch": statistics.mean(rollout_ms)}
 
 
+_PIPE_RATES = {}
+
+
+def pipe_peaks(device: int) -> dict:
+    """Measured FFMA2 and MUFU ex2 rates of the device (probed once per process)."""
+    if device not in _PIPE_RATES:
+        from paper_1503_00330_b300.api import pipe_rates
+        _PIPE_RATES[device] = pipe_rates(device)
+    return _PIPE_RATES[device]
+
+
+def mufu_check(precision, rollout_ms, K, T, M, L, device):
+    """The rollout kernel's secondary pipe: MUFU ex2 results per launch against the measured
+    ex2 rate.  FP32 form: 3 per field pair and slot (the rescale and the two weights); tensor-core
+    form: 1 per field evaluation (padded to 128-field tiles) and 1 per 16-field chunk (rescale)."""
+    avg_s = statistics.mean(rollout_ms) / 1e3
+    if precision == "fp32":
+        per_slot_step = 12 * (-(-L // 2)) * 3
+        binding = "FP32 FMA pipe"
+    else:
+        L_pad = -(-L // TC_FIELDS_PER_TILE) * TC_FIELDS_PER_TILE
+        per_slot_step = 12 * L_pad * 17 / 16
+        binding = "tensor pipe (MMA issue)"
+    n = float(K) * T * M * per_slot_step
+    rate = float(pipe_peaks(device)["ex2_per_s"])
+    return {"pipe": "MUFU ex2", "achieved": n / avg_s, "peak": rate, "unit": "ex2/s", "frac": n / avg_s / rate,
+            "ex2_per_launch": n, "binding_pipe": binding}
+
+
 # FP64-pipe instructions per rollout-step in the scan (lane level): convert and
 # FMA for the suffix sum, subtract, multiply and convert for the exponent.
 SCAN_FP64_PER_ROLLOUT_STEP = 5
@@ -359,6 +388,7 @@ def time_form(precision, p, args, dev):
     total_s = sum(step_ms) / 1e3
     roof = form_roofline(precision, rollout_ms, K, T, M, L, dev, measured_peaks(), args.workload)
     roof["rollout_share_of_step"] = sum(rollout_ms) / sum(step_ms)
+    roof["secondary"] = mufu_check(precision, rollout_ms, K, T, M, L, dev.index or 0)
     return {"value": K * T * M * args.steps / total_s, "ms_per_update": 1e3 * total_s / args.steps,
             "ms_per_update_stats": {"best": min(step_ms), "median": statistics.median(step_ms), "n": len(step_ms)},
             "roofline": roof, "reduction": reduction_rooflines(scan_ms, merge_ms, K, T, measured_peaks(), dev.index or 0)}
@@ -630,9 +660,9 @@ def run_ours(args):
 
     peaks = measured_peaks()
     roofline = form_roofline(args.precision, rollout_ms, K, T, M, L, dev, peaks, args.workload)
-    from paper_1503_00330_b300.api import pipe_rates
-    rates = pipe_rates(local)   # measured pipe rates: context beside the unit-count FP32 peak
+    rates = pipe_peaks(local)   # measured pipe rates: context beside the unit-count FP32 peak
     roofline["rollout_share_of_step"] = sum(rollout_ms) / sum(step_ms)
+    roofline["secondary"] = mufu_check(args.precision, rollout_ms, K, T, M, L, local)
     reduction = reduction_rooflines(scan_ms, merge_ms, K, T, peaks, local)
     forms = {args.precision: {"value": value, "ms_per_update": 1e3 * total_s / args.steps,
                               "roofline": roofline, "reduction": reduction}}
