@@ -177,16 +177,21 @@ __device__ __forceinline__ float feature(const float (&zext)[17])
     }
 }
 
+// Features K and K+1 as fp16 hi and lo pairs (hi = f rounded to fp16, lo = the
+// exact FP32 remainder f - hi rounded to fp16), two at a time on packed
+// conversions.  The constant feature's lo part is 2^-14 (see the header).
 template <int K>
 __device__ __forceinline__ void split_pair(const float (&zext)[17], uint32_t &hw, uint32_t &lw)
 {
-    const float f0 = feature<K>(zext), f1 = feature<K + 1>(zext);
-    const __half h0 = __float2half_rn(f0), h1 = __float2half_rn(f1);
-    hw = pack_h2(h0, h1);
+    const float2 f = make_float2(feature<K>(zext), feature<K + 1>(zext));
+    const __half2 h = __floats2half2_rn(f.x, f.y);
+    const float2 hf = __half22float2(h);
+    const __half2 l = __floats2half2_rn(f.x - hf.x, f.y - hf.y);
+    hw = *reinterpret_cast<const uint32_t *>(&h);
     if constexpr (K == TC_CONST_FEATURE)
-        lw = pack_h2(__ushort_as_half((unsigned short)0x0400u), __float2half_rn(f1 - __half2float(h1)));   // 2^-14
+        lw = pack_h2(__ushort_as_half((unsigned short)0x0400u), __high2half(l));   // 2^-14
     else
-        lw = pack_h2(__float2half_rn(f0 - __half2float(h0)), __float2half_rn(f1 - __half2float(h1)));
+        lw = *reinterpret_cast<const uint32_t *>(&l);
 }
 
 // Writes the hi/lo fp16 feature rows of slot r from z (zext[16] == 1), one
