@@ -463,8 +463,9 @@ __device__ bool tc_issuer_item(const TcArgs &a, const TcSmem &S, uint32_t tbase,
 // Epilogue warps (2-9) for one work item: the 128 slots starting at
 // slot_base, outputs o_begin .. o_begin + n_out - 1.  With ncl > 1 CTAs in
 // the cluster (split form, rollouts only), every CTA evaluates its own share
-// of the outputs, sends their means and variances to the other CTAs'
-// y / var buffers (distributed shared memory) and then steps the dynamics of
+// of the outputs, sends each one's means and variances to the other CTAs'
+// y / var buffers (distributed shared memory) right after its merge, behind
+// the next output's tiles, and at the end of the step steps the dynamics of
 // all 128 slots itself -- the same arithmetic on the same values in every
 // CTA; only rank 0 writes the outputs.  Per step, xfull completes when the
 // other CTAs' values have landed and xfree when they have read this CTA's
@@ -531,6 +532,11 @@ __device__ void tc_epilogue_item(const TcArgs &a, const TcSmem &S, uint32_t tbas
     named_bar_sync(1, NE);
 
     for (int t = 0; t < nsteps; ++t) {
+        // split form: the other CTAs have read this CTA's values of the last
+        // step before any of this step's are sent (after each merge below)
+        if (!PREDICT && ncl > 1 && owner && t > 0 && !aborted &&
+            !mbar_wait_cluster_bounded(S.xfree, (uint32_t)((t - 1) & 1), abort_flag))
+            aborted = true;
         for (int o = o_begin; o < o_begin + n_out; ++o) {
             const float yref = yrbuf[o * BM + r];
             Soft st{-INFINITY, 0.f, 0.f, 0.f};
@@ -580,29 +586,25 @@ __device__ void tc_epilogue_item(const TcArgs &a, const TcSmem &S, uint32_t tbas
                 // mean y_ref + E[e]; variance E[e^2 + sigma^2] - E[e]^2
                 const float inv = 1.0f / st.s0;
                 const float me = st.s1 * inv;
-                ybuf[o * BM + r] = yref + me;
-                vbuf[o * BM + r] = fmaxf(fmaf(-me, me, st.s2 * inv), 0.0f);
+                const float yo = yref + me, vo = fmaxf(fmaf(-me, me, st.s2 * inv), 0.0f);
+                ybuf[o * BM + r] = yo;
+                vbuf[o * BM + r] = vo;
+                if (!PREDICT && ncl > 1 && !aborted)   // send now, behind the next output's tiles
+                    for (uint32_t pr = 0; pr < ncl; ++pr) {
+                        if (pr == rank) continue;
+                        st_cluster_f32(mapa_shared(ybuf, pr) + (uint32_t)((o * BM + r) * 4), yo);
+                        st_cluster_f32(mapa_shared(vbuf, pr) + (uint32_t)((o * BM + r) * 4), vo);
+                    }
             }
         }
 
         // ------------------------------------------ exchange (split form only)
         if (!PREDICT && ncl > 1 && owner) {
-            if (t > 0 && !aborted && !mbar_wait_cluster_bounded(S.xfree, (uint32_t)((t - 1) & 1), abort_flag))
-                aborted = true;
-            if (!aborted) {
-                for (uint32_t pr = 0; pr < ncl; ++pr) {
-                    if (pr == rank) continue;
-                    // the peer's y / var rows of this CTA's outputs (same offsets as here)
-                    const uint32_t ry = mapa_shared(ybuf, pr) + (uint32_t)((o_begin * BM + r) * 4);
-                    const uint32_t rv = mapa_shared(vbuf, pr) + (uint32_t)((o_begin * BM + r) * 4);
-#pragma unroll
-                    for (int i = 0; i < n_out; ++i) {
-                        st_cluster_f32(ry + i * BM * 4, ybuf[(o_begin + i) * BM + r]);
-                        st_cluster_f32(rv + i * BM * 4, vbuf[(o_begin + i) * BM + r]);
-                    }
-                    mbar_arrive_remote(mapa_shared(S.xfull, pr));
-                }
-            }
+            // every output's values were sent after its merge; the arrivals
+            // (release) publish them, then this CTA waits for the others'
+            if (!aborted)
+                for (uint32_t pr = 0; pr < ncl; ++pr)
+                    if (pr != rank) mbar_arrive_remote(mapa_shared(S.xfull, pr));
             if (!aborted && !mbar_wait_cluster_bounded(S.xfull, (uint32_t)(t & 1), abort_flag)) aborted = true;
         }
 
