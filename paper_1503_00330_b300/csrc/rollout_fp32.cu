@@ -521,6 +521,79 @@ __global__ void __launch_bounds__(NTHREADS, 1) rollout_fp32_group_kernel(const _
 
 std::atomic<uint64_t> g_attr_set[2];
 
+// Prediction of a few rows (the receding-horizon plant step, one row, and a
+// serving group's plant steps, one row per agent): one CTA per (row, output).
+// Its threads take the output's field pairs p = tid, tid + PR_THREADS, ... for
+// that one row, straight from the packed records in global memory (they stay
+// L2-resident), and the per-thread softmax states are merged over the CTA in a
+// fixed order, so every row's result is deterministic and independent of the
+// other rows.  Two passes, as in the rollout kernel's prediction mode: the
+// second centres the local predictions on the first pass's mean.
+constexpr int PR_THREADS = 256;
+
+__device__ __forceinline__ void soft_merge(Soft &a, const Soft &b)
+{
+    const float M = fmaxf(a.m, b.m);
+    if (M == -INFINITY) return;   // neither holds a field yet
+    const float ca = ex2(a.m - M), cb = ex2(b.m - M);
+    a.s0 = fmaf(a.s0, ca, b.s0 * cb);
+    a.s1 = fmaf(a.s1, ca, b.s1 * cb);
+    a.s2 = fmaf(a.s2, ca, b.s2 * cb);
+    a.s3 = fmaf(a.s3, ca, b.s3 * cb);
+    a.m = M;
+}
+
+__global__ void __launch_bounds__(PR_THREADS) predict_rows_kernel(const __grid_constant__ RolloutArgs a)
+{
+    __shared__ float zs[NZ];
+    __shared__ Soft wpart[PR_THREADS / 32];
+    __shared__ float yvar[2];
+    const int row = blockIdx.x, o = blockIdx.y, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid < NZ) zs[tid] = a.z_in[(size_t)row * NZ + tid];
+    __syncthreads();
+    float2 z2[NZ];
+#pragma unroll
+    for (int c = 0; c < NZ; ++c) z2[c] = make_float2(zs[c], zs[c]);
+    float yref = 0.0f, y = 0.0f, var = 0.0f;
+    for (int pass = 0; pass < 2; ++pass) {
+        const float2 yr = make_float2(-yref, -yref);
+        Soft st, unused;
+        soft_init(st);
+        soft_init(unused);
+        for (int p = tid; p < a.P; p += PR_THREADS) {
+            const float4 *r4 = reinterpret_cast<const float4 *>(a.rec + ((size_t)o * a.P + p) * REC_LEN);
+            process_pair(r4, z2, z2, yr, yr, st, unused);   // the second slot is not needed
+        }
+        // lane 0 of each warp merges its lanes in a fixed tree order, thread 0 the warps in order
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            const Soft other{__shfl_down_sync(0xffffffffu, st.m, off), __shfl_down_sync(0xffffffffu, st.s0, off),
+                             __shfl_down_sync(0xffffffffu, st.s1, off), __shfl_down_sync(0xffffffffu, st.s2, off),
+                             __shfl_down_sync(0xffffffffu, st.s3, off)};
+            soft_merge(st, other);
+        }
+        if (lane == 0) wpart[warp] = st;
+        __syncthreads();
+        if (tid == 0) {
+            Soft all = wpart[0];
+            for (int w = 1; w < PR_THREADS / 32; ++w) soft_merge(all, wpart[w]);
+            const float inv = 1.0f / all.s0;
+            const float mean_e = all.s1 * inv;
+            yvar[0] = yref + mean_e;
+            yvar[1] = fmaxf(fmaf(-mean_e, mean_e, all.s2 * inv), 0.0f) + all.s3 * inv;
+        }
+        __syncthreads();
+        y = yvar[0];
+        var = yvar[1];
+        yref = y;
+        __syncthreads();   // yvar is rewritten by the next pass
+    }
+    if (tid == 0) {
+        a.y_out[(size_t)row * NY + o] = y;
+        a.var_out[(size_t)row * NY + o] = var;
+    }
+}
+
 template <bool PREDICT>
 cudaError_t launch_impl(const RolloutArgs &a, cudaStream_t s, long long slots)
 {
@@ -546,7 +619,9 @@ cudaError_t launch_rollout_fp32(const RolloutArgs &a, cudaStream_t s)
 
 cudaError_t launch_predict_fp32(const RolloutArgs &a, cudaStream_t s)
 {
-    return launch_impl<true>(a, s, (long long)a.n_pred);
+    if (a.n_pred <= 0 || a.n_pred > 0x7fffffff || a.P <= 0) return cudaErrorInvalidValue;
+    predict_rows_kernel<<<dim3((unsigned)a.n_pred, NY), PR_THREADS, 0, s>>>(a);
+    return cudaGetLastError();
 }
 
 std::atomic<uint64_t> g_batch_attr, g_group_attr;

@@ -394,6 +394,30 @@ def test_precision_workload_sampled(oracle):
     assert ec <= S_TOL
 
 
+@pytest.mark.parametrize("L,form", [(70, "fp32"), (1, "fp32"), (257, "tc")])
+def test_rh_advance_plant_step(oracle, L, form):
+    """The receding-horizon step (Sec. 3.1): the plant, the LWPR mean model, moves x0 by
+    one Euler step under u_out[0] (R13), against the oracle's Eq. 1 prediction; the plan
+    is shifted left with its last control repeated (bitwise)."""
+    from paper_1503_00330_b300.api import Controller
+    p = W.problem(64, 9, L, seed=40 + L)
+    ctl = Controller(p.model, p.cost, precision=form)
+    g = np.random.default_rng(L)
+    x0 = (p.x0 + g.normal(0, 0.3, 12)).astype(np.float32)
+    u = g.normal(0, 0.3, (p.T, 4)).astype(np.float32)
+    xd = torch.as_tensor(x0, device="cuda").clone()
+    ud = torch.as_tensor(u, device="cuda").clone()
+    un = torch.empty_like(ud)
+    ctl.rh_advance(xd, ud, un)
+    ctl.sync()
+    y, _ = oracle.lwpr_predict(p.model, np.concatenate([x0, u[0]]))
+    x_ref = x0.astype(np.float64) + float(p.model.dt) * y.reshape(-1)
+    err = np.max(np.abs(xd.cpu().numpy() - x_ref) / (1.0 + np.abs(x_ref)))
+    print(f"plant step L={L} ({form}): rel err {err:.3g}")
+    assert err <= 1e-6
+    assert np.array_equal(un.cpu().numpy(), np.concatenate([u[1:], u[-1:]]))
+
+
 @pytest.mark.parametrize("form", ["fp32", "tc"])
 def test_u_out_may_alias_u_nominal(form):
     """The header lets u_out alias u_nominal (an in-place plan update): the
