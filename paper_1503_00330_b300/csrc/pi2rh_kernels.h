@@ -25,7 +25,7 @@ inline cudaError_t set_smem_once(std::atomic<uint64_t> &done, Kernel *kernel, in
     return e;
 }
 
-// Arguments of the fused rollout kernel (also used in prediction-only mode).
+// Arguments of the fused rollout kernel (also of the prediction kernel).
 struct RolloutArgs {
     const float2 *rec;       // packed model [NY][P][REC_LEN]
     int P;                   // field pairs per output
@@ -41,8 +41,8 @@ struct RolloutArgs {
     float *cost_tk;          // [T][K] running cost (mean over sub-rollouts)
     float4 *eps_tk;          // [T][K] control perturbations
     float *phi;              // [K] terminal cost (mean over sub-rollouts)
-    const float *z_in;       // prediction mode: [n_pred][NZ]
-    float *y_out, *var_out;  // prediction mode: [n_pred][NY]
+    const float *z_in;       // prediction: [n_pred][NZ]
+    float *y_out, *var_out;  // prediction: [n_pred][NY]
     int n_pred;
     int *err;                // device error word
 };

@@ -197,21 +197,18 @@ __device__ __forceinline__ void fp32_init_barriers(const Fp32Smem &S)
     fence_mbar_init();
 }
 
-// Producer (one lane): streams the field-pair records of outputs o_lo ..
-// o_lo + n_out - 1 for one work item (nsteps passes over them) through the
-// stage ring.  `g0` is the ring position at the start of the item; returns
-// the position after it, or -1 after a timeout (abort flag set).
-template <bool PREDICT>
-__device__ long long fp32_producer(const RolloutArgs &a, const Fp32Smem &S, long long g0, long long &issued,
-                                   int o_lo = 0, int n_out = NY)
+// Producer (one lane): streams the field-pair records of all outputs for one
+// work item (T passes over them) through the stage ring.  `g0` is the ring
+// position at the start of the item; returns the position after it, or -1
+// after a timeout (abort flag set).
+__device__ long long fp32_producer(const RolloutArgs &a, const Fp32Smem &S, long long g0, long long &issued)
 {
     unsigned char *stage_base = S.stage_base;
     uint64_t *full = S.full, *empty = S.empty;
     volatile int *abort_flag = S.abort_flag;
     const int P = a.P, spo = a.stages_per_out;
-    const int G = n_out * spo;
-    const int nsteps = PREDICT ? 2 : a.T;
-    const long long total = g0 + (long long)G * nsteps;
+    const int G = NY * spo;
+    const long long total = g0 + (long long)G * a.T;
         for (long long g = g0; g < total; ++g) {
             const int slot = (int)(g % NSTAGE);
             if (g >= NSTAGE) {
@@ -223,7 +220,7 @@ __device__ long long fp32_producer(const RolloutArgs &a, const Fp32Smem &S, long
                 }
             }
             const int gs = (int)((g - g0) % G);
-            const int o = o_lo + gs / spo, s = gs % spo;
+            const int o = gs / spo, s = gs % spo;
             const int p0 = s * RF_PAIRS_PER_STAGE;
             const int np = min(RF_PAIRS_PER_STAGE, P - p0);
             const uint32_t bytes = (uint32_t)np * REC_BYTES;
@@ -237,12 +234,8 @@ __device__ long long fp32_producer(const RolloutArgs &a, const Fp32Smem &S, long
 
 // Consumers (8 warps): evaluate the LWPR model for the 64 slots of one work
 // item starting at slot_base, step the dynamics and write the item's outputs.
-// `g` is the ring position (advanced in step with the producer).  Prediction
-// mode may cover only outputs o_lo .. o_lo + n_out - 1 (each output's mean and
-// variance depend on that output's fields alone).
-template <bool PREDICT>
-__device__ void fp32_consumer(const RolloutArgs &a, const Fp32Smem &S, long long slot_base, long long &g, bool &aborted,
-                              int o_lo = 0, int n_out = NY)
+// `g` is the ring position (advanced in step with the producer).
+__device__ void fp32_consumer(const RolloutArgs &a, const Fp32Smem &S, long long slot_base, long long &g, bool &aborted)
 {
     unsigned char *stage_base = S.stage_base;
     float *part = S.part, *zbuf = S.zbuf, *xbuf = S.xbuf, *ybuf = S.ybuf, *vbuf = S.vbuf, *yrbuf = S.yrbuf,
@@ -252,25 +245,18 @@ __device__ void fp32_consumer(const RolloutArgs &a, const Fp32Smem &S, long long
     volatile int *abort_flag = S.abort_flag;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int P = a.P, spo = a.stages_per_out;
-    const int nsteps = PREDICT ? 2 : a.T;
-    const int M = PREDICT ? 1 : a.M;
+    const int nsteps = a.T;
+    const int M = a.M;
     const int slotA = lane, slotB = lane + 32;
 
     // Step-thread state: thread tid < SLOTS owns slot tid.
     const bool stepper = tid < SLOTS;
     const long long gslot = slot_base + tid;
     const int k = (int)(gslot / M), m = (int)(gslot % M);
-    const bool writer = stepper && !PREDICT && k < a.K && m == 0;
+    const bool writer = stepper && k < a.K && m == 0;
 
     if (stepper) {
-        if (PREDICT) {
-            const bool ok = gslot < a.n_pred;
-#pragma unroll
-            for (int c = 0; c < NZ; ++c)
-                zbuf[c * SLOTS + tid] = ok ? a.z_in[(size_t)gslot * NZ + c] : 0.0f;
-#pragma unroll
-            for (int o = 0; o < NY; ++o) yrbuf[o * SLOTS + tid] = 0.0f;
-        } else {
+        {
             float4 n = box_muller4(noise_block(a.seed, (uint32_t)k, 0u, 0u, 0u));
             float eps[4] = {a.sqrt_sigma_u[0] * n.x, a.sqrt_sigma_u[1] * n.y,
                             a.sqrt_sigma_u[2] * n.z, a.sqrt_sigma_u[3] * n.w};
@@ -297,7 +283,7 @@ __device__ void fp32_consumer(const RolloutArgs &a, const Fp32Smem &S, long long
             zA[c] = make_float2(va, va);
             zB[c] = make_float2(vb, vb);
         }
-        for (int o = o_lo; o < o_lo + n_out; ++o) {
+        for (int o = 0; o < NY; ++o) {
             const float ya = -yrbuf[o * SLOTS + slotA], yb = -yrbuf[o * SLOTS + slotB];
             const float2 yrA = make_float2(ya, ya), yrB = make_float2(yb, yb);
             Soft stA, stB;
@@ -342,17 +328,7 @@ __device__ void fp32_consumer(const RolloutArgs &a, const Fp32Smem &S, long long
             }
         }
 
-        if (stepper && PREDICT) {
-            if (t == 0) {
-                for (int o = o_lo; o < o_lo + n_out; ++o) yrbuf[o * SLOTS + tid] = ybuf[o * SLOTS + tid];
-            } else if (gslot < a.n_pred) {
-                for (int o = o_lo; o < o_lo + n_out; ++o) {
-                    a.y_out[(size_t)gslot * NY + o] = ybuf[o * SLOTS + tid];
-                    a.var_out[(size_t)gslot * NY + o] = vbuf[o * SLOTS + tid];
-                }
-            }
-        }
-        if (stepper && !PREDICT) {
+        if (stepper) {
             float y[NY], var[NY];
 #pragma unroll
             for (int o = 0; o < NY; ++o) {
@@ -421,23 +397,19 @@ __device__ void fp32_consumer(const RolloutArgs &a, const Fp32Smem &S, long long
     }
 }
 
-// blockIdx.x = 64-slot block; in prediction mode blockIdx.y selects a group
-// of NY / gridDim.y outputs.
-template <bool PREDICT>
+// blockIdx.x = 64-slot block.
 __global__ void __launch_bounds__(NTHREADS, 1) rollout_fp32_kernel(const __grid_constant__ RolloutArgs a)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     const Fp32Smem S = fp32_smem(smem);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int n_out = PREDICT ? NY / (int)gridDim.y : NY;
-    const int o_lo = PREDICT ? (int)blockIdx.y * n_out : 0;
     if (tid == 0) fp32_init_barriers(S);
     for (int i = tid; i < a.cost.n_obs; i += NTHREADS) S.obs_s[i] = a.cost.obs[i];
     __syncthreads();
     if (warp == CW) {
         if (lane != 0) return;
         long long issued = 0;
-        fp32_producer<PREDICT>(a, S, 0, issued, o_lo, n_out);
+        fp32_producer(a, S, 0, issued);
         // keep the CTA alive until every copy issued has landed
         for (long long g = (issued > NSTAGE ? issued - NSTAGE : 0); g < issued; ++g)
             if (!mbar_wait_drain(&S.full[g % NSTAGE], (uint32_t)((g / NSTAGE) & 1))) atomicOr(a.err, DEVERR_TIMEOUT_DRAIN);
@@ -445,7 +417,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) rollout_fp32_kernel(const __grid_
     }
     long long g = 0;
     bool aborted = false;
-    fp32_consumer<PREDICT>(a, S, (long long)blockIdx.x * SLOTS, g, aborted, o_lo, n_out);
+    fp32_consumer(a, S, (long long)blockIdx.x * SLOTS, g, aborted);
 }
 
 // Persistent batched form: CTAs take (controller, slot block) work items from
@@ -475,11 +447,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) rollout_fp32_batch_kernel(const _
         __syncthreads();
         if (warp == CW) {
             if (lane == 0) {
-                const long long next = fp32_producer<false>(a, S, g, issued);
+                const long long next = fp32_producer(a, S, g, issued);
                 g = next < 0 ? g : next;
             }
         } else {
-            fp32_consumer<false>(a, S, (long long)it.y * SLOTS, g, aborted);
+            fp32_consumer(a, S, (long long)it.y * SLOTS, g, aborted);
         }
         __syncthreads();
     }
@@ -509,17 +481,17 @@ __global__ void __launch_bounds__(NTHREADS, 1) rollout_fp32_group_kernel(const _
     if (warp == CW) {
         if (lane != 0) return;
         long long issued = 0;
-        fp32_producer<false>(a, S, 0, issued);
+        fp32_producer(a, S, 0, issued);
         for (long long g = (issued > NSTAGE ? issued - NSTAGE : 0); g < issued; ++g)
             if (!mbar_wait_drain(&S.full[g % NSTAGE], (uint32_t)((g / NSTAGE) & 1))) atomicOr(a.err, DEVERR_TIMEOUT_DRAIN);
         return;
     }
     long long g = 0;
     bool aborted = false;
-    fp32_consumer<false>(a, S, (long long)it.y * SLOTS, g, aborted);
+    fp32_consumer(a, S, (long long)it.y * SLOTS, g, aborted);
 }
 
-std::atomic<uint64_t> g_attr_set[2];
+std::atomic<uint64_t> g_attr_set;
 
 // Prediction of a few rows (the receding-horizon plant step, one row, and a
 // serving group's plant steps, one row per agent): one CTA per (row, output).
@@ -527,8 +499,8 @@ std::atomic<uint64_t> g_attr_set[2];
 // that one row, straight from the packed records in global memory (they stay
 // L2-resident), and the per-thread softmax states are merged over the CTA in a
 // fixed order, so every row's result is deterministic and independent of the
-// other rows.  Two passes, as in the rollout kernel's prediction mode: the
-// second centres the local predictions on the first pass's mean.
+// other rows.  Two passes: the second centres the local predictions on the
+// first pass's mean (the centring the rollout kernel gets from the last step).
 constexpr int PR_THREADS = 256;
 
 __device__ __forceinline__ void soft_merge(Soft &a, const Soft &b)
@@ -594,18 +566,14 @@ __global__ void __launch_bounds__(PR_THREADS) predict_rows_kernel(const __grid_c
     }
 }
 
-template <bool PREDICT>
 cudaError_t launch_impl(const RolloutArgs &a, cudaStream_t s, long long slots)
 {
     if (a.cost.n_obs > MAX_OBS || a.P <= 0 || a.stages_per_out <= 0) return cudaErrorInvalidValue;
-    cudaError_t e = set_smem_once(g_attr_set[PREDICT], rollout_fp32_kernel<PREDICT>, SMEM_BYTES);
+    cudaError_t e = set_smem_once(g_attr_set, rollout_fp32_kernel, SMEM_BYTES);
     if (e != cudaSuccess) return e;
     const long long blocks = (slots + SLOTS - 1) / SLOTS;
     if (blocks <= 0 || blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
-    // prediction of a few rows (the receding-horizon plant step): one CTA per
-    // output instead of one CTA sweeping all 12 outputs
-    const unsigned out_groups = PREDICT && blocks * NY <= 4 * 148 ? NY : 1;
-    rollout_fp32_kernel<PREDICT><<<dim3((unsigned)blocks, out_groups), NTHREADS, SMEM_BYTES, s>>>(a);
+    rollout_fp32_kernel<<<(unsigned)blocks, NTHREADS, SMEM_BYTES, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -614,12 +582,12 @@ cudaError_t launch_impl(const RolloutArgs &a, cudaStream_t s, long long slots)
 cudaError_t launch_rollout_fp32(const RolloutArgs &a, cudaStream_t s)
 {
     if (a.M < 1 || a.M > SLOTS || (a.M & (a.M - 1)) != 0) return cudaErrorInvalidValue;
-    return launch_impl<false>(a, s, (long long)a.K * a.M);
+    return launch_impl(a, s, (long long)a.K * a.M);
 }
 
 cudaError_t launch_predict_fp32(const RolloutArgs &a, cudaStream_t s)
 {
-    if (a.n_pred <= 0 || a.n_pred > 0x7fffffff || a.P <= 0) return cudaErrorInvalidValue;
+    if (a.n_pred <= 0 || a.P <= 0) return cudaErrorInvalidValue;
     predict_rows_kernel<<<dim3((unsigned)a.n_pred, NY), PR_THREADS, 0, s>>>(a);
     return cudaGetLastError();
 }
