@@ -83,9 +83,11 @@ __device__ __forceinline__ float2 f2(float4 v, int hi)
 
 // Row I of the symmetric quadratic form: s += d_I (sum_{j>=I} A_Ij d_j), for
 // both slots; rows are expanded at compile time so every index is constant.
+// Even rows add into s, odd rows into s2 (summed once at the end), which
+// halves the dependency chain across the 16 rows.
 template <int I>
 __device__ __forceinline__ void quad_rows(const float4 *__restrict__ r4, const float2 (&dA)[NZ],
-                                          const float2 (&dB)[NZ], float2 &sA, float2 &sB)
+                                          const float2 (&dB)[NZ], float2 &sA, float2 &sB, float2 &sA2, float2 &sB2)
 {
     if constexpr (I < NZ) {
         constexpr int base = REC_A + tri_index(I, I);   // first entry of row I
@@ -99,9 +101,14 @@ __device__ __forceinline__ void quad_rows(const float4 *__restrict__ r4, const f
             tA = __ffma2_rn(aij, dA[j], tA);
             tB = __ffma2_rn(aij, dB[j], tB);
         }
-        sA = __ffma2_rn(dA[I], tA, sA);
-        sB = __ffma2_rn(dB[I], tB, sB);
-        quad_rows<I + 1>(r4, dA, dB, sA, sB);
+        if (I & 1) {
+            sA2 = __ffma2_rn(dA[I], tA, sA2);
+            sB2 = __ffma2_rn(dB[I], tB, sB2);
+        } else {
+            sA = __ffma2_rn(dA[I], tA, sA);
+            sB = __ffma2_rn(dB[I], tB, sB);
+        }
+        quad_rows<I + 1>(r4, dA, dB, sA, sB, sA2, sB2);
     }
 }
 
@@ -122,7 +129,10 @@ __device__ __forceinline__ void process_pair(const float4 *__restrict__ r4, cons
     float4 tail = r4[REC_B >> 1];        // {b.x, b.y, var.x, var.y}
     float4 tail2 = r4[REC_BIAS >> 1];    // {bias.x, bias.y, 0, 0}
     float2 sA = f2(tail2, 0), sB = sA;
-    quad_rows<0>(r4, dA, dB, sA, sB);
+    float2 sA2 = make_float2(0.f, 0.f), sB2 = sA2;
+    quad_rows<0>(r4, dA, dB, sA, sB, sA2, sB2);
+    sA = __fadd2_rn(sA, sA2);
+    sB = __fadd2_rn(sB, sB2);
     float2 b = f2(tail, 0);
     float2 eA = __fadd2_rn(b, yrA), eB = __fadd2_rn(b, yrB);   // yr holds -y_ref
 #pragma unroll
