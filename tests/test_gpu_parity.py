@@ -433,3 +433,35 @@ def test_u_out_may_alias_u_nominal(form):
     ctl.sync()
     assert u_in.data_ptr() == plan.data_ptr()
     assert torch.equal(plan, u_sep) and torch.equal(c_in, c_sep)
+
+
+def _damped_model(L, seed):
+    """The synthetic model with each output's slope on its own state set to -3
+    and the other slopes scaled by 0.3, so that long rollouts stay bounded
+    (the undamped draw grows without bound over thousands of steps)."""
+    m = W.make_lwpr(L, seed)
+    beta = m.beta.astype(np.float64) * 0.3
+    for o in range(beta.shape[0]):
+        beta[o, :, o] = -3.0
+    m.beta = np.ascontiguousarray(beta.astype(np.float32))
+    return m
+
+
+@pytest.mark.parametrize("form", ["fp32", "tc"])
+@pytest.mark.parametrize("K,T,L,M,lam,damped", [(3, 4096, 1, 1, 1.0, True), (24, 1000, 5, 2, 5.0, True),
+                                                (5, 12, 3, 64, 1.0, False)])
+def test_end_to_end_long_horizon_and_most_subrollouts(oracle, form, K, T, L, M, lam, damped):
+    """T = 4096 (the longest horizon the no-alloc entry point takes; 128 scan
+    chunks) and T = 1000 with sub-rollouts, and M = 64 sub-rollouts per rollout
+    (the largest M), in both forms, at the end-to-end tolerances."""
+    model = _damped_model(L, 2000 + K) if damped else None
+    p = W.problem(K, T, L, seed=2000 + K, n_obs=5, M=M, model=model, lam=lam)
+    ctl = _ctrl(p, precision=form)
+    u, c = ctl.update(p.x0, p.u_nom, p.K, p.T, p.lam, p.sigma_u, p.seed)
+    ctl.sync()
+    uref, cref = _oracle_update(oracle, p)
+    eu = _u_err(u.cpu().numpy(), uref)
+    ec = np.max(np.abs(c.cpu().numpy() - cref) / cref)
+    print(f"K={K} T={T} L={L} M={M} ({form}): u err {eu} cost err {ec:.3g}")
+    assert np.all(eu <= U_TOL)
+    assert ec <= S_TOL
