@@ -504,13 +504,18 @@ __global__ void __launch_bounds__(NTHREADS, 1) rollout_fp32_group_kernel(const _
 std::atomic<uint64_t> g_attr_set;
 
 // Prediction of a few rows (the receding-horizon plant step, one row, and a
-// serving group's plant steps, one row per agent): one CTA per (row, output).
-// Its threads take the output's field pairs p = tid, tid + PR_THREADS, ... for
-// that one row, straight from the packed records in global memory (they stay
-// L2-resident), and the per-thread softmax states are merged over the CTA in a
-// fixed order, so every row's result is deterministic and independent of the
-// other rows.  Two passes: the second centres the local predictions on the
-// first pass's mean (the centring the rollout kernel gets from the last step).
+// serving group's plant steps, one row per agent): one cluster of PR_SPLIT
+// CTAs per (row, output), PR_THREADS threads in all.  Thread v of the cluster
+// takes the output's field pairs p = v, v + PR_THREADS, ... for that one row;
+// it copies each record into shared memory with all of its 16-byte copies in
+// flight (cp.async), which turns the walk through the record from a chain of
+// dependent global loads into one round trip.  The per-thread softmax states
+// are merged in a fixed order (a shuffle tree per warp, then the warps in
+// order by cluster rank 0 over distributed shared memory), so every row's
+// result is deterministic and independent of the other rows.  Two passes: the
+// second centres the local predictions on the first pass's mean (the centring
+// the rollout kernel gets from the last step); with at most PR_THREADS pairs
+// the records stay in shared memory for it.
 constexpr int PR_THREADS = 256;
 
 __device__ __forceinline__ void soft_merge(Soft &a, const Soft &b)
@@ -525,28 +530,62 @@ __device__ __forceinline__ void soft_merge(Soft &a, const Soft &b)
     a.m = M;
 }
 
-__global__ void __launch_bounds__(PR_THREADS) predict_rows_kernel(const __grid_constant__ RolloutArgs a)
+constexpr int PR_SPLIT = 4;                               // CTAs per (row, output): one cluster
+constexpr int PR_CTA_THREADS = PR_THREADS / PR_SPLIT;     // 64
+constexpr int PR_SMEM = PR_CTA_THREADS * REC_BYTES;       // one record per thread: 88,064 B
+
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src)
 {
-    __shared__ float zs[NZ];
-    __shared__ Soft wpart[PR_THREADS / 32];
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem_dst)), "l"(gmem_src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
+__device__ __forceinline__ float ld_cluster_f32(uint32_t addr)
+{
+    float v;
+    asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(addr) : "memory");
+    return v;
+}
+
+// blockIdx = (row, output, cluster rank).  Thread t of rank c is thread
+// v = c * PR_CTA_THREADS + t of the cluster.
+__global__ void __launch_bounds__(PR_CTA_THREADS) predict_rows_kernel(const __grid_constant__ RolloutArgs a)
+{
+    extern __shared__ __align__(16) unsigned char pr_rec[];
+    __shared__ Soft wpart[PR_CTA_THREADS / 32];
     __shared__ float yvar[2];
     const int row = blockIdx.x, o = blockIdx.y, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid < NZ) zs[tid] = a.z_in[(size_t)row * NZ + tid];
-    __syncthreads();
+    const uint32_t crank = cluster_rank();
+    const int vt = (int)crank * PR_CTA_THREADS + tid;
     float2 z2[NZ];
 #pragma unroll
-    for (int c = 0; c < NZ; ++c) z2[c] = make_float2(zs[c], zs[c]);
+    for (int c = 0; c < NZ; ++c) {
+        const float zc = a.z_in[(size_t)row * NZ + c];
+        z2[c] = make_float2(zc, zc);
+    }
+    float4 *mine = reinterpret_cast<float4 *>(pr_rec + (size_t)tid * REC_BYTES);
+    const int rounds = (a.P + PR_THREADS - 1) / PR_THREADS;
     float yref = 0.0f, y = 0.0f, var = 0.0f;
     for (int pass = 0; pass < 2; ++pass) {
         const float2 yr = make_float2(-yref, -yref);
         Soft st, unused;
         soft_init(st);
         soft_init(unused);
-        for (int p = tid; p < a.P; p += PR_THREADS) {
-            const float4 *r4 = reinterpret_cast<const float4 *>(a.rec + ((size_t)o * a.P + p) * REC_LEN);
-            process_pair(r4, z2, z2, yr, yr, st, unused);   // the second slot is not needed
+        for (int i = 0; i < rounds; ++i) {
+            const int p = vt + i * PR_THREADS;
+            if (p >= a.P) break;
+            if (pass == 0 || rounds > 1) {   // with one round the record stays for the second pass
+                const float4 *src = reinterpret_cast<const float4 *>(a.rec + ((size_t)o * a.P + p) * REC_LEN);
+#pragma unroll 2
+                for (int j = 0; j < REC_BYTES / 16; ++j) cp_async16(mine + j, src + j);
+                cp_async_wait_all();
+            }
+            process_pair(mine, z2, z2, yr, yr, st, unused);   // the second slot is not needed
         }
-        // lane 0 of each warp merges its lanes in a fixed tree order, thread 0 the warps in order
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
             const Soft other{__shfl_down_sync(0xffffffffu, st.m, off), __shfl_down_sync(0xffffffffu, st.s0, off),
@@ -555,26 +594,36 @@ __global__ void __launch_bounds__(PR_THREADS) predict_rows_kernel(const __grid_c
             soft_merge(st, other);
         }
         if (lane == 0) wpart[warp] = st;
-        __syncthreads();
-        if (tid == 0) {
+        cluster_sync_all();   // every rank's warp states written
+        if (crank == 0 && tid == 0) {
             Soft all = wpart[0];
-            for (int w = 1; w < PR_THREADS / 32; ++w) soft_merge(all, wpart[w]);
+            for (int w = 1; w < PR_THREADS / 32; ++w) {
+                const uint32_t base = mapa_shared(&wpart[w % (PR_CTA_THREADS / 32)], (uint32_t)(w / (PR_CTA_THREADS / 32)));
+                const Soft other{ld_cluster_f32(base), ld_cluster_f32(base + 4), ld_cluster_f32(base + 8),
+                                 ld_cluster_f32(base + 12), ld_cluster_f32(base + 16)};
+                soft_merge(all, other);
+            }
             const float inv = 1.0f / all.s0;
             const float mean_e = all.s1 * inv;
-            yvar[0] = yref + mean_e;
-            yvar[1] = fmaxf(fmaf(-mean_e, mean_e, all.s2 * inv), 0.0f) + all.s3 * inv;
+            const float yv = yref + mean_e;
+            const float vv = fmaxf(fmaf(-mean_e, mean_e, all.s2 * inv), 0.0f) + all.s3 * inv;
+            for (uint32_t r = 0; r < PR_SPLIT; ++r) {
+                st_cluster_f32(mapa_shared(&yvar[0], r), yv);
+                st_cluster_f32(mapa_shared(&yvar[1], r), vv);
+            }
         }
-        __syncthreads();
+        cluster_sync_all();   // yvar everywhere; the warp states read
         y = yvar[0];
         var = yvar[1];
         yref = y;
-        __syncthreads();   // yvar is rewritten by the next pass
     }
-    if (tid == 0) {
+    if (crank == 0 && tid == 0) {
         a.y_out[(size_t)row * NY + o] = y;
         a.var_out[(size_t)row * NY + o] = var;
     }
 }
+
+std::atomic<uint64_t> g_pred_attr;
 
 cudaError_t launch_impl(const RolloutArgs &a, cudaStream_t s, long long slots)
 {
@@ -598,8 +647,21 @@ cudaError_t launch_rollout_fp32(const RolloutArgs &a, cudaStream_t s)
 cudaError_t launch_predict_fp32(const RolloutArgs &a, cudaStream_t s)
 {
     if (a.n_pred <= 0 || a.P <= 0) return cudaErrorInvalidValue;
-    predict_rows_kernel<<<dim3((unsigned)a.n_pred, NY), PR_THREADS, 0, s>>>(a);
-    return cudaGetLastError();
+    cudaError_t e = set_smem_once(g_pred_attr, predict_rows_kernel, PR_SMEM);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    cfg.gridDim = dim3((unsigned)a.n_pred, NY, PR_SPLIT);
+    cfg.blockDim = dim3(PR_CTA_THREADS);
+    cfg.dynamicSmemBytes = PR_SMEM;
+    cfg.stream = s;
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 1;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = PR_SPLIT;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, predict_rows_kernel, a);
 }
 
 std::atomic<uint64_t> g_batch_attr, g_group_attr;
