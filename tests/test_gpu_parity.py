@@ -83,8 +83,10 @@ def test_normals_fp32(oracle):
 # ---------------------------------------------------------------------------
 # LWPR prediction (Eq. 1)
 # ---------------------------------------------------------------------------
-@pytest.mark.parametrize("L,n", [(1, 5), (3, 70), (17, 130), (64, 200), (255, 65)])
+@pytest.mark.parametrize("L,n", [(1, 5), (3, 70), (17, 130), (64, 200), (255, 65), (700, 40), (1025, 9)])
 def test_lwpr_predict(oracle, L, n):
+    """L = 700 and 1025 give 350 and 513 field pairs: two and three rounds of the
+    prediction kernel's 256 threads, with the records reloaded for the second pass."""
     p = W.problem(8, 4, L, seed=L)
     ctl = _ctrl(p)
     g = np.random.default_rng(L)
