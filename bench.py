@@ -354,6 +354,24 @@ def reduction_rooflines(scan_ms, merge_ms, K, T, peaks, device=0):
     return out
 
 
+def plant_step_roofline(plant_ms, L, peaks, precision):
+    """The plant step of the receding-horizon loop (``pi_rh_advance``: rh_build_z, the
+    clustered prediction kernel, rh_apply), timed with CUDA events on the launching
+    stream.  Its algorithmic bytes are one read of the FP32 field-pair records of the 12
+    outputs (1376 B per pair of fields; the second, re-centred pass re-reads them from
+    shared memory when L <= 512, from L2 otherwise).  It is a small launch, bound by
+    latency: the fraction is given against the measured HBM copy peak."""
+    recs = 12 * ((L + 1) // 2) * 1376
+    hbm = float(peaks.get("hbm_gbs", 6492.1))
+    avg = statistics.mean(plant_ms)
+    gbs = recs / (avg / 1e3) / 1e9
+    return {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+            "bytes_per_launch": recs, "ms_per_launch": avg, "launches_per_step": 3,
+            "kernel": "rh_build_z + predict_rows_kernel + rh_apply",
+            "data": ("records last read by the rollout kernel (L2-resident)" if precision == "fp32" else
+                     "records not read by the tensor-core rollout, so they come from DRAM after the L2 flush")}
+
+
 def time_form(precision, p, args, dev):
     """The receding-horizon loop of `p` timed the same way with the other form."""
     import torch
@@ -368,13 +386,16 @@ def time_form(precision, p, args, dev):
     costs = torch.empty(K, dtype=torch.float32, device=dev)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
-    rollout_ms, step_ms, scan_ms, merge_ms = [], [], [], []
+    rollout_ms, step_ms, scan_ms, merge_ms, plant_ms = [], [], [], [], []
     for i in range(args.warmup + args.steps):
         flush.zero_()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        pa, pb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
         ctl.update(x0, ua, K, T, p.lam, p.sigma_u, p.seed + i, u_out=ub, costs_out=costs)
+        pa.record(stream)
         ctl.rh_advance(x0, ub, ua)
+        pb.record(stream)
         b.record(stream)
         st = ctl.stage_times()
         b.synchronize()
@@ -383,6 +404,7 @@ def time_form(precision, p, args, dev):
             scan_ms.append(st[1])
             merge_ms.append(st[2])
             step_ms.append(a.elapsed_time(b))
+            plant_ms.append(pa.elapsed_time(pb))
     ctl.sync()
     ctl.close()
     total_s = sum(step_ms) / 1e3
@@ -391,7 +413,8 @@ def time_form(precision, p, args, dev):
     roof["secondary"] = mufu_check(precision, rollout_ms, K, T, M, L, dev.index or 0)
     return {"value": K * T * M * args.steps / total_s, "ms_per_update": 1e3 * total_s / args.steps,
             "ms_per_update_stats": {"best": min(step_ms), "median": statistics.median(step_ms), "n": len(step_ms)},
-            "roofline": roof, "reduction": reduction_rooflines(scan_ms, merge_ms, K, T, measured_peaks(), dev.index or 0)}
+            "roofline": roof, "reduction": {**reduction_rooflines(scan_ms, merge_ms, K, T, measured_peaks(), dev.index or 0),
+                                            "plant_step": plant_step_roofline(plant_ms, L, measured_peaks(), precision)}}
 
 
 def run_batched(args):
@@ -605,9 +628,13 @@ def run_ours(args):
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
-    def rh_step(it):
+    def rh_step(it, plant_ev=None):
         ctl.update(x0, ua, K, T, p.lam, p.sigma_u, p.seed + it, u_out=ub, costs_out=costs)
+        if plant_ev is not None:
+            plant_ev[0].record(stream)
         ctl.rh_advance(x0, ub, ua)                   # next warm start back into ua
+        if plant_ev is not None:
+            plant_ev[1].record(stream)
 
     for it in range(args.warmup):
         rh_step(it)
@@ -615,6 +642,7 @@ def run_ours(args):
 
     # ---- device-timed region -------------------------------------------------
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    pev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     rollout_ms, step_ms, scan_ms, merge_ms = [], [], [], []
     if dist is not None:
         dist.barrier()
@@ -624,7 +652,7 @@ def run_ours(args):
         for i in range(args.steps):
             flush.zero_()                               # L2 flush, outside the event window
             ev[i][0].record(stream)
-            rh_step(args.warmup + i)
+            rh_step(args.warmup + i, pev[i])
             ev[i][1].record(stream)
             st = ctl.stage_times()                      # waits for this update
             rollout_ms.append(st[0])
@@ -636,6 +664,7 @@ def run_ours(args):
     launches = ctl.launch_count() - launches0
     ctl.sync()
     step_ms = [a.elapsed_time(b) for a, b in ev]
+    plant_ms = [a.elapsed_time(b) for a, b in pev]
     total_s = reduce_max(dist, sum(step_ms) / 1e3, dev)
     value = job_throughput(dist, K * T * M * args.steps, sum(step_ms) / 1e3, dev)
 
@@ -664,6 +693,7 @@ def run_ours(args):
     roofline["rollout_share_of_step"] = sum(rollout_ms) / sum(step_ms)
     roofline["secondary"] = mufu_check(args.precision, rollout_ms, K, T, M, L, local)
     reduction = reduction_rooflines(scan_ms, merge_ms, K, T, peaks, local)
+    reduction["plant_step"] = plant_step_roofline(plant_ms, L, peaks, args.precision)
     forms = {args.precision: {"value": value, "ms_per_update": 1e3 * total_s / args.steps,
                               "roofline": roofline, "reduction": reduction}}
     if not args.no_compare:
