@@ -50,7 +50,9 @@ struct RolloutArgs {
 // Rollout slots (rollout x sub-rollout) per CTA of the FP32 rollout kernel.
 constexpr int RF_SLOTS = 64;
 constexpr int RF_CONSUMER_WARPS = 8;
-constexpr int RF_PAIRS_PER_STAGE = RF_CONSUMER_WARPS;
+// Field-pair records per stage of the FP32 kernel's record ring: 8 per
+// consumer warp, so each warp's waits and arrivals are amortized over 8 records.
+constexpr int RF_PAIRS_PER_STAGE = 8 * RF_CONSUMER_WARPS;
 
 // Work list of the persistent batched rollout kernels: item = (controller,
 // slot block); CTAs claim items through *counter (zeroed before the launch).

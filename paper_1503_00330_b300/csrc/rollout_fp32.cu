@@ -15,9 +15,11 @@
 //
 // Data movement: the model is far larger than shared memory (12 L records of
 // 1376 bytes per field pair), so it is streamed through a ring of NSTAGE
-// shared-memory stages by one producer warp issuing 1-D bulk asynchronous
-// copies (TMA) that complete on mbarriers; eight consumer warps each take one
-// field-pair record per stage.  All 32 lanes of a consumer warp read the same
+// shared-memory stages (two of 64 records, 88 KB each) by one producer warp
+// issuing 1-D bulk asynchronous copies (TMA) that complete on mbarriers; each
+// of the eight consumer warps takes 8 field-pair records per stage, records
+// j * 8 + warp, so a warp still walks pairs warp, warp + 8, ... in order and
+// pays one wait and one arrival per 8 records.  All 32 lanes of a consumer warp read the same
 // record (shared-memory broadcast), and each lane evaluates it for two slots,
 // so every parameter load feeds four field-slot evaluations on the packed
 // FP32x2 FMA datapath.  Every wait is bounded; on expiry the kernel records a
@@ -28,7 +30,7 @@ namespace pi2rh {
 
 namespace {
 
-constexpr int NSTAGE = 4;
+constexpr int NSTAGE = 2;
 constexpr int CW = RF_CONSUMER_WARPS;          // consumer warps
 constexpr int NTHREADS = (CW + 1) * 32;        // + one producer warp
 constexpr int NCONS = CW * 32;                 // consumer threads
@@ -51,6 +53,7 @@ constexpr int OFF_BAR = OFF_OBS + MAX_OBS * 8;                      // full[NSTA
 constexpr int OFF_ABORT = OFF_BAR + 2 * NSTAGE * 8;
 constexpr int SMEM_BYTES = OFF_ABORT + 16;
 static_assert(OFF_PART % 16 == 0 && OFF_BAR % 8 == 0, "alignment");
+static_assert(SMEM_BYTES <= 232448, "shared memory budget");
 
 struct Soft {
     float m, s0, s1, s2, s3;
@@ -309,11 +312,14 @@ __device__ void fp32_consumer(const RolloutArgs &a, const Fp32Smem &S, long long
                     }
                     aborted = true;
                 }
-                const int pair = s * RF_PAIRS_PER_STAGE + warp;
-                if (!aborted && pair < P) {
-                    const float4 *r4 = reinterpret_cast<const float4 *>(
-                        stage_base + (size_t)slot * STAGE_BYTES + (size_t)warp * REC_BYTES);
-                    process_pair(r4, zA, zB, yrA, yrB, stA, stB);
+#pragma unroll 1
+                for (int j = 0; j < RF_PAIRS_PER_STAGE / CW; ++j) {
+                    const int pair = s * RF_PAIRS_PER_STAGE + j * CW + warp;
+                    if (!aborted && pair < P) {
+                        const float4 *r4 = reinterpret_cast<const float4 *>(
+                            stage_base + (size_t)slot * STAGE_BYTES + (size_t)(j * CW + warp) * REC_BYTES);
+                        process_pair(r4, zA, zB, yrA, yrB, stA, stB);
+                    }
                 }
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&empty[slot]);
