@@ -312,7 +312,7 @@ __device__ void fp32_consumer(const RolloutArgs &a, const Fp32Smem &S, long long
                     }
                     aborted = true;
                 }
-#pragma unroll 1
+#pragma unroll 2
                 for (int j = 0; j < RF_PAIRS_PER_STAGE / CW; ++j) {
                     const int pair = s * RF_PAIRS_PER_STAGE + j * CW + warp;
                     if (!aborted && pair < P) {
