@@ -62,7 +62,7 @@ constexpr int TNF = TC_TILE_FIELDS;     // fields per tile (MMA N)
 constexpr int KF = TC_KF;               // feature columns of phi (S GEMM K)
 constexpr int NCH = TC_CHUNKS_PER_TILE; // chunks per tile
 constexpr int NSLOT = 12;               // chunk slots in the ring
-constexpr int CPG = 4;                  // chunks per copy group (one bulk copy per contiguous run, one barrier pair)
+constexpr int CPG = 6;                  // chunks per copy group (one bulk copy per contiguous run, one barrier pair)
 constexpr int NGRP = NSLOT / CPG;       // groups in the ring
 static_assert(NSLOT % CPG == 0, "the ring holds whole groups");
 constexpr int NCONST = 4;
