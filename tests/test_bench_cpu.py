@@ -29,3 +29,17 @@ def test_warmup_below_three_is_refused():
     out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
                           "--warmup", "2"], capture_output=True, text=True, timeout=120, cwd=ROOT)
     assert out.returncode != 0 and "warmup" in (out.stderr + out.stdout)
+
+
+def test_plant_step_roofline_counts_one_read_of_the_records():
+    """The plant step's algorithmic bytes are one read of the 12 outputs' FP32
+    field-pair records (1376 B per pair, ceil(L/2) pairs per output), and its
+    fraction is the achieved bandwidth over the HBM peak given."""
+    sys.path.insert(0, ROOT)
+    import bench
+    r = bench.plant_step_roofline([0.02, 0.02], 512, {"hbm_gbs": 6000.0}, "tc")
+    assert r["bytes_per_launch"] == 12 * 256 * 1376
+    assert abs(r["achieved"] - 12 * 256 * 1376 / 0.02e-3 / 1e9) < 1e-9
+    assert abs(r["frac"] - r["achieved"] / 6000.0) < 1e-12
+    assert r["bound"] == "hbm" and r["launches_per_step"] == 3
+    assert bench.plant_step_roofline([0.01], 513, {}, "fp32")["bytes_per_launch"] == 12 * 257 * 1376
