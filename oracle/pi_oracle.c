@@ -39,8 +39,9 @@
  *   - noise: Philox4x32-10 (Salmon et al., SC'11) with counter (k, t, blk, m) and
  *     key (seed lo, seed hi); uniforms u = (2*(r >> 9) + 1) * 2^-24 (exact in
  *     FP32 and FP64); Box-Muller in double precision.
- *   - the obstacle indicator (an integer decision) is taken in FP32, the
- *     precision of the kernels, with separately rounded products and sums.
+ *   - the obstacle indicator of Sec. 5 (inside a cylinder of radius r, strict
+ *     "<": a point on the boundary is outside) is decided in FP64 on the FP64
+ *     state, like every other step here.
  */
 #include <math.h>
 #include <stdint.h>
@@ -202,20 +203,15 @@ void orc_lwpr_predict(const orc_lwpr *P, const double *z, double *y_out, double 
 /* yaw, x[9..11] body rates.                                                */
 /* ------------------------------------------------------------------------ */
 
-/* Integer decision "inside some cylinder", in FP32 with separately rounded
- * operations (the precision of the kernels). */
+/* Sec. 5 crash indicator C: 1 when the position lies strictly inside some
+ * vertical cylinder of radius r (d^2 < r^2), decided in FP64. */
 int orc_inside_any(const orc_cost *C, double px, double py)
 {
-    volatile float fpx = (float)px, fpy = (float)py;
-    volatile float r = (float)C->radius;
-    volatile float r2 = r * r;
+    const double r2 = C->radius * C->radius;
     for (int i = 0; i < C->n_obs; ++i) {
-        volatile float dx = fpx - (float)C->obs_xy[2 * i];
-        volatile float dy = fpy - (float)C->obs_xy[2 * i + 1];
-        volatile float dx2 = dx * dx;
-        volatile float dy2 = dy * dy;
-        volatile float d2 = dx2 + dy2;
-        if (d2 < r2) return 1;
+        double dx = px - C->obs_xy[2 * i];
+        double dy = py - C->obs_xy[2 * i + 1];
+        if (dx * dx + dy * dy < r2) return 1;
     }
     return 0;
 }

@@ -274,6 +274,21 @@ def test_cost_boundary_is_outside(oracle):
     assert oracle.inside_any(cp, 2.0, 2.0) == 0
 
 
+def test_cost_indicator_is_decided_on_the_fp64_state(oracle):
+    """Sec. 5's crash indicator is a property of the real position: points 1e-12
+    inside and outside the boundary of radius 0.3 (0.3 rounded to FP32, as the
+    kernels receive it) are told apart.  Both round to the same FP32 position,
+    so an indicator taken in FP32 would give them the same answer."""
+    cp = _cost(radius=0.3)
+    r = float(np.float32(0.3))
+    assert np.float32(r * (1 - 1e-12)) == np.float32(r * (1 + 1e-12))
+    assert oracle.inside_any(cp, r * (1 - 1e-12), 0.0) == 1
+    assert oracle.inside_any(cp, r * (1 + 1e-12), 0.0) == 0
+    assert oracle.inside_any(cp, 0.0, -r * (1 - 1e-12)) == 1
+    d = r / np.sqrt(2.0) * (1 - 1e-12)                # off the axes as well
+    assert oracle.inside_any(cp, d, d) == 1
+
+
 def test_cost_gaussian_bumps(oracle):
     """The paper's obstacle term 100 sum_i exp(-10 (dx^2 + dy^2)) plus 10 C."""
     cp = W.CostParams(goal=(0, 0, 0), Q_pos=(0, 0, 0), w_obs=100.0, obs_sharp=10.0, radius=0.3,
