@@ -176,15 +176,22 @@ int pi_update(pi_ctx *ctx, const float *x0, const float *u_nominal, int K, int T
  * moment), or a host program that owns all GPU memory through its own pool.
  * There is no counterpart in the paper; it is a deployment variant.
  *
- * Same arguments, results and stream semantics as pi_update, but it calls no
+ * Same arguments, results and stream semantics as pi_update, in either form
+ * (it runs the rollout kernel of the context's opts.precision, FP32 or tensor
+ * cores, and the same reduction kernels, so its results equal pi_update's bit
+ * for bit), but it calls no
  * allocating routine: the per-update scratch lives in one fixed device array
  * of about 21 MiB inside the library, held by every GPU that loads the library
  * until the process exits.  Limits: K <= PI2RH_NOALLOC_MAX_K,
  * T <= PI2RH_NOALLOC_MAX_T, K*T <= PI2RH_NOALLOC_MAX_KT; larger sizes return
  * PI_ERR_INVALID_ARG with a message and launch nothing.
  * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) and caches it; make that first call before any
- * stream capture.  All calls on a device share the one array: calls whose
+ * (cudaGetSymbolAddress) and caches it.  Under CUDA's lazy module loading
+ * (the default) that lookup is also when the runtime loads the array onto the
+ * device, which commits its memory: make the first call on each device during
+ * set-up (a small update will do), before the real-time loop starts and
+ * before any stream capture.  Stage times (pi_set_timing / pi_stage_times)
+ * cover this entry point as they cover pi_update.  All calls on a device share the one array: calls whose
  * work overlaps on the GPU (different streams or contexts without ordering
  * between them) race and corrupt each other's results; order them on one
  * stream or synchronize between them.  Every scratch element a call reads is

@@ -8,14 +8,20 @@
 // allocate behind its back.  Such a caller creates its pi_ctx during set-up
 // and then calls this entry point in its loop.
 //
-// Instead of the context's growable scratch, this path keeps the per-update
+// It runs the rollout kernel of the context's form (FP32 or tensor cores), then
+// the same scan and merge kernels as pi_update, so its results are those of
+// pi_update bit for bit.  Instead of the context's growable scratch, this path keeps the per-update
 // scratch (cost [T][K], eps [T][K][4], phi [K], log-sum-exp partials) in one
 // file-scope device array of fixed size, NOALLOC_BYTES (about 21 MiB), which
 // every GPU that loads the library holds until the process exits.  The
 // array's name is only a host-side stand-in for the device symbol, so the
 // host code below asks the runtime for its device address with
 // cudaGetSymbolAddress, once per device, with that device current, and passes
-// that address to the kernels.
+// that address to the kernels.  With CUDA's lazy module loading (the default),
+// that first lookup is also when the runtime loads this file's module on the
+// device and commits the array's memory, so the first call on each device
+// belongs in the caller's set-up, before its real-time loop and before any
+// stream capture.
 #include <cmath>
 #include <mutex>
 #include <string>
@@ -112,32 +118,43 @@ extern "C" int pi_update_noalloc(pi_ctx *c, const float *x0, const float *u_nom,
         float *phi = reinterpret_cast<float *>(base + NA_PHI_OFF);
         double *part = reinterpret_cast<double *>(base + NA_PART_OFF);
 
-        RolloutArgs a{};
-        a.rec = c->d_rec;
-        a.P = c->P;
-        a.stages_per_out = c->spo;
-        a.cost = c->cost;
-        a.dt = c->dt;
-        a.M = c->opts.M;
-        a.model_noise = c->opts.model_noise == PI_NOISE_SAMPLED ? 1 : 0;
-        a.err = c->d_err;
-        a.K = K;
-        a.T = T;
-        for (int i = 0; i < 4; ++i) a.sqrt_sigma_u[i] = sqrtf(sigma_u[i]);
-        a.seed = seed;
-        a.x0 = x0;
-        a.u_nom = u_nom;
-        a.cost_tk = cost;
-        a.eps_tk = eps;
-        a.phi = phi;
+        const bool tc = c->opts.precision == PI_PRECISION_TC_FP16X3;
+        if (c->timing) rc = na_cuda(cudaEventRecord(c->ev[0], c->stream), "event record");
+        if (rc == PI_OK && tc) {
+            TcArgs t = ctx_tc_args(c);
+            t.K = K;
+            t.T = T;
+            for (int i = 0; i < 4; ++i) t.sqrt_sigma_u[i] = sqrtf(sigma_u[i]);
+            t.seed = seed;
+            t.x0 = x0;
+            t.u_nom = u_nom;
+            t.cost_tk = cost;
+            t.eps_tk = eps;
+            t.phi = phi;
+            rc = na_cuda(launch_rollout_tc(t, c->stream), "tensor-core rollout kernel launch");
+        } else if (rc == PI_OK) {
+            RolloutArgs a = ctx_rollout_args(c);
+            a.K = K;
+            a.T = T;
+            for (int i = 0; i < 4; ++i) a.sqrt_sigma_u[i] = sqrtf(sigma_u[i]);
+            a.seed = seed;
+            a.x0 = x0;
+            a.u_nom = u_nom;
+            a.cost_tk = cost;
+            a.eps_tk = eps;
+            a.phi = phi;
+            rc = na_cuda(launch_rollout_fp32(a, c->stream), "rollout kernel launch");
+        }
+        if (rc == PI_OK && c->timing) rc = na_cuda(cudaEventRecord(c->ev[1], c->stream), "event record");
         const double inv_lam_log2e = 1.4426950408889634074 / (double)lambda;
-        rc = na_cuda(launch_rollout_fp32(a, c->stream), "rollout kernel launch");
         if (rc == PI_OK)
             rc = na_cuda(launch_scan_lse(cost, phi, eps, K, T, c->dt, inv_lam_log2e, costs_out, part, c->stream),
                          "scan kernel launch");
+        if (rc == PI_OK && c->timing) rc = na_cuda(cudaEventRecord(c->ev[2], c->stream), "event record");
         if (rc == PI_OK)
             rc = na_cuda(launch_lse_merge(part, scan_blocks(K), T, inv_lam_log2e, u_nom, u_out, c->stream),
                          "merge kernel launch");
+        if (rc == PI_OK && c->timing) rc = na_cuda(cudaEventRecord(c->ev[3], c->stream), "event record");
         if (rc == PI_OK) c->launches += 3;
     }
     if (prev >= 0 && prev != c->device) cudaSetDevice(prev);
