@@ -352,29 +352,10 @@ def _edge_ranges(K, n=256):
     return [(0, n), (K - n, n)]
 
 
-def test_realtime_workload_sampled(oracle):
-    """K=8192, T=100, L=512, 16 obstacles, launched as the benchmark launches it:
-    the full-K costs of sampled rollouts against the oracle, u_out checked by
-    properties (finite, a convex combination of the perturbations)."""
-    p = W.realtime()
-    ctl = _ctrl(p)
-    u, c = ctl.update(p.x0, p.u_nom, p.K, p.T, p.lam, p.sigma_u, p.seed)
-    cost, eps, phi = ctl.debug_rollout(p.x0, p.u_nom, p.K, p.T, p.sigma_u, p.seed)
-    ctl.sync()
-    c = c.cpu().numpy().astype(np.float64)
-    ks, S0 = _sampled_S0(oracle, p, _edge_ranges(p.K))
-    err = np.abs(c[ks] - S0) / S0
-    print("realtime sampled S0 (512 rollouts) max rel err", err.max())
-    assert np.all(err <= S_TOL)
-    u = u.cpu().numpy()
-    e = np.transpose(eps.cpu().numpy(), (1, 0, 2))
-    assert np.all(np.isfinite(u))
-    assert np.all(u <= p.u_nom + e.max(0) + 1e-6) and np.all(u >= p.u_nom + e.min(0) - 1e-6)
-
-
 def test_precision_workload_sampled(oracle):
     """K=65536, T=100, L=2048, cond(D_j) log-uniform in [1, 1e3]: 512 sampled
-    rollouts' S_{k,0} at full K, and a full u_out check at K=512 (same L, T)."""
+    rollouts' S_{k,0} at full K (the full update at K=2048 and the realtime
+    update in full are checked in the full-size parity tests)."""
     p = W.precision()
     ctl = _ctrl(p)
     u, c = ctl.update(p.x0, p.u_nom, p.K, p.T, p.lam, p.sigma_u, p.seed)
@@ -385,15 +366,6 @@ def test_precision_workload_sampled(oracle):
     print("precision sampled S0 (512 rollouts) max rel err", err.max())
     assert np.all(err <= S_TOL)
     assert np.all(np.isfinite(u.cpu().numpy()))
-    p.K = 512
-    u, c = ctl.update(p.x0, p.u_nom, p.K, p.T, p.lam, p.sigma_u, p.seed)
-    ctl.sync()
-    uref, cref = _oracle_update(oracle, p)
-    eu = _u_err(u.cpu().numpy(), uref)
-    ec = np.max(np.abs(c.cpu().numpy() - cref) / cref)
-    print("precision K=512: u err", eu, "cost err", ec)
-    assert np.all(eu <= U_TOL)
-    assert ec <= S_TOL
 
 
 @pytest.mark.parametrize("L,form", [(70, "fp32"), (1, "fp32"), (257, "tc")])
