@@ -184,18 +184,21 @@ def reduce_max(dist, v: float, device):
     return float(t.item())
 
 
-def cpu_baseline(p, k_sample: int):
-    """FP64 oracle on the first k_sample / M rollouts of one update of the
-    workload (all host threads), and on a 1/8 sample on one thread."""
+def cpu_baseline(p, k_sample: int, k_single: int = 32):
+    """FP64 oracle on one update of the workload's seed-0 inputs with the first
+    k_sample / M rollouts (all host threads), and on k_single rollouts on one
+    thread.  The sample's results are returned too: they are the reference the
+    per-form errors are measured against (rollout k depends only on its own noise
+    counters, so rollouts 0..k_sample-1 of the full-size launch are the sample's)."""
     from oracle import oracle as O
     O.build()
     k_sample = max(1, k_sample // max(p.M, 1))
     t0 = time.perf_counter()
-    O.pi_update(p.model, p.cost, p.x0, p.u_nom, k_sample, p.T, p.lam, p.sigma_u, p.seed, M=p.M,
-                model_noise=p.model_noise)
+    u, S0 = O.pi_update(p.model, p.cost, p.x0, p.u_nom, k_sample, p.T, p.lam, p.sigma_u, p.seed, M=p.M,
+                        model_noise=p.model_noise)
     el = time.perf_counter() - t0
     cores = O.max_threads()
-    k1 = max(k_sample // 8, 1)
+    k1 = max(min(k_single, k_sample), 1)
     O.set_threads(1)
     try:
         t1 = time.perf_counter()
@@ -204,10 +207,49 @@ def cpu_baseline(p, k_sample: int):
         el1 = time.perf_counter() - t1
     finally:
         O.set_threads(cores)
-    return {"value": k_sample * p.T * p.M / el, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"one update of {k_sample} of the {p.K} rollouts (T={p.T}, L={p.model.L}, M={p.M}), "
-                      f"{el:.2f} s",
+    base = {"value": k_sample * p.T * p.M / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"one update of {k_sample} of the {p.K} rollouts (T={p.T}, L={p.model.L}, M={p.M}; "
+                      f"seed-0 inputs), {el:.2f} s",
             "single_thread": {"value": k1 * p.T * p.M / el1, "sample": f"{k1} rollouts on 1 thread, {el1:.2f} s"}}
+    return base, {"K": k_sample, "u": u, "S0": S0}
+
+
+def form_errors(p, form, ref, dev):
+    """Error of each form against the FP64 oracle on the workload's seed-0 inputs (x0 = 0,
+    u_nom = 0, seed = workload seed), on the same context kind the bench times:
+      * costs S_{k,0} of rollouts 0..Ks-1 of the full-size launch (the bench's launch
+        configuration), against the oracle's sample update of Ks rollouts;
+      * u_out (per channel, max_t |du| / max_t |u_ref|) and every cost of a Ks-rollout
+        update against the same oracle update.
+    A rollout whose cost differs by at least half an obstacle step (w_obs dt) is counted as
+    an indicator flip (the oracle decides the crash indicator on its FP64 state, the kernels
+    on their FP32 state) and reported apart."""
+    import torch
+    from paper_1503_00330_b300.api import Controller
+    Ks = ref["K"]
+    ctl = Controller(p.model, p.cost, M=p.M, model_noise=p.model_noise, device=dev.index, precision=form)
+    ctl.reserve(p.K, p.T)
+    x0 = torch.as_tensor(p.x0, device=dev)
+    un = torch.as_tensor(p.u_nom, device=dev)
+    _, c_full = ctl.update(x0, un, p.K, p.T, p.lam, p.sigma_u, p.seed)
+    u_s, c_s = ctl.update(x0, un, Ks, p.T, p.lam, p.sigma_u, p.seed)
+    ctl.sync()
+    S0 = np.asarray(ref["S0"], np.float64)
+    flip = 0.5 * float(p.cost.w_obs) * float(p.model.dt) / p.M
+    out = {}
+    for name, c in (("costs_full_launch", c_full.cpu().numpy()[:Ks]), ("costs_sample_update", c_s.cpu().numpy())):
+        d = np.abs(c.astype(np.float64) - S0)
+        ok = d < flip
+        out[name] = {"rel_err_max": float(np.max(d[ok] / np.abs(S0[ok]))) if ok.any() else None,
+                     "rollouts": int(Ks), "indicator_flips": int((~ok).sum())}
+    uref = np.asarray(ref["u"], np.float64)
+    eu = np.abs(u_s.cpu().numpy().astype(np.float64) - uref).max(0) / np.abs(uref).max(0)
+    out["u_out_rel_err_per_channel"] = [float(e) for e in eu]
+    out["u_out_rel_err_max"] = float(eu.max())
+    out["reference"] = (f"FP64 oracle, one update of the first {Ks} rollouts (the CPU-baseline sample); "
+                        f"costs also against rollouts 0..{Ks - 1} of the full K={p.K} launch")
+    ctl.close()
+    return out
 
 
 def run_reference(args):
@@ -242,11 +284,25 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# Stated accuracy of each form against the FP64 oracle (u_out per channel and costs, relative)
+ERROR_BOUND = {"fp32": 1e-5, "tc": 2e-3}
 TC_FIELDS_PER_TILE = 128                      # fields per tensor-core tile (MMA N)
 TC_MMA_FLOPS_PER_FIELD = 3 * 2 * (160 + 16)   # hi*hi + hi*lo + lo*hi over K=160 (S) and K=16 (Y)
 
 
-def form_roofline(precision, rollout_ms, K, T, M, L, dev, peaks, workload):
+def tensor_peak(peaks, clocks):
+    """Dense bf16 tensor peak for a run with the given clock record: the burst figure when
+    the run was not held at the power cap (the kernel ran at full clock, as the burst GEMM
+    did), the seconds-long sustained figure when the record shows sw_power_cap."""
+    capped = clocks is not None and "sw_power_cap" in (clocks.get("reasons") or [])
+    if capped:
+        return float(peaks.get("bf16_tflops_sustained", 1366.3)), \
+            "measured dense bf16 sustained (the run's clock record shows sw_power_cap)"
+    return float(peaks.get("bf16_tflops", 1788.7)), \
+        "measured dense bf16 burst (no power cap in the run's clock record)"
+
+
+def form_roofline(precision, rollout_ms, K, T, M, L, dev, peaks, workload, clocks=None):
     """Roofline of the rollout kernel from its per-launch CUDA-event times."""
     import torch
     props = torch.cuda.get_device_properties(dev)
@@ -263,13 +319,14 @@ def form_roofline(precision, rollout_ms, K, T, M, L, dev, peaks, workload):
                 "rollout_ms_per_launch": statistics.mean(rollout_ms)}
     L_pad = -(-L // TC_FIELDS_PER_TILE) * TC_FIELDS_PER_TILE
     issued = float(K) * T * M * 12 * L_pad * TC_MMA_FLOPS_PER_FIELD
-    peak = float(peaks.get("bf16_tflops_sustained", 1366.3))
+    peak, basis = tensor_peak(peaks, clocks)
     achieved = issued / avg_s / 1e12
     return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "traffic": profile_traffic(f"rollout_tc_{workload}.md"), "kernel": "rollout_tc_kernel",
-            "peak_basis": "measured dense bf16 sustained (fp16 has the same nominal rate); achieved counts the "
-                          "issued fp16 MMA flops (3 split products x 2 x 176 per field)",
-            "useful_tflops": useful / avg_s / 1e12,
+            "peak_basis": basis + "; fp16 has the same nominal rate; achieved counts the issued fp16 MMA "
+                                  "flops (3 split products x 2 x 176 per field, fields padded to 128-field tiles)",
+            "useful_tflops": useful / avg_s / 1e12, "useful_frac": useful / avg_s / 1e12 / peak,
+            "useful_basis": f"{FLOPS_PER_FIELD} algorithmic flop per field evaluation (the FP32 form's count)",
             "rollout_ms_per_launch": statistics.mean(rollout_ms)}
 
 
@@ -387,7 +444,10 @@ def time_form(precision, p, args, dev):
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
     rollout_ms, step_ms, scan_ms, merge_ms, plant_ms = [], [], [], [], []
+    sampler = ClockSampler(dev.index or 0)
     for i in range(args.warmup + args.steps):
+        if i == args.warmup:
+            sampler.__enter__()
         flush.zero_()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         pa, pb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -405,16 +465,68 @@ def time_form(precision, p, args, dev):
             merge_ms.append(st[2])
             step_ms.append(a.elapsed_time(b))
             plant_ms.append(pa.elapsed_time(pb))
+    sampler.__exit__(None, None, None)
+    clk = sampler.summary()
     ctl.sync()
     ctl.close()
     total_s = sum(step_ms) / 1e3
-    roof = form_roofline(precision, rollout_ms, K, T, M, L, dev, measured_peaks(), args.workload)
+    roof = form_roofline(precision, rollout_ms, K, T, M, L, dev, measured_peaks(), args.workload, clocks=clk)
     roof["rollout_share_of_step"] = sum(rollout_ms) / sum(step_ms)
     roof["secondary"] = mufu_check(precision, rollout_ms, K, T, M, L, dev.index or 0)
     return {"value": K * T * M * args.steps / total_s, "ms_per_update": 1e3 * total_s / args.steps,
             "ms_per_update_stats": {"best": min(step_ms), "median": statistics.median(step_ms), "n": len(step_ms)},
             "roofline": roof, "reduction": {**reduction_rooflines(scan_ms, merge_ms, K, T, measured_peaks(), dev.index or 0),
-                                            "plant_step": plant_step_roofline(plant_ms, L, measured_peaks(), precision)}}
+                                            "plant_step": plant_step_roofline(plant_ms, L, measured_peaks(), precision)},
+            "clocks": clk}
+
+
+def time_updates(precision, p, steps, warmup, dev, workload):
+    """Plain pi_update calls of `p` (no receding-horizon step), device-timed with CUDA events
+    on the launching stream, L2 flushed outside each event window, clocks sampled."""
+    import torch
+    from paper_1503_00330_b300.api import Controller
+    K, T, M, L = p.K, p.T, p.M, p.model.L
+    ctl = Controller(p.model, p.cost, M=M, model_noise=p.model_noise, device=dev.index, precision=precision)
+    ctl.set_timing(True)
+    ctl.reserve(K, T)
+    x0 = torch.as_tensor(p.x0, device=dev).clone()
+    un = torch.as_tensor(p.u_nom, device=dev).clone()
+    u = torch.empty_like(un)
+    costs = torch.empty(K, dtype=torch.float32, device=dev)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    for i in range(warmup):
+        ctl.update(x0, un, K, T, p.lam, p.sigma_u, p.seed + i, u_out=u, costs_out=costs)
+    ctl.sync()
+    rollout_ms, step_ms, scan_ms, merge_ms = [], [], [], []
+    launches0 = ctl.launch_count()
+    with ClockSampler(dev.index or 0) as clocks:
+        for i in range(steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            ctl.update(x0, un, K, T, p.lam, p.sigma_u, p.seed + warmup + i, u_out=u, costs_out=costs)
+            b.record(stream)
+            st = ctl.stage_times()
+            b.synchronize()
+            rollout_ms.append(st[0])
+            scan_ms.append(st[1])
+            merge_ms.append(st[2])
+            step_ms.append(a.elapsed_time(b))
+    launches = ctl.launch_count() - launches0
+    ctl.sync()
+    ctl.close()
+    clk = clocks.summary()
+    total_s = sum(step_ms) / 1e3
+    roof = form_roofline(precision, rollout_ms, K, T, M, L, dev, measured_peaks(), workload, clocks=clk)
+    roof["rollout_share_of_step"] = sum(rollout_ms) / sum(step_ms)
+    roof["secondary"] = mufu_check(precision, rollout_ms, K, T, M, L, dev.index or 0)
+    return {"value": K * T * M * steps / total_s, "ms_per_update": 1e3 * total_s / steps, "steps": steps,
+            "warmup": warmup,
+            "ms_per_update_stats": {"best": min(step_ms), "median": statistics.median(step_ms), "n": len(step_ms)},
+            "gpu_launches": launches, "roofline": roof,
+            "reduction": reduction_rooflines(scan_ms, merge_ms, K, T, measured_peaks(), dev.index or 0),
+            "clocks": clk}
 
 
 def run_batched(args):
@@ -482,10 +594,12 @@ def run_batched(args):
         else:
             issued = sum(p.K * p.T * p.M * 12 * (-(-p.model.L // TC_FIELDS_PER_TILE) * TC_FIELDS_PER_TILE)
                          for p in probs) * TC_MMA_FLOPS_PER_FIELD
-            peak = float(measured_peaks().get("bf16_tflops_sustained", 1366.3))
+            peak, basis = tensor_peak(measured_peaks(), entry["clocks"])
             ach = issued / (statistics.mean(ms) / 1e3) / 1e12
+            uf = useful / (statistics.mean(ms) / 1e3) / 1e12
             entry["roofline"] = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                                 "frac": ach / peak, "useful_tflops": useful / (statistics.mean(ms) / 1e3) / 1e12,
+                                 "frac": ach / peak, "useful_tflops": uf, "useful_frac": uf / peak,
+                                 "peak_basis": basis,
                                  "kernel": "rollout_tc_batch_kernel (time of the whole batched update)"}
         forms[form] = entry
         batch.close()
@@ -550,11 +664,13 @@ def run_serving(args):
         lat = (rec["t_result_ns"] - rec["t_submit_ns"]) / 1e6
         queue = (rec["t_launch_ns"] - rec["t_submit_ns"]) / 1e6
         useful = steps * 12 * L * FLOPS_PER_FIELD
+        clk = clocks.summary()
         if args.precision == "tc":
             issued = steps * 12 * L_pad * TC_MMA_FLOPS_PER_FIELD
-            peak = float(measured_peaks().get("bf16_tflops_sustained", 1366.3))
+            peak, basis = tensor_peak(measured_peaks(), clk)
             roof = {"bound": "tensor", "achieved": issued / span / 1e12, "peak": peak, "unit": "TFLOP/s",
                     "frac": issued / span / 1e12 / peak, "useful_tflops": useful / span / 1e12,
+                    "useful_frac": useful / span / 1e12 / peak, "peak_basis": basis,
                     "kernel": "rollout_tc_batch_kernel (issued MMA flops over the whole serving span)"}
         else:
             peak = torch.cuda.get_device_properties(0).multi_processor_count * FP32_LANES_PER_SM * 2 * \
@@ -570,7 +686,7 @@ def run_serving(args):
                 "queue_ms": {"p50": float(np.percentile(queue, 50)), "p99": float(np.percentile(queue, 99))},
                 "group_size": {"mean": float(rec["group_size"].mean()), "max": int(rec["group_size"].max())},
                 "gpu_launches": int(st1["launches"] - st0["launches"]), "groups": int(st1["groups"] - st0["groups"]),
-                "pool_peak_bytes": int(st1["pool_peak_bytes"]), "roofline": roof, "clocks": clocks.summary(),
+                "pool_peak_bytes": int(st1["pool_peak_bytes"]), "roofline": roof, "clocks": clk,
                 "all_ok": bool(np.all(rec["status"] == 0))}
 
     full = run(50.0, args.serve_seconds, seed=1)
@@ -688,17 +804,28 @@ def run_ours(args):
         return
 
     peaks = measured_peaks()
-    roofline = form_roofline(args.precision, rollout_ms, K, T, M, L, dev, peaks, args.workload)
+    clk = clocks.summary()
+    roofline = form_roofline(args.precision, rollout_ms, K, T, M, L, dev, peaks, args.workload, clocks=clk)
     rates = pipe_peaks(local)   # measured pipe rates: context beside the unit-count FP32 peak
     roofline["rollout_share_of_step"] = sum(rollout_ms) / sum(step_ms)
     roofline["secondary"] = mufu_check(args.precision, rollout_ms, K, T, M, L, local)
     reduction = reduction_rooflines(scan_ms, merge_ms, K, T, peaks, local)
     reduction["plant_step"] = plant_step_roofline(plant_ms, L, peaks, args.precision)
     forms = {args.precision: {"value": value, "ms_per_update": 1e3 * total_s / args.steps,
-                              "roofline": roofline, "reduction": reduction}}
+                              "roofline": roofline, "reduction": reduction, "clocks": clk}}
     if not args.no_compare:
         other = "tc" if args.precision == "fp32" else "fp32"
         forms[other] = time_form(other, p, args, dev)
+    # the precision workload (K=65536, T=100, L=2048, conditioned D) in both forms, beside the headline
+    prec = None
+    if ws == 1 and args.workload == "realtime" and not args.no_precision:
+        from paper_1503_00330_b300 import workloads as W
+        pp = W.precision(0)
+        prec = {"config": {"workload": "precision: K=65536 rollouts, T=100 steps, L=2048 fields x 12 outputs, "
+                                       "cond(D_j) log-uniform in [1, 1e3], 16 obstacles; plain pi_update calls",
+                           "K": pp.K, "T": pp.T, "L": pp.model.L, "M": pp.M,
+                           "l2": "flushed between timed updates (256 MiB write outside the event window)"},
+                "forms": {f: time_updates(f, pp, args.precision_steps, 3, dev, "precision") for f in ("fp32", "tc")}}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
@@ -720,9 +847,21 @@ def run_ours(args):
                                             "the FP32 roofline keeps the unit-count peak"},
             "forms": forms,
             "paper_context": PAPER_CONTEXT,
-            "clocks": clocks.summary()}
+            "clocks": clk}
     if ws == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(p, args.cpu_sample)
+        base, ref = cpu_baseline(p, args.cpu_sample)
+        line["cpu_baseline"] = base
+        for f in forms:
+            forms[f]["error"] = {**form_errors(p, f, ref, dev), "tolerance_u_out": ERROR_BOUND[f],
+                                 "tolerance_costs": ERROR_BOUND[f]}
+        if prec is not None:
+            pbase, pref = cpu_baseline(pp, args.precision_sample, k_single=8)
+            prec["cpu_baseline"] = pbase
+            for f in prec["forms"]:
+                prec["forms"][f]["error"] = {**form_errors(pp, f, pref, dev), "tolerance_u_out": ERROR_BOUND[f],
+                                             "tolerance_costs": ERROR_BOUND[f]}
+    if prec is not None:
+        line["precision_workload"] = prec
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
@@ -736,7 +875,13 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=["realtime", "realtime_short", "small", "precision", "precision_short", "batched",
                                                    "serving", "subrollouts"], default="realtime")
-    ap.add_argument("--cpu-sample", type=int, default=256, help="rollouts in the CPU-baseline sample")
+    ap.add_argument("--cpu-sample", type=int, default=2048,
+                    help="rollouts in the CPU-baseline sample (also the error reference of each form)")
+    ap.add_argument("--precision-sample", type=int, default=512,
+                    help="rollouts in the precision workload's CPU-baseline / error-reference sample")
+    ap.add_argument("--precision-steps", type=int, default=3,
+                    help="timed updates of the precision workload (default line only)")
+    ap.add_argument("--no-precision", action="store_true", help="skip the precision workload in the default line")
     ap.add_argument("--ref-sample", type=int, default=64, help="rollouts per reference-arm step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", choices=["fp32", "tc"], default="fp32",

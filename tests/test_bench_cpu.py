@@ -43,3 +43,14 @@ def test_plant_step_roofline_counts_one_read_of_the_records():
     assert abs(r["frac"] - r["achieved"] / 6000.0) < 1e-12
     assert r["bound"] == "hbm" and r["launches_per_step"] == 3
     assert bench.plant_step_roofline([0.01], 513, {}, "fp32")["bytes_per_launch"] == 12 * 257 * 1376
+
+
+def test_tensor_peak_follows_the_clock_record():
+    """The tensor roofline divides by the measured burst bf16 rate unless the run's
+    clock record shows the power cap, where the seconds-long sustained rate applies."""
+    sys.path.insert(0, ROOT)
+    import bench
+    peaks = {"bf16_tflops": 1788.7, "bf16_tflops_sustained": 1393.1}
+    assert bench.tensor_peak(peaks, {"reasons": []})[0] == 1788.7
+    assert bench.tensor_peak(peaks, {"reasons": ["sw_power_cap"]})[0] == 1393.1
+    assert bench.tensor_peak(peaks, None)[0] == 1788.7
