@@ -23,9 +23,9 @@
 // Roles (one CTA per SM, 128 slots, 320 threads):
 //   warp 0:        producer (one elected lane issues) -- 1-D bulk copies
 //                  (TMA) of the pre-packed coefficient chunks (8 KB each,
-//                  11 per tile of 128 fields) in groups of CPG chunks (one
-//                  copy per contiguous run, one barrier pair per group) into
-//                  a ring of NSLOT chunk slots, and of the per-field
+//                  11 per tile of 128 fields) in two groups per tile
+//                  (chunks 0-5 and 6-10, one copy and one barrier pair each)
+//                  into a ring that holds one tile, and of the per-field
 //                  constants (cy, sigma^2) into a 4-deep constant ring;
 //   warp 1:        MMA issuer (the whole warp runs the loop, one elected
 //                  lane issues) -- per tile of 128 fields, 30 MMAs (M=128,
@@ -61,10 +61,15 @@ constexpr int BM = TC_SLOTS;            // rollout slots per CTA (MMA M)
 constexpr int TNF = TC_TILE_FIELDS;     // fields per tile (MMA N)
 constexpr int KF = TC_KF;               // feature columns of phi (S GEMM K)
 constexpr int NCH = TC_CHUNKS_PER_TILE; // chunks per tile
-constexpr int NSLOT = 12;               // chunk slots in the ring
-constexpr int CPG = 6;                  // chunks per copy group (one bulk copy per contiguous run, one barrier pair)
-constexpr int NGRP = NSLOT / CPG;       // groups in the ring
-static_assert(NSLOT % CPG == 0, "the ring holds whole groups");
+// The chunk ring holds one tile: copy group A = chunks 0..GA-1 in slots
+// 0..GA-1, group B = the rest; each group is one bulk copy and one full/empty
+// barrier pair, so every slot, descriptor offset and barrier of the MMA
+// issuer's per-tile sequence is a compile-time constant.
+constexpr int NSLOT = NCH;              // chunk slots in the ring (one tile)
+constexpr int GA = 6;                   // chunks of copy group A (the N = 256 pair and K steps 1-4)
+constexpr int GB = NCH - GA;            // chunks of copy group B (K steps 5-9)
+constexpr int NGRP = 2;
+static_assert(GA >= 2 && GB >= 1, "group A holds the N = 256 chunk pair");
 constexpr int NCONST = 4;
 constexpr int NEPI = 8;                 // epilogue warps
 constexpr int NTHREADS = (2 + NEPI) * 32;
@@ -88,8 +93,8 @@ constexpr int OFF_Q = OFF_YREF + NY * BM * 4;                   // [BM]
 constexpr int OFF_OBS = OFF_Q + BM * 4;
 constexpr int OFF_BAR = OFF_OBS + MAX_OBS * 8;
 // barriers: full[NGRP], empty[NGRP], acc_full[2], acc_empty[2],
-//           const_full[4], const_empty[4], phi_ready, xfull, xfree
-constexpr int NBARS = 2 * NGRP + 4 + 2 * NCONST + 3;
+//           const_full[4], const_empty[4], phi_ready, xfull, xfree, drain
+constexpr int NBARS = 2 * NGRP + 4 + 2 * NCONST + 4;
 constexpr int OFF_TSLOT = OFF_BAR + NBARS * 8;
 constexpr int OFF_ABORT = OFF_TSLOT + 8;
 constexpr int SMEM_BYTES = OFF_ABORT + 16;
@@ -218,6 +223,7 @@ struct TcSmem {
     float2 *obs_s;
     uint64_t *full, *empty, *acc_full, *acc_empty, *const_full, *const_empty, *phi_ready;
     uint64_t *xfull, *xfree;   // output exchange between the CTAs of a cluster (split form)
+    uint64_t *drain;           // the issuer's last commit after a timeout
     uint32_t *tslot;
     volatile int *abort_flag;
 };
@@ -244,6 +250,7 @@ __device__ __forceinline__ TcSmem tc_smem(unsigned char *smem)
     S.phi_ready = S.const_empty + NCONST;
     S.xfull = S.phi_ready + 1;
     S.xfree = S.phi_ready + 2;
+    S.drain = S.phi_ready + 3;
     S.tslot = reinterpret_cast<uint32_t *>(smem + OFF_TSLOT);
     S.abort_flag = reinterpret_cast<volatile int *>(smem + OFF_ABORT);
     return S;
@@ -276,31 +283,31 @@ __device__ __forceinline__ void tc_setup(const TcSmem &S, uint32_t ncl)
         const uint32_t xc = ncl > 1 ? (ncl - 1) * BM : 1;
         mbar_init(S.xfull, xc);
         mbar_init(S.xfree, xc);
+        mbar_init(S.drain, 1);
         *S.abort_flag = 0;
         fence_mbar_init();
     }
 }
 
-// Persistent per-role positions in the rings (carried across work items):
-// g counts tiles (constant ring), grp counts chunk groups (coefficient ring).
+// Persistent per-role positions (carried across work items): g counts the
+// tiles whose copies (producer) or MMAs (issuer) have been issued; ts counts
+// the issuer's steps (feature tiles).  The tile counter fixes every ring
+// position and barrier phase: tile g uses constant slot g & 3, chunk groups
+// A and B at phase g & 1, accumulator buffer g & 1.
 struct TcProducer {
-    long long g = 0, grp = 0, issued_tiles = 0;
+    long long g = 0, na = 0, nb = 0;   // tiles started; A and B groups issued
 };
 struct TcIssuer {
-    long long g = 0, grp = 0, grp_committed = -1, ts = 0;
+    long long g = 0, ts = 0;
+    bool drained = false;   // committed to the drain barrier after a timeout
 };
 
 // Producer (all of warp 0; one elected lane issues the copies) for one work
-// item -- the tiles of outputs o_begin .. o_begin + n_out - 1 -- ; false
-// after a timeout.
-//
-// The coefficient chunks of a step are one contiguous run of global memory
-// (tiles of consecutive outputs are adjacent), and a bulk copy costs about the
-// same whatever its size up to tens of KB, so chunks travel in groups of CPG:
-// one copy per contiguous run (two when a step boundary falls inside the
-// group), one full/empty barrier pair per group.  Groups never straddle work
-// items.  A tile's constants are issued before the group holding its first
-// chunk.
+// item -- the tiles of outputs o_begin .. o_begin + n_out - 1, every step --;
+// false after a timeout.  Per tile: its constants into the 4-deep constant
+// ring, then copy group A (chunks 0..GA-1, one bulk copy) once the MMAs of the
+// previous tile's group A are done, then group B likewise.  A tile's chunks
+// are contiguous in global memory, so each group is one copy.
 template <bool PREDICT>
 __device__ bool tc_producer_item(const TcArgs &a, const TcSmem &S, TcProducer &P, int o_begin, int n_out)
 {
@@ -310,22 +317,17 @@ __device__ bool tc_producer_item(const TcArgs &a, const TcSmem &S, TcProducer &P
     const int G = n_out * a.tiles_per_out;
     const long long tile0 = (long long)o_begin * a.tiles_per_out;
     const int nsteps = PREDICT ? 2 : a.T;
-    const long long step_chunks = (long long)G * NCH;
-    const long long nchunk = step_chunks * nsteps;
-    const unsigned char *step_src = a.wtiles + tile0 * TC_TILE_BYTES;   // chunk i of a step at + i * 8 KB
     bool ok = true;
-    long long next_tile = 0;   // item-local tiles whose constants are issued
-    for (long long c0 = 0; c0 < nchunk && ok; c0 += CPG) {
-        const int n = (int)(nchunk - c0 < CPG ? nchunk - c0 : CPG);
-        const long long last_tile = (c0 + n - 1) / NCH;
-        for (; next_tile <= last_tile; ++next_tile) {
+    for (int t = 0; t < nsteps && ok; ++t) {
+        for (int jt = 0; jt < G; ++jt) {
             const long long gt = P.g;
+            const long long tile = tile0 + jt;
+            const unsigned char *src = a.wtiles + tile * TC_TILE_BYTES;
             const int c = (int)(gt & 3);
             if (gt >= 4)
                 ok = __all_sync(0xffffffffu,
                                 mbar_wait_bounded(&const_empty[c], (uint32_t)(((gt >> 2) - 1) & 1), abort_flag));
             if (!ok) break;
-            const long long tile = tile0 + next_tile % G;
             if (elect_one()) {
                 mbar_arrive_expect_tx(&const_full[c], TC_CONST_BYTES);
                 bulk_g2s(smem + OFF_CONST + c * TC_CONST_BYTES, a.wconst + tile * TC_CONST_BYTES, TC_CONST_BYTES,
@@ -333,41 +335,58 @@ __device__ bool tc_producer_item(const TcArgs &a, const TcSmem &S, TcProducer &P
             }
             __syncwarp();
             P.g = gt + 1;
-            P.issued_tiles = P.g;
+            const uint32_t prev = (uint32_t)((gt - 1) & 1);   // phase of the previous tile's groups
+            if (gt >= 1) ok = __all_sync(0xffffffffu, mbar_wait_bounded(&empty[0], prev, abort_flag));
+            if (!ok) break;
+            if (elect_one()) {
+                mbar_arrive_expect_tx(&full[0], (uint32_t)(GA * TC_CHUNK_BYTES));
+                bulk_g2s(smem + OFF_RING, src, (uint32_t)(GA * TC_CHUNK_BYTES), &full[0]);
+            }
+            __syncwarp();
+            P.na = gt + 1;
+            if (gt >= 1) ok = __all_sync(0xffffffffu, mbar_wait_bounded(&empty[1], prev, abort_flag));
+            if (!ok) break;
+            if (elect_one()) {
+                mbar_arrive_expect_tx(&full[1], (uint32_t)(GB * TC_CHUNK_BYTES));
+                bulk_g2s(smem + OFF_RING + GA * TC_CHUNK_BYTES, src + GA * TC_CHUNK_BYTES,
+                         (uint32_t)(GB * TC_CHUNK_BYTES), &full[1]);
+            }
+            __syncwarp();
+            P.nb = gt + 1;
         }
-        if (!ok) break;
-        const long long grp = P.grp;
-        const int gs = (int)(grp % NGRP);
-        if (grp >= NGRP)
-            ok = __all_sync(0xffffffffu,
-                            mbar_wait_bounded(&empty[gs], (uint32_t)(((grp / NGRP) - 1) & 1), abort_flag));
-        if (!ok) break;
-        unsigned char *dst = smem + OFF_RING + gs * CPG * TC_CHUNK_BYTES;
-        const long long i0 = c0 % step_chunks;
-        const int n1 = (int)(step_chunks - i0 < n ? step_chunks - i0 : n);
-        if (elect_one()) {
-            mbar_arrive_expect_tx(&full[gs], (uint32_t)(n * TC_CHUNK_BYTES));
-            bulk_g2s(dst, step_src + i0 * TC_CHUNK_BYTES, (uint32_t)(n1 * TC_CHUNK_BYTES), &full[gs]);
-            if (n1 < n)
-                bulk_g2s(dst + n1 * TC_CHUNK_BYTES, step_src, (uint32_t)((n - n1) * TC_CHUNK_BYTES), &full[gs]);
-        }
-        __syncwarp();
-        P.grp = grp + 1;
     }
     return ok;
 }
 
-// MMA issuer (all of warp 1) for one work item; false after a timeout.
-// The whole warp runs the loop, so every counter and descriptor is
-// warp-uniform, and the lane elect.sync picks issues the MMAs and commits.  (A
-// lone lane of a diverged warp issued them about 1.4x slower whenever the
-// epilogue warps sharing its sub-partition were busy.)  Per tile: chunks 0
-// and 1 feed one N = 256 MMA triple (K step 0 of S into accumulator columns
-// 0-127 and the Y GEMM into 128-255), chunks 2..10 one N = 128 triple each
-// (K steps 1..9 of S) -- 30 MMAs.  Waits once per chunk group and releases
-// the group's slots with one commit after the MMAs that read it (a group
-// ending at chunk 0 is released after the triple issued at chunk 1); the
-// group's chunk c sits in ring slot group * CPG + c.
+// The MMAs of chunks J..J1-1 of a tile (all in the ring slots of the same
+// index): chunk 1 issues the N = 256 triple of K step 0 of S (columns 0-127)
+// and the Y GEMM (128-255), whose B operand is chunks 0 and 1 (hi and lo,
+// 256 rows each); chunk j >= 2 issues the N = 128 triple of K step j - 1.
+template <int J, int J1>
+__device__ __forceinline__ void tc_issue_chunks(uint32_t dS, uint64_t a_hi, uint64_t a_lo, uint64_t b0,
+                                                uint32_t idesc, uint32_t idesc_wide)
+{
+    if constexpr (J < J1) {
+        constexpr uint64_t CH = TC_CHUNK_BYTES >> 4;
+        if constexpr (J == 1) {
+            mma3_elect(dS, a_hi, a_lo, b0, b0 + CH, idesc_wide, 0u);
+        } else if constexpr (J >= 2) {
+            constexpr uint64_t ka = (uint64_t)((J - 1) * 16);
+            mma3_elect(dS, a_hi + ka, a_lo + ka, b0 + J * CH, b0 + J * CH + (uint64_t)(TC_HALF_CHUNK >> 4), idesc,
+                       1u);
+        }
+        tc_issue_chunks<J + 1, J1>(dS, a_hi, a_lo, b0, idesc, idesc_wide);
+    }
+}
+
+// MMA issuer (all of warp 1) for one work item; false after a timeout.  The
+// whole warp runs the loop, so every counter and descriptor is warp-uniform,
+// and the lane elect.sync picks issues the MMAs and commits.  (The issuing
+// warp shares its scheduler with two epilogue warps, so every instruction of
+// this loop costs issue slots on the critical path: the per-tile sequence
+// below has no per-chunk bookkeeping.)  Per tile: wait for group A, its 18
+// MMAs (the N = 256 triple and K steps 1-4), release A; wait for group B, its
+// 15 MMAs (K steps 5-9), release B; signal the accumulator.
 template <bool PREDICT>
 __device__ bool tc_issuer_item(const TcArgs &a, const TcSmem &S, uint32_t tbase, TcIssuer &I, int n_out)
 {
@@ -377,86 +396,47 @@ __device__ bool tc_issuer_item(const TcArgs &a, const TcSmem &S, uint32_t tbase,
     volatile int *abort_flag = S.abort_flag;
     const int G = n_out * a.tiles_per_out;
     const int nsteps = PREDICT ? 2 : a.T;
-    const long long nchunk = (long long)G * nsteps * NCH;
-    long long &g = I.g, &ts = I.ts;
     const uint32_t idesc = idesc_f16_f32(BM, TNF), idesc_wide = idesc_f16_f32(BM, 2 * TNF);
     // descriptors: A = feature tile K step j (rows 2560 B apart; step j at
     // +256 B), B = a chunk half (128 rows x 16 K, rows 256 B apart; 256 rows
-    // for the whole first two chunks); step, slot and half offsets are added
-    // to the 14-bit start field (>> 4; the addresses stay < 256 KB).
+    // for the whole first two chunks); chunk and half offsets are added to the
+    // 14-bit start field (>> 4; the addresses stay < 256 KB).
     const uint64_t a_hi = smem_desc_kmajor(smem_u32(smem + OFF_PHI_HI), 128, 16 * KF);
     const uint64_t a_lo = smem_desc_kmajor(smem_u32(smem + OFF_PHI_LO), 128, 16 * KF);
     const uint64_t b0 = smem_desc_kmajor(smem_u32(smem + OFF_RING), 128, 256);
-    // group state: counter, ring group, its phase, chunk within it
-    long long grp = I.grp;
-    uint32_t gs = (uint32_t)(grp % NGRP), gph = (uint32_t)((grp / NGRP) & 1);
-    int cg = 0;
-    long long ci = 0;   // chunks of this item consumed
+    long long g = I.g;
     bool ok = true;
-    for (int t = 0; t < nsteps && ok; ++t, ++ts) {
-        ok = __all_sync(0xffffffffu, mbar_wait_bounded(phi_ready, (uint32_t)(ts & 1), abort_flag));
+    for (int t = 0; t < nsteps && ok; ++t) {
+        ok = __all_sync(0xffffffffu, mbar_wait_bounded(phi_ready, (uint32_t)(I.ts & 1), abort_flag));
+        ++I.ts;
         tc_fence_after();
         for (int jt = 0; jt < G && ok; ++jt, ++g) {
             const int buf = (int)(g & 1);
+            const uint32_t ph = (uint32_t)(g & 1);
             if (g >= 2)
                 ok = __all_sync(0xffffffffu,
                                 mbar_wait_bounded(&acc_empty[buf], (uint32_t)(((g >> 1) - 1) & 1), abort_flag));
+            if (ok) ok = __all_sync(0xffffffffu, mbar_wait_bounded(&full[0], ph, abort_flag));
             if (!ok) break;
             tc_fence_after();
             const uint32_t dS = tbase + buf * 256;   // S: columns 0-127, Y: 128-255
-#pragma unroll
-            for (int j = 0; j < NCH; ++j) {
-                if (cg == 0 && ok) {
-                    ok = __all_sync(0xffffffffu, mbar_wait_bounded(&full[gs], gph, abort_flag));
-                    tc_fence_after();
-                }
-                if (ok && j > 0) {
-                    const uint32_t slot = gs * CPG + cg;
-                    const uint64_t bc = b0 + (uint64_t)(slot * (TC_CHUNK_BYTES >> 4));
-                    if (j == 1) {
-                        // chunk 0 sits in the ring slot before this one (the last
-                        // slot of the previous group when this chunk opens a group)
-                        const uint32_t pslot = cg > 0 ? slot - 1 : (gs == 0 ? NGRP : gs) * CPG - 1;
-                        const uint64_t bp = b0 + (uint64_t)(pslot * (TC_CHUNK_BYTES >> 4));
-                        mma3_elect(dS, a_hi, a_lo, bp, bc, idesc_wide, 0u);
-                        if (cg == 0) {
-                            // chunk 0 closed the previous group: release it now
-                            const uint32_t pg = gs == 0 ? NGRP - 1 : gs - 1;
-                            commit_elect(&empty[pg]);
-                            I.grp_committed = grp - 1;
-                        }
-                    } else {
-                        mma3_elect(dS, a_hi + (uint64_t)((j - 1) * 16), a_lo + (uint64_t)((j - 1) * 16), bc,
-                                   bc + (uint64_t)(TC_HALF_CHUNK >> 4), idesc, 1u);
-                    }
-                }
-                ++ci;
-                if (++cg == CPG || ci == nchunk) {
-                    // chunk 0 is read by the MMAs issued at chunk 1: a group it
-                    // closes is released there
-                    if (ok && j > 0) {
-                        commit_elect(&empty[gs]);
-                        I.grp_committed = grp;
-                    }
-                    cg = 0;
-                    ++grp;
-                    if (++gs == NGRP) {
-                        gs = 0;
-                        gph ^= 1;
-                    }
-                }
-            }
-            if (ok) commit_elect(&acc_full[buf]);
+            tc_issue_chunks<1, GA>(dS, a_hi, a_lo, b0, idesc, idesc_wide);
+            commit_elect(&empty[0]);
+            ok = __all_sync(0xffffffffu, mbar_wait_bounded(&full[1], ph, abort_flag));
+            if (!ok) break;
+            tc_fence_after();
+            tc_issue_chunks<GA, NCH>(dS, a_hi, a_lo, b0, idesc, idesc_wide);
+            commit_elect(&empty[1]);
+            commit_elect(&acc_full[buf]);
         }
     }
-    // after a timeout, one more commit (on the current group's barrier, whose
-    // phase nothing else completes) covers every MMA issued; the drain waits
-    // for it
+    // after a timeout, one commit on the drain barrier (which nothing else
+    // completes) covers every MMA issued; the drain waits for it
     if (!ok) {
-        commit_elect(&empty[gs]);
-        I.grp_committed = grp;
+        commit_elect(S.drain);
+        I.drained = true;
     }
-    I.grp = grp;
+    I.g = g;
     return ok;
 }
 
@@ -706,23 +686,21 @@ __device__ __forceinline__ void tc_drain(const TcArgs &a, const TcSmem &S, const
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (warp == 0 && lane == 0) {
-        // keep the CTA alive until every copy issued has landed
-        for (long long r = (P.grp > NGRP ? P.grp - NGRP : 0); r < P.grp; ++r)
-            if (!mbar_wait_drain(&S.full[r % NGRP], (uint32_t)((r / NGRP) & 1))) atomicOr(a.err, DEVERR_TIMEOUT_DRAIN);
-        for (long long g = (P.issued_tiles > NCONST ? P.issued_tiles - NCONST : 0); g < P.issued_tiles; ++g)
+        // keep the CTA alive until every copy issued has landed: the last
+        // phase of each group barrier, and of the last constant slots
+        if (P.na > 0 && !mbar_wait_drain(&S.full[0], (uint32_t)((P.na - 1) & 1))) atomicOr(a.err, DEVERR_TIMEOUT_DRAIN);
+        if (P.nb > 0 && !mbar_wait_drain(&S.full[1], (uint32_t)((P.nb - 1) & 1))) atomicOr(a.err, DEVERR_TIMEOUT_DRAIN);
+        for (long long g = (P.g > NCONST ? P.g - NCONST : 0); g < P.g; ++g)
             if (!mbar_wait_drain(&S.const_full[g & 3], (uint32_t)((g >> 2) & 1))) atomicOr(a.err, DEVERR_TIMEOUT_DRAIN);
     }
     if (warp == 1 && lane == 0) {
         // every MMA issued must complete before the tensor memory is freed:
         // normally the last tile's accumulator commit covers them all, after a
-        // timeout the issuer's final group commit does
+        // timeout the issuer's commit on the drain barrier does
         if (issuer_ok && I.g > 0 &&
             !mbar_wait_drain(&S.acc_full[(I.g - 1) & 1], (uint32_t)(((I.g - 1) >> 1) & 1)))
             atomicOr(a.err, DEVERR_TIMEOUT_DRAIN);
-        if (!issuer_ok && I.grp_committed >= 0) {
-            const long long r = I.grp_committed;
-            if (!mbar_wait_drain(&S.empty[r % NGRP], (uint32_t)((r / NGRP) & 1))) atomicOr(a.err, DEVERR_TIMEOUT_DRAIN);
-        }
+        if (I.drained && !mbar_wait_drain(S.drain, 0u)) atomicOr(a.err, DEVERR_TIMEOUT_DRAIN);
     }
 }
 
