@@ -291,15 +291,19 @@ TC_MMA_FLOPS_PER_FIELD = 3 * 2 * (160 + 16)   # hi*hi + hi*lo + lo*hi over K=160
 
 
 def tensor_peak(peaks, clocks):
-    """Dense bf16 tensor peak for a run with the given clock record: the burst figure when
-    the run was not held at the power cap (the kernel ran at full clock, as the burst GEMM
-    did), the seconds-long sustained figure when the record shows sw_power_cap."""
-    capped = clocks is not None and "sw_power_cap" in (clocks.get("reasons") or [])
-    if capped:
+    """Dense bf16 tensor peak for a run with the given clock record: the seconds-long
+    sustained figure when the run was held down by the power cap (sw_power_cap active and
+    the median SM clock under load below 95 % of the maximum, as in the sustained GEMM
+    loop), else the burst figure (the kernel ran at full clock, as the burst GEMM did)."""
+    clocks = clocks or {}
+    capped = "sw_power_cap" in (clocks.get("reasons") or [])
+    mhz, mx = clocks.get("sm_mhz"), clocks.get("sm_max_mhz")
+    held = capped and mhz is not None and mx and float(mhz) < 0.95 * float(mx)
+    if held:
         return float(peaks.get("bf16_tflops_sustained", 1366.3)), \
-            "measured dense bf16 sustained (the run's clock record shows sw_power_cap)"
-    return float(peaks.get("bf16_tflops", 1788.7)), \
-        "measured dense bf16 burst (no power cap in the run's clock record)"
+            f"measured dense bf16 sustained (sw_power_cap, median SM clock {float(mhz):.0f} MHz under load)"
+    note = "no power cap" if not capped else f"sw_power_cap flagged, median SM clock {float(mhz):.0f} MHz"
+    return float(peaks.get("bf16_tflops", 1788.7)), f"measured dense bf16 burst ({note} in the run's clock record)"
 
 
 def form_roofline(precision, rollout_ms, K, T, M, L, dev, peaks, workload, clocks=None):

@@ -47,10 +47,15 @@ def test_plant_step_roofline_counts_one_read_of_the_records():
 
 def test_tensor_peak_follows_the_clock_record():
     """The tensor roofline divides by the measured burst bf16 rate unless the run's
-    clock record shows the power cap, where the seconds-long sustained rate applies."""
+    clock record shows it held down by the power cap (sw_power_cap and a median SM
+    clock below 95 % of the maximum), where the seconds-long sustained rate applies."""
     sys.path.insert(0, ROOT)
     import bench
     peaks = {"bf16_tflops": 1788.7, "bf16_tflops_sustained": 1393.1}
-    assert bench.tensor_peak(peaks, {"reasons": []})[0] == 1788.7
-    assert bench.tensor_peak(peaks, {"reasons": ["sw_power_cap"]})[0] == 1393.1
+    assert bench.tensor_peak(peaks, {"reasons": [], "sm_mhz": 2032.0, "sm_max_mhz": 2032.0})[0] == 1788.7
+    capped = {"reasons": ["sw_power_cap"], "sm_mhz": 1432.0, "sm_max_mhz": 2032.0}
+    assert bench.tensor_peak(peaks, capped)[0] == 1393.1
+    # the cap flagged in a few samples while the clock stayed at its maximum: burst
+    flagged = {"reasons": ["sw_power_cap"], "sm_mhz": 2021.0, "sm_max_mhz": 2032.0}
+    assert bench.tensor_peak(peaks, flagged)[0] == 1788.7
     assert bench.tensor_peak(peaks, None)[0] == 1788.7
