@@ -285,9 +285,14 @@ def run_reference(args):
 
 
 # Stated accuracy of each form against the FP64 oracle (u_out per channel and costs, relative)
-ERROR_BOUND = {"fp32": 1e-5, "tc": 2e-3}
+ERROR_BOUND = {"fp32": 1e-5, "tc": 2e-3, "tc_fp16x2": 2e-3}
+FORMS = ("fp32", "tc", "tc_fp16x2")
 TC_FIELDS_PER_TILE = 128                      # fields per tensor-core tile (MMA N)
-TC_MMA_FLOPS_PER_FIELD = 3 * 2 * (160 + 16)   # hi*hi + hi*lo + lo*hi over K=160 (S) and K=16 (Y)
+# Issued MMA flops per field (2 per multiply-add): K step 0 of the exponent GEMM and the K=16
+# prediction GEMM with 3 split products; the 128 quadratic features (K steps 1-8) with 3
+# (tc) or 2 (tc_fp16x2); K step 9 (8 quadratic features, the constant, padding) with 3.
+TC_MMA_FLOPS_PER_FIELD = {"tc": 2 * (3 * (16 + 16) + 3 * 128 + 3 * 16),
+                          "tc_fp16x2": 2 * (3 * (16 + 16) + 2 * 128 + 3 * 16)}
 
 
 def tensor_peak(peaks, clocks):
@@ -322,13 +327,15 @@ def form_roofline(precision, rollout_ms, K, T, M, L, dev, peaks, workload, clock
                               f"x {sm_max_mhz:.0f} MHz (max SM clock)",
                 "rollout_ms_per_launch": statistics.mean(rollout_ms)}
     L_pad = -(-L // TC_FIELDS_PER_TILE) * TC_FIELDS_PER_TILE
-    issued = float(K) * T * M * 12 * L_pad * TC_MMA_FLOPS_PER_FIELD
+    per_field = TC_MMA_FLOPS_PER_FIELD[precision]
+    issued = float(K) * T * M * 12 * L_pad * per_field
     peak, basis = tensor_peak(peaks, clocks)
     achieved = issued / avg_s / 1e12
     return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": profile_traffic(f"rollout_tc_{workload}.md"), "kernel": "rollout_tc_kernel",
-            "peak_basis": basis + "; fp16 has the same nominal rate; achieved counts the issued fp16 MMA "
-                                  "flops (3 split products x 2 x 176 per field, fields padded to 128-field tiles)",
+            "traffic": profile_traffic(f"rollout_tc_{workload}.md") if precision == "tc" else None,
+            "kernel": "rollout_tc_kernel" + ("" if precision == "tc" else " (2 split products on the quadratic features)"),
+            "peak_basis": basis + f"; fp16 has the same nominal rate; achieved counts the issued fp16 MMA "
+                                  f"flops ({per_field} per field, fields padded to 128-field tiles)",
             "useful_tflops": useful / avg_s / 1e12, "useful_frac": useful / avg_s / 1e12 / peak,
             "useful_basis": f"{FLOPS_PER_FIELD} algorithmic flop per field evaluation (the FP32 form's count)",
             "rollout_ms_per_launch": statistics.mean(rollout_ms)}
@@ -546,7 +553,8 @@ def run_batched(args):
     dev = torch.device("cuda", 0)
     probs = W.batched(64, seed=0)
     # schedule per form from the autotuner (JSON-cached by batch shape), unless fixed on the command line
-    sched = {"fp32": ("longest_first", min(args.batch_tile, 1)), "tc": ("longest_first", args.batch_tile)}
+    sched = {"fp32": ("longest_first", min(args.batch_tile, 1)), "tc": ("longest_first", args.batch_tile),
+             "tc_fp16x2": ("longest_first", args.batch_tile)}
     tuned = None
     if args.batch_tile < 0:
         from paper_1503_00330_b300 import autotune
@@ -557,10 +565,11 @@ def run_batched(args):
             if f not in best or ms < best[f][2]:
                 best[f] = (o, int(t), ms)
         sched = {f: (o, t) for f, (o, t, _) in best.items()}
+        sched["tc_fp16x2"] = sched["tc"]      # the same kernel with fewer MMAs: the tensor-core pick
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
     forms = {}
-    order = [args.precision] + ([] if args.no_compare else [f for f in ("fp32", "tc") if f != args.precision])
+    order = [args.precision] + ([] if args.no_compare else [f for f in FORMS if f != args.precision])
     for form in order:
         ctls = [Controller(p.model, p.cost, M=p.M, model_noise=p.model_noise, precision=form) for p in probs]
         batch = Batch(ctls, [p.K for p in probs], [p.T for p in probs], precision=form,
@@ -597,7 +606,7 @@ def run_batched(args):
                                  "kernel": "rollout_fp32_batch_kernel (time of the whole batched update)"}
         else:
             issued = sum(p.K * p.T * p.M * 12 * (-(-p.model.L // TC_FIELDS_PER_TILE) * TC_FIELDS_PER_TILE)
-                         for p in probs) * TC_MMA_FLOPS_PER_FIELD
+                         for p in probs) * TC_MMA_FLOPS_PER_FIELD[form]
             peak, basis = tensor_peak(measured_peaks(), entry["clocks"])
             ach = issued / (statistics.mean(ms) / 1e3) / 1e12
             uf = useful / (statistics.mean(ms) / 1e3) / 1e12
@@ -669,8 +678,8 @@ def run_serving(args):
         queue = (rec["t_launch_ns"] - rec["t_submit_ns"]) / 1e6
         useful = steps * 12 * L * FLOPS_PER_FIELD
         clk = clocks.summary()
-        if args.precision == "tc":
-            issued = steps * 12 * L_pad * TC_MMA_FLOPS_PER_FIELD
+        if args.precision != "fp32":
+            issued = steps * 12 * L_pad * TC_MMA_FLOPS_PER_FIELD[args.precision]
             peak, basis = tensor_peak(measured_peaks(), clk)
             roof = {"bound": "tensor", "achieved": issued / span / 1e12, "peak": peak, "unit": "TFLOP/s",
                     "frac": issued / span / 1e12 / peak, "useful_tflops": useful / span / 1e12,
@@ -818,8 +827,9 @@ def run_ours(args):
     forms = {args.precision: {"value": value, "ms_per_update": 1e3 * total_s / args.steps,
                               "roofline": roofline, "reduction": reduction, "clocks": clk}}
     if not args.no_compare:
-        other = "tc" if args.precision == "fp32" else "fp32"
-        forms[other] = time_form(other, p, args, dev)
+        for other in FORMS:
+            if other != args.precision:
+                forms[other] = time_form(other, p, args, dev)
     # the precision workload (K=65536, T=100, L=2048, conditioned D) in both forms, beside the headline
     prec = None
     if ws == 1 and args.workload == "realtime" and not args.no_precision:
@@ -829,7 +839,7 @@ def run_ours(args):
                                        "cond(D_j) log-uniform in [1, 1e3], 16 obstacles; plain pi_update calls",
                            "K": pp.K, "T": pp.T, "L": pp.model.L, "M": pp.M,
                            "l2": "flushed between timed updates (256 MiB write outside the event window)"},
-                "forms": {f: time_updates(f, pp, args.precision_steps, 3, dev, "precision") for f in ("fp32", "tc")}}
+                "forms": {f: time_updates(f, pp, args.precision_steps, 3, dev, "precision") for f in FORMS}}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
@@ -888,7 +898,7 @@ def main():
     ap.add_argument("--no-precision", action="store_true", help="skip the precision workload in the default line")
     ap.add_argument("--ref-sample", type=int, default=64, help="rollouts per reference-arm step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--precision", choices=["fp32", "tc"], default="fp32",
+    ap.add_argument("--precision", choices=list(FORMS), default="fp32",
                     help="form of the headline line (the other form is timed too and reported under 'forms')")
     ap.add_argument("--no-compare", action="store_true", help="skip timing the other form")
     ap.add_argument("--batch-tile", type=int, default=-1,

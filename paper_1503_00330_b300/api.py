@@ -36,7 +36,7 @@ def _sigma4(sigma_u):
 class Controller:
     """One LWPR model + cost on one GPU (a ``pi_ctx``)."""
 
-    PRECISIONS = {"fp32": 0, "tc": 1}
+    PRECISIONS = {"fp32": 0, "tc": 1, "tc_fp16x2": 2}
 
     def __init__(self, model: LwprModel, cost: CostParams, M: int = 1, model_noise: bool = True,
                  device: int = 0, precision: str = "fp32"):

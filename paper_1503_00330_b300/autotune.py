@@ -87,7 +87,7 @@ def tune(problems, forms=("fp32", "tc"), orders=ORDERS, reps: int = 2, cache_pat
                       x0=[p.x0 for p in problems], u_nom=[p.u_nom for p in problems])
         for order in orders:
             batch.set_schedule(order)
-            for tile in (tc_tiles if form == "tc" else FP32_TILES):
+            for tile in (FP32_TILES if form == "fp32" else tc_tiles):
                 batch.set_tile(tile)
                 t0 = time.perf_counter()
                 ms = time_batch(batch, problems, reps=reps)

@@ -140,7 +140,7 @@ int launch_rollouts(pi_ctx *c, const float *x0, const float *u_nom, int K, int T
                     const float *sigma_u, uint64_t seed, float *cost, float4 *eps, float *phi)
 {
     NvtxRange nv("pi2rh rollout");
-    if (c->opts.precision == PI_PRECISION_TC_FP16X3) {
+    if (pi2rh_is_tc(c->opts.precision)) {
         TcArgs t = tc_args(c);
         t.K = K;
         t.T = T;
@@ -344,7 +344,7 @@ int pi_create(const pi_lwpr_params *lw, const pi_cost_params *cp, const pi_opts 
     if (!(lw->dt > 0.0f) || !std::isfinite(lw->dt)) return fail(PI_ERR_INVALID_ARG, "dt must be > 0");
     if (!lw->c || !lw->D || !lw->beta || !lw->b || !lw->sigma)
         return fail(PI_ERR_INVALID_ARG, "an LWPR array is NULL");
-    if (opts.precision != PI_PRECISION_FP32 && opts.precision != PI_PRECISION_TC_FP16X3)
+    if (opts.precision != PI_PRECISION_FP32 && !pi2rh_is_tc(opts.precision))
         return fail(PI_ERR_UNSUPPORTED, "precision %d is not available", opts.precision);
     if (opts.model_noise != PI_NOISE_SAMPLED && opts.model_noise != PI_NOISE_MEAN_ONLY)
         return fail(PI_ERR_INVALID_ARG, "model_noise must be 0 or 1");
@@ -425,7 +425,7 @@ int pi_create(const pi_lwpr_params *lw, const pi_cost_params *cp, const pi_opts 
         return bail(e, "obstacle copy");
     if ((e = cudaMalloc(&c->d_err, sizeof(int))) != cudaSuccess) return bail(e, "error word alloc");
     if ((e = cudaMemset(c->d_err, 0, sizeof(int))) != cudaSuccess) return bail(e, "error word clear");
-    if (opts.precision == PI_PRECISION_TC_FP16X3) {
+    if (pi2rh_is_tc(opts.precision)) {
         std::vector<unsigned char> wt;
         std::vector<float> wc;
         c->tiles_per_out = (L + TC_TILE_FIELDS - 1) / TC_TILE_FIELDS;
@@ -617,7 +617,7 @@ int pi_debug_lwpr(pi_ctx *c, const float *z, int n, float *y, float *var)
     if (n < 1 || !z || !y || !var) return fail(PI_ERR_INVALID_ARG, "bad argument");
     DeviceGuard dg(c->device);
     PI_CUDA(dg.err, "cudaSetDevice");
-    if (c->opts.precision == PI_PRECISION_TC_FP16X3) {
+    if (pi2rh_is_tc(c->opts.precision)) {
         TcArgs t = tc_args(c);
         t.M = 1;
         t.z_in = z;

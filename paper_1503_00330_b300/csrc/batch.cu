@@ -65,13 +65,13 @@ int bcuda(cudaError_t e, const char *what)
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
-int slots_per_block(int form) { return form == PI_PRECISION_TC_FP16X3 ? TC_SLOTS : RF_SLOTS; }
+int slots_per_block(int form) { return pi2rh_is_tc(form) ? TC_SLOTS : RF_SLOTS; }
 
 // Relative cost of one rollout block of controller i (stage or tile count per step x steps).
 double block_work(const pi_batch *b, int i)
 {
     const pi_ctx *c = b->items[i].ctx;
-    const double per_step = b->form == PI_PRECISION_TC_FP16X3 ? (double)c->tiles_per_out : (double)c->spo;
+    const double per_step = pi2rh_is_tc(b->form) ? (double)c->tiles_per_out : (double)c->spo;
     return per_step * b->items[i].T;
 }
 
@@ -114,8 +114,9 @@ int capture(pi_batch *b)
     B_TRY(bcuda(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeRelaxed), "begin capture"));
     cudaError_t e = cudaMemsetAsync(b->d_counter, 0, sizeof(int), b->stream);
     if (e == cudaSuccess) {
-        if (b->form == PI_PRECISION_TC_FP16X3) {
-            TcBatchArgs tb{static_cast<const TcArgs *>(b->d_args), b->d_ritems, b->n_ritems, b->d_counter};
+        if (pi2rh_is_tc(b->form)) {
+            TcBatchArgs tb{static_cast<const TcArgs *>(b->d_args), b->d_ritems, b->n_ritems, b->d_counter,
+                           pi2rh_tc_qprod(b->form)};
             e = b->split > 0 ? launch_rollout_tc_group(tb, b->split, b->stream)
                              : launch_rollout_tc_batch(tb, b->grid, b->stream);
         } else {
@@ -166,7 +167,7 @@ int pi_batch_create(const pi_batch_item *items, int n, int precision, pi_batch *
     if (!out) return bfail(PI_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (!items || n < 1) return bfail(PI_ERR_INVALID_ARG, "a batch needs at least one item");
-    if (precision != PI_PRECISION_FP32 && precision != PI_PRECISION_TC_FP16X3)
+    if (precision != PI_PRECISION_FP32 && !pi2rh_is_tc(precision))
         return bfail(PI_ERR_UNSUPPORTED, "unknown precision");
     const int dev = items[0].ctx ? items[0].ctx->device : 0;
     for (int i = 0; i < n; ++i) {
@@ -176,9 +177,9 @@ int pi_batch_create(const pi_batch_item *items, int n, int precision, pi_batch *
         if (it.K < 1 || it.T < 1 || (long long)it.K * it.ctx->opts.M > (1LL << 31) - 1)
             return bfail(PI_ERR_INVALID_ARG, "item " + std::to_string(i) + ": bad K or T");
         if (it.ctx->device != dev) return bfail(PI_ERR_INVALID_ARG, "all contexts must share one device");
-        if (precision == PI_PRECISION_TC_FP16X3 && !it.ctx->d_wtiles)
+        if (pi2rh_is_tc(precision) && (!it.ctx->d_wtiles || it.ctx->opts.precision != precision))
             return bfail(PI_ERR_INVALID_ARG, "item " + std::to_string(i) +
-                                                 ": tensor-core batch needs contexts created with PI_PRECISION_TC_FP16X3");
+                                                 ": a tensor-core batch needs contexts created with the batch's precision");
     }
     int prev = -1;
     cudaGetDevice(&prev);
@@ -249,7 +250,7 @@ int pi_batch_create(const pi_batch_item *items, int n, int precision, pi_batch *
     }
     b->n_sitems = (int)sitems.size();
     b->n_mitems = (int)mitems.size();
-    const size_t arg_bytes = precision == PI_PRECISION_TC_FP16X3 ? n * sizeof(TcArgs) : n * sizeof(RolloutArgs);
+    const size_t arg_bytes = pi2rh_is_tc(precision) ? n * sizeof(TcArgs) : n * sizeof(RolloutArgs);
     size_t max_ritems = 0;
     for (int i = 0; i < n; ++i)
         max_ritems += ((size_t)items[i].K * items[i].ctx->opts.M + RF_SLOTS - 1) / RF_SLOTS;
@@ -296,7 +297,7 @@ int pi_batch_set_tile(pi_batch *b, int split)
     if (!b) return bfail(PI_ERR_INVALID_ARG, "batch is NULL");
     if (split < 0 || split > 4)
         return bfail(PI_ERR_INVALID_ARG, "split must be 0..4");
-    if (split > 1 && b->form != PI_PRECISION_TC_FP16X3)
+    if (split > 1 && !pi2rh_is_tc(b->form))
         return bfail(PI_ERR_INVALID_ARG, "FP32 batches take tile shape 0 or 1 (outputs are not split)");
     int prev = -1;
     cudaGetDevice(&prev);
@@ -347,8 +348,8 @@ int pi_batch_update(pi_batch *b, const float *lambda, const float *sigma_u, cons
     // order after the caller's stream, refresh the tables, replay, order the caller after us
     if (!rc) rc = bcuda(cudaEventRecord(b->ev_in, b->user_stream), "event record");
     if (!rc) rc = bcuda(cudaStreamWaitEvent(b->stream, b->ev_in, 0), "stream wait");
-    const void *src = b->form == PI_PRECISION_TC_FP16X3 ? (const void *)b->h_targs.data() : (const void *)b->h_args.data();
-    const size_t bytes = b->form == PI_PRECISION_TC_FP16X3 ? b->n * sizeof(TcArgs) : b->n * sizeof(RolloutArgs);
+    const void *src = pi2rh_is_tc(b->form) ? (const void *)b->h_targs.data() : (const void *)b->h_args.data();
+    const size_t bytes = pi2rh_is_tc(b->form) ? b->n * sizeof(TcArgs) : b->n * sizeof(RolloutArgs);
     if (!rc) rc = bcuda(cudaMemcpyAsync(b->d_args, src, bytes, cudaMemcpyHostToDevice, b->stream), "upload arguments");
     if (!rc)
         rc = bcuda(cudaMemcpyAsync(b->d_rargs, b->h_rargs.data(), b->n * sizeof(ReduceArgs), cudaMemcpyHostToDevice,

@@ -118,7 +118,7 @@ extern "C" int pi_update_noalloc(pi_ctx *c, const float *x0, const float *u_nom,
         float *phi = reinterpret_cast<float *>(base + NA_PHI_OFF);
         double *part = reinterpret_cast<double *>(base + NA_PART_OFF);
 
-        const bool tc = c->opts.precision == PI_PRECISION_TC_FP16X3;
+        const bool tc = pi2rh_is_tc(c->opts.precision);
         if (c->timing) rc = na_cuda(cudaEventRecord(c->ev[0], c->stream), "event record");
         if (rc == PI_OK && tc) {
             TcArgs t = ctx_tc_args(c);

@@ -49,6 +49,15 @@ struct NvtxRange {
     NvtxRange &operator=(const NvtxRange &) = delete;
 };
 
+// True for the tensor-core precisions (one packed model, the tensor-core rollout kernel).
+inline bool pi2rh_is_tc(int precision)
+{
+    return precision == PI_PRECISION_TC_FP16X3 || precision == PI_PRECISION_TC_FP16X2;
+}
+
+// Split products on the quadratic-feature K steps of a tensor-core precision.
+inline int pi2rh_tc_qprod(int precision) { return precision == PI_PRECISION_TC_FP16X2 ? 2 : 3; }
+
 // Records msg as the calling thread's last error (pi_last_error) and returns code.
 int pi2rh_fail(int code, const char *msg);
 
@@ -78,5 +87,6 @@ inline pi2rh::TcArgs ctx_tc_args(const pi_ctx *c)
     t.M = c->opts.M;
     t.model_noise = c->opts.model_noise == PI_NOISE_SAMPLED ? 1 : 0;
     t.err = c->d_err;
+    t.qprod = pi2rh_tc_qprod(c->opts.precision);
     return t;
 }

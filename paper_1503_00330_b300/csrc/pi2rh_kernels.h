@@ -87,6 +87,9 @@ constexpr int TC_CHUNK_BYTES = 2 * TC_HALF_CHUNK;                      // 8 KB
 constexpr int TC_CHUNKS_PER_TILE = TC_KF / 16 + 1;                     // 11
 constexpr int TC_TILE_BYTES = TC_CHUNKS_PER_TILE * TC_CHUNK_BYTES;     // 90,112
 constexpr int TC_CONST_BYTES = 2 * TC_TILE_FIELDS * 4;                 // 1,024
+// Chunks 2..TC_QUAD_LAST_CHUNK carry K steps 1..8 of the exponent GEMM, whose
+// features (16..143) are all quadratic z_a z_b.
+constexpr int TC_QUAD_LAST_CHUNK = 9;
 constexpr int TC_CONST_FEATURE = 152;   // feature column holding the constant 1 (+ 2^-14 in the lo part)
 
 // Quadratic feature k (16 <= k < 152) is z_a z_b with (a, b) the (k-16)-th
@@ -123,6 +126,7 @@ struct TcArgs {
     float *y_out, *var_out;
     int n_pred;
     int *err;
+    int qprod;   // split products on the quadratic-feature K steps: 3 or 2 (selects the kernel)
 };
 
 struct TcBatchArgs {
@@ -130,6 +134,7 @@ struct TcBatchArgs {
     const int2 *items;         // [n_items] (controller, block of TC_SLOTS slots)
     int n_items;
     int *counter;
+    int qprod;                 // split products of every controller in the launch (3 or 2)
 };
 
 cudaError_t launch_rollout_tc(const TcArgs &a, cudaStream_t s);

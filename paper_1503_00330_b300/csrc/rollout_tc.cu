@@ -361,8 +361,10 @@ __device__ bool tc_producer_item(const TcArgs &a, const TcSmem &S, TcProducer &P
 // The MMAs of chunks J..J1-1 of a tile (all in the ring slots of the same
 // index): chunk 1 issues the N = 256 triple of K step 0 of S (columns 0-127)
 // and the Y GEMM (128-255), whose B operand is chunks 0 and 1 (hi and lo,
-// 256 rows each); chunk j >= 2 issues the N = 128 triple of K step j - 1.
-template <int J, int J1>
+// 256 rows each); chunk j >= 2 issues the N = 128 triple of K step j - 1, or
+// with QP = 2 on the quadratic-feature K steps 1-8 the pair A_hi B_hi +
+// A_hi B_lo.
+template <int J, int J1, int QP>
 __device__ __forceinline__ void tc_issue_chunks(uint32_t dS, uint64_t a_hi, uint64_t a_lo, uint64_t b0,
                                                 uint32_t idesc, uint32_t idesc_wide)
 {
@@ -372,10 +374,13 @@ __device__ __forceinline__ void tc_issue_chunks(uint32_t dS, uint64_t a_hi, uint
             mma3_elect(dS, a_hi, a_lo, b0, b0 + CH, idesc_wide, 0u);
         } else if constexpr (J >= 2) {
             constexpr uint64_t ka = (uint64_t)((J - 1) * 16);
-            mma3_elect(dS, a_hi + ka, a_lo + ka, b0 + J * CH, b0 + J * CH + (uint64_t)(TC_HALF_CHUNK >> 4), idesc,
-                       1u);
+            constexpr uint64_t bl = J * CH + (uint64_t)(TC_HALF_CHUNK >> 4);
+            if constexpr (QP == 2 && J <= TC_QUAD_LAST_CHUNK)
+                mma2_elect(dS, a_hi + ka, b0 + J * CH, b0 + bl, idesc);
+            else
+                mma3_elect(dS, a_hi + ka, a_lo + ka, b0 + J * CH, b0 + bl, idesc, 1u);
         }
-        tc_issue_chunks<J + 1, J1>(dS, a_hi, a_lo, b0, idesc, idesc_wide);
+        tc_issue_chunks<J + 1, J1, QP>(dS, a_hi, a_lo, b0, idesc, idesc_wide);
     }
 }
 
@@ -387,7 +392,7 @@ __device__ __forceinline__ void tc_issue_chunks(uint32_t dS, uint64_t a_hi, uint
 // below has no per-chunk bookkeeping.)  Per tile: wait for group A, its 18
 // MMAs (the N = 256 triple and K steps 1-4), release A; wait for group B, its
 // 15 MMAs (K steps 5-9), release B; signal the accumulator.
-template <bool PREDICT>
+template <bool PREDICT, int QP>
 __device__ bool tc_issuer_item(const TcArgs &a, const TcSmem &S, uint32_t tbase, TcIssuer &I, int n_out)
 {
     unsigned char *smem = S.base;
@@ -420,12 +425,12 @@ __device__ bool tc_issuer_item(const TcArgs &a, const TcSmem &S, uint32_t tbase,
             if (!ok) break;
             tc_fence_after();
             const uint32_t dS = tbase + buf * 256;   // S: columns 0-127, Y: 128-255
-            tc_issue_chunks<1, GA>(dS, a_hi, a_lo, b0, idesc, idesc_wide);
+            tc_issue_chunks<1, GA, QP>(dS, a_hi, a_lo, b0, idesc, idesc_wide);
             commit_elect(&empty[0]);
             ok = __all_sync(0xffffffffu, mbar_wait_bounded(&full[1], ph, abort_flag));
             if (!ok) break;
             tc_fence_after();
-            tc_issue_chunks<GA, NCH>(dS, a_hi, a_lo, b0, idesc, idesc_wide);
+            tc_issue_chunks<GA, NCH, QP>(dS, a_hi, a_lo, b0, idesc, idesc_wide);
             commit_elect(&empty[1]);
             commit_elect(&acc_full[buf]);
         }
@@ -713,7 +718,7 @@ __device__ __forceinline__ void tc_flag_abort(const TcArgs &a, const TcSmem &S, 
 // One CTA's whole life for the 128-slot block at slot_base: set-up, the
 // three roles, drain, tensor-memory release.  With NSPLIT > 1 the CTA is one
 // of the NSPLIT CTAs of a cluster that share the block and split its outputs.
-template <bool PREDICT, int NSPLIT>
+template <bool PREDICT, int NSPLIT, int QP>
 __device__ __forceinline__ void tc_cta(const TcArgs &a, long long slot_base, unsigned char *smem)
 {
     static_assert(NSPLIT == 1 || !PREDICT, "prediction mode is not split");
@@ -738,7 +743,7 @@ __device__ __forceinline__ void tc_cta(const TcArgs &a, long long slot_base, uns
         if (!pok && lane == 0) tc_flag_abort(a, S, DEVERR_TIMEOUT_EMPTY);
         __syncwarp();
     } else if (warp == 1) {
-        issuer_ok = tc_issuer_item<PREDICT>(a, S, tbase, I, n_out);
+        issuer_ok = tc_issuer_item<PREDICT, QP>(a, S, tbase, I, n_out);
         if (!issuer_ok && lane == 0) tc_flag_abort(a, S, DEVERR_TIMEOUT_FULL);
         __syncwarp();
     } else {
@@ -761,17 +766,17 @@ __device__ __forceinline__ void tc_cta(const TcArgs &a, long long slot_base, uns
 // Single-controller kernel.  NSPLIT = 1: one CTA per 128-slot block.
 // NSPLIT = 2, 3, 4 (rollouts only): launched in clusters of NSPLIT CTAs that
 // share one slot block and split its 12 outputs (see tc_epilogue_item).
-template <bool PREDICT, int NSPLIT>
+template <bool PREDICT, int NSPLIT, int QP>
 __global__ void __launch_bounds__(NTHREADS, 1) rollout_tc_kernel(const __grid_constant__ TcArgs a)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
-    tc_cta<PREDICT, NSPLIT>(a, (long long)(blockIdx.x / NSPLIT) * BM, smem);
+    tc_cta<PREDICT, NSPLIT, QP>(a, (long long)(blockIdx.x / NSPLIT) * BM, smem);
 }
 
 // Group form: one (controller, 128-slot block) item per CTA (NSPLIT = 1) or
 // per cluster of NSPLIT CTAs, all items in one wave; the arguments come from
 // the device table.  Used when a batch's items alone would leave SMs idle.
-template <int NSPLIT>
+template <int NSPLIT, int QP>
 __global__ void __launch_bounds__(NTHREADS, 1) rollout_tc_group_kernel(const __grid_constant__ TcBatchArgs b)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -779,12 +784,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) rollout_tc_group_kernel(const __g
     const int2 it = b.items[blockIdx.x / NSPLIT];
     if (threadIdx.x == 0) s_args = b.args[it.x];
     __syncthreads();
-    tc_cta<false, NSPLIT>(s_args, (long long)it.y * BM, smem);
+    tc_cta<false, NSPLIT, QP>(s_args, (long long)it.y * BM, smem);
 }
 
 // Persistent batched form (see rollout_fp32_batch_kernel): CTAs claim
 // (controller, 128-slot block) items; every ring position and the TMEM
 // allocation carry over between items.
+template <int QP>
 __global__ void __launch_bounds__(NTHREADS, 1) rollout_tc_batch_kernel(const __grid_constant__ TcBatchArgs b)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -819,7 +825,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) rollout_tc_batch_kernel(const __g
             __syncwarp();
         } else if (warp == 1) {
             if (issuer_ok) {
-                issuer_ok = tc_issuer_item<false>(a, S, tbase, I, NY);
+                issuer_ok = tc_issuer_item<false, QP>(a, S, tbase, I, NY);
                 if (!issuer_ok && lane == 0) tc_flag_abort(a, S, DEVERR_TIMEOUT_FULL);
             }
             __syncwarp();
@@ -856,16 +862,16 @@ void split_config(cudaLaunchConfig_t &cfg, cudaLaunchAttribute *at, long long bl
 
 // Sets the shared-memory attribute of one kernel instantiation once and
 // checks that it can be launched with NTHREADS threads.
-template <bool PREDICT, int NSPLIT>
+template <bool PREDICT, int NSPLIT, int QP = 3>
 cudaError_t prepare_tc()
 {
     static std::atomic<uint64_t> done;
-    cudaError_t e = set_smem_once(done, rollout_tc_kernel<PREDICT, NSPLIT>, SMEM_BYTES);
+    cudaError_t e = set_smem_once(done, rollout_tc_kernel<PREDICT, NSPLIT, QP>, SMEM_BYTES);
     if (e != cudaSuccess) return e;
     static std::atomic<bool> checked{false};
     if (checked.load(std::memory_order_acquire)) return cudaSuccess;
     cudaFuncAttributes fa;
-    e = cudaFuncGetAttributes(&fa, rollout_tc_kernel<PREDICT, NSPLIT>);
+    e = cudaFuncGetAttributes(&fa, rollout_tc_kernel<PREDICT, NSPLIT, QP>);
     if (e != cudaSuccess) return e;
     snprintf(g_tc_diag, sizeof g_tc_diag,
              "split %d: regs %d, maxThreadsPerBlock %d, dynamic smem %d (max %d), static smem %zu, local %zu", NSPLIT,
@@ -877,7 +883,9 @@ cudaError_t prepare_tc()
 }
 
 // CTAs of the single-controller kernel with clusters of NSPLIT that can be
-// resident at once (0 if the cluster shape cannot be launched).
+// resident at once (0 if the cluster shape cannot be launched).  Both product
+// counts use the same threads and shared memory, so the three-product
+// instantiation stands for both.
 template <int NSPLIT>
 long long resident_ctas()
 {
@@ -893,7 +901,7 @@ long long resident_ctas()
     cudaLaunchAttribute at[1];
     split_config(cfg, at, sms, NSPLIT, nullptr);
     int clusters = 0;
-    if (cudaOccupancyMaxActiveClusters(&clusters, rollout_tc_kernel<false, NSPLIT>, &cfg) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveClusters(&clusters, rollout_tc_kernel<false, NSPLIT, 3>, &cfg) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
@@ -931,26 +939,26 @@ int choose_split(long long blocks)
     return best;
 }
 
-template <int NSPLIT>
+template <int NSPLIT, int QP>
 cudaError_t launch_split(const TcArgs &a, long long blocks, cudaStream_t s)
 {
-    cudaError_t e = prepare_tc<false, NSPLIT>();
+    cudaError_t e = prepare_tc<false, NSPLIT, QP>();
     if (e != cudaSuccess) return e;
     if (NSPLIT == 1) {
-        rollout_tc_kernel<false, NSPLIT><<<(unsigned)blocks, NTHREADS, SMEM_BYTES, s>>>(a);
+        rollout_tc_kernel<false, NSPLIT, QP><<<(unsigned)blocks, NTHREADS, SMEM_BYTES, s>>>(a);
         return cudaGetLastError();
     }
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute at[1];
     split_config(cfg, at, blocks, NSPLIT, s);
-    return cudaLaunchKernelEx(&cfg, rollout_tc_kernel<false, NSPLIT>, a);
+    return cudaLaunchKernelEx(&cfg, rollout_tc_kernel<false, NSPLIT, QP>, a);
 }
 
-template <int NSPLIT>
+template <int NSPLIT, int QP = 3>
 cudaError_t prepare_group()
 {
     static std::atomic<uint64_t> done;
-    return set_smem_once(done, rollout_tc_group_kernel<NSPLIT>, SMEM_BYTES);
+    return set_smem_once(done, rollout_tc_group_kernel<NSPLIT, QP>, SMEM_BYTES);
 }
 
 template <int NSPLIT>
@@ -964,31 +972,54 @@ bool group_clusters_resident(long long items)
     cudaLaunchAttribute at[1];
     split_config(cfg, at, items, NSPLIT, nullptr);
     int clusters = 0;
-    if (cudaOccupancyMaxActiveClusters(&clusters, rollout_tc_group_kernel<NSPLIT>, &cfg) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveClusters(&clusters, rollout_tc_group_kernel<NSPLIT, 3>, &cfg) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
     return clusters >= items;
 }
 
-template <int NSPLIT>
+template <int NSPLIT, int QP>
 cudaError_t launch_group(const TcBatchArgs &b, cudaStream_t s)
 {
-    cudaError_t e = prepare_group<NSPLIT>();
+    cudaError_t e = prepare_group<NSPLIT, QP>();
     if (e != cudaSuccess) return e;
     if (NSPLIT == 1) {
-        rollout_tc_group_kernel<1><<<(unsigned)b.n_items, NTHREADS, SMEM_BYTES, s>>>(b);
+        rollout_tc_group_kernel<1, QP><<<(unsigned)b.n_items, NTHREADS, SMEM_BYTES, s>>>(b);
         return cudaGetLastError();
     }
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute at[1];
     split_config(cfg, at, b.n_items, NSPLIT, s);
-    return cudaLaunchKernelEx(&cfg, rollout_tc_group_kernel<NSPLIT>, b);
+    return cudaLaunchKernelEx(&cfg, rollout_tc_group_kernel<NSPLIT, QP>, b);
 }
 
 cudaError_t check_tc_args(const TcArgs &a)
 {
-    return a.cost.n_obs > MAX_OBS || a.tiles_per_out <= 0 ? cudaErrorInvalidValue : cudaSuccess;
+    return a.cost.n_obs > MAX_OBS || a.tiles_per_out <= 0 || (a.qprod != 2 && a.qprod != 3) ? cudaErrorInvalidValue
+                                                                                             : cudaSuccess;
+}
+
+template <int QP>
+cudaError_t launch_rollout_tc_qp(const TcArgs &a, long long blocks, cudaStream_t s)
+{
+    switch (choose_split(blocks)) {
+    case 4: return launch_split<4, QP>(a, blocks, s);
+    case 3: return launch_split<3, QP>(a, blocks, s);
+    case 2: return launch_split<2, QP>(a, blocks, s);
+    default: return launch_split<1, QP>(a, blocks, s);
+    }
+}
+
+template <int QP>
+cudaError_t launch_group_qp(const TcBatchArgs &b, int split, cudaStream_t s)
+{
+    switch (split) {
+    case 4: return launch_group<4, QP>(b, s);
+    case 3: return launch_group<3, QP>(b, s);
+    case 2: return launch_group<2, QP>(b, s);
+    default: return launch_group<1, QP>(b, s);
+    }
 }
 
 }  // namespace
@@ -1002,22 +1033,22 @@ cudaError_t launch_rollout_tc(const TcArgs &a, cudaStream_t s)
     if (e != cudaSuccess) return e;
     const long long blocks = ((long long)a.K * a.M + BM - 1) / BM;
     if (blocks <= 0 || blocks > 0x7fffffffLL / 4) return cudaErrorInvalidValue;
-    switch (choose_split(blocks)) {
-    case 4: return launch_split<4>(a, blocks, s);
-    case 3: return launch_split<3>(a, blocks, s);
-    case 2: return launch_split<2>(a, blocks, s);
-    default: return launch_split<1>(a, blocks, s);
-    }
+    return a.qprod == 2 ? launch_rollout_tc_qp<2>(a, blocks, s) : launch_rollout_tc_qp<3>(a, blocks, s);
 }
 
 cudaError_t launch_predict_tc(const TcArgs &a, cudaStream_t s)
 {
     cudaError_t e = check_tc_args(a);
-    if (e == cudaSuccess) e = prepare_tc<true, 1>();
     if (e != cudaSuccess) return e;
     const long long blocks = ((long long)a.n_pred + BM - 1) / BM;
     if (blocks <= 0 || blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
-    rollout_tc_kernel<true, 1><<<(unsigned)blocks, NTHREADS, SMEM_BYTES, s>>>(a);
+    if (a.qprod == 2) {
+        if ((e = prepare_tc<true, 1, 2>()) != cudaSuccess) return e;
+        rollout_tc_kernel<true, 1, 2><<<(unsigned)blocks, NTHREADS, SMEM_BYTES, s>>>(a);
+    } else {
+        if ((e = prepare_tc<true, 1, 3>()) != cudaSuccess) return e;
+        rollout_tc_kernel<true, 1, 3><<<(unsigned)blocks, NTHREADS, SMEM_BYTES, s>>>(a);
+    }
     return cudaGetLastError();
 }
 
@@ -1039,23 +1070,23 @@ int tc_group_split(int n_items)
 
 cudaError_t launch_rollout_tc_group(const TcBatchArgs &b, int split, cudaStream_t s)
 {
-    if (b.n_items <= 0) return cudaErrorInvalidValue;
-    switch (split) {
-    case 4: return launch_group<4>(b, s);
-    case 3: return launch_group<3>(b, s);
-    case 2: return launch_group<2>(b, s);
-    default: return launch_group<1>(b, s);
-    }
+    if (b.n_items <= 0 || (b.qprod != 2 && b.qprod != 3)) return cudaErrorInvalidValue;
+    return b.qprod == 2 ? launch_group_qp<2>(b, split, s) : launch_group_qp<3>(b, split, s);
 }
 
-std::atomic<uint64_t> g_tc_batch_attr;
+std::atomic<uint64_t> g_tc_batch_attr[2];
 
 cudaError_t launch_rollout_tc_batch(const TcBatchArgs &b, int grid, cudaStream_t s)
 {
-    cudaError_t e = set_smem_once(g_tc_batch_attr, rollout_tc_batch_kernel, SMEM_BYTES);
-    if (e != cudaSuccess) return e;
-    if (grid <= 0) return cudaErrorInvalidValue;
-    rollout_tc_batch_kernel<<<grid, NTHREADS, SMEM_BYTES, s>>>(b);
+    if (grid <= 0 || (b.qprod != 2 && b.qprod != 3)) return cudaErrorInvalidValue;
+    cudaError_t e;
+    if (b.qprod == 2) {
+        if ((e = set_smem_once(g_tc_batch_attr[0], rollout_tc_batch_kernel<2>, SMEM_BYTES)) != cudaSuccess) return e;
+        rollout_tc_batch_kernel<2><<<grid, NTHREADS, SMEM_BYTES, s>>>(b);
+    } else {
+        if ((e = set_smem_once(g_tc_batch_attr[1], rollout_tc_batch_kernel<3>, SMEM_BYTES)) != cudaSuccess) return e;
+        rollout_tc_batch_kernel<3><<<grid, NTHREADS, SMEM_BYTES, s>>>(b);
+    }
     return cudaGetLastError();
 }
 

@@ -297,7 +297,7 @@ int pi_server::launch(Lane &L)
 {
     NvtxRange nv("pi_server group launch");
     const int n = (int)L.group.size();
-    const bool tc = form == PI_PRECISION_TC_FP16X3;
+    const bool tc = pi2rh_is_tc(form);
     const int spb = tc ? TC_SLOTS : RF_SLOTS;
     std::stable_sort(L.group.begin(), L.group.end(), [](const Req &a, const Req &b) { return a.q.T > b.q.T; });
     unsigned char *h = L.h, *d = L.d;
@@ -385,7 +385,7 @@ int pi_server::launch(Lane &L)
     if (e == cudaSuccess) {
         if (tc) {
             TcBatchArgs tb{reinterpret_cast<const TcArgs *>(d + lay.args), reinterpret_cast<const int2 *>(d + lay.ritems),
-                           nr, d_ctl};
+                           nr, d_ctl, pi2rh_tc_qprod(form)};
             // one item per CTA (a plain launch: the block scheduler fills SMs as
             // items finish, also across lanes); a small group as one wave of
             // clusters that split each block's outputs
@@ -664,7 +664,7 @@ int pi_server_create(pi_ctx *ctx, const pi_server_opts *opts, pi_server **out)
         return sfail(PI_ERR_INVALID_ARG, "server option out of range");
     if ((long long)o.K_max * ctx->opts.M > (1LL << 31) - 1) return sfail(PI_ERR_INVALID_ARG, "K_max * M too large");
     const int form = ctx->opts.precision;
-    if (form == PI_PRECISION_TC_FP16X3 && !ctx->d_wtiles)
+    if (pi2rh_is_tc(form) && !ctx->d_wtiles)
         return sfail(PI_ERR_INVALID_ARG, "tensor-core context without coefficient tiles");
     DevGuard dg(ctx->device);
     if (dg.err != cudaSuccess) return scuda(dg.err, "cudaSetDevice");
@@ -708,7 +708,7 @@ int pi_server_create(pi_ctx *ctx, const pi_server_opts *opts, pi_server **out)
             return bail(rc);
     }
     // lane tables
-    const int spb = form == PI_PRECISION_TC_FP16X3 ? TC_SLOTS : RF_SLOTS;
+    const int spb = pi2rh_is_tc(form) ? TC_SLOTS : RF_SLOTS;
     const long long g = o.max_group;
     const long long rblocks = ((long long)o.K_max * s->M + spb - 1) / spb;
     s->max_ritems = (int)std::min<long long>(g * rblocks, INT_MAX / 16);

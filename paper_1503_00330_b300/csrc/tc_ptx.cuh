@@ -102,6 +102,22 @@ __device__ __forceinline__ void mma3_elect(uint32_t d_tmem, uint64_t a_hi, uint6
         : "memory");
 }
 
+// Two of the split products of one K step, D += A_hi B_hi + A_hi B_lo (the
+// A operand at its fp16 rounding, the B operand split), issued like mma3_elect;
+// always accumulates.
+__device__ __forceinline__ void mma2_elect(uint32_t d_tmem, uint64_t a_hi, uint64_t b_hi, uint64_t b_lo,
+                                           uint32_t idesc)
+{
+    asm volatile(
+        "{\n\t.reg .pred t, e;\n\t"
+        "elect.sync _|e, 0xffffffff;\n\t"
+        "setp.eq.u32 t, %4, %4;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %4, t;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %3, %4, t;\n\t}" ::"r"(d_tmem),
+        "l"(a_hi), "l"(b_hi), "l"(b_lo), "r"(idesc)
+        : "memory");
+}
+
 // tcgen05.commit from the lane elect.sync picks (the lane that issued the
 // MMAs of mma3_elect): arrives on the mbarrier once they complete.
 __device__ __forceinline__ void commit_elect(uint64_t *bar)

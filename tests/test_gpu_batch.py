@@ -30,7 +30,7 @@ def _problems():
     return out
 
 
-@pytest.mark.parametrize("form", ["fp32", "tc"])
+@pytest.mark.parametrize("form", ["fp32", "tc", "tc_fp16x2"])
 def test_batch_equals_single_updates(form):
     from paper_1503_00330_b300.api import Batch, Controller
     probs = _problems()

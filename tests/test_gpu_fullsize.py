@@ -18,10 +18,12 @@ reported; a rollout with flips must differ from the oracle by exactly its
 flips' cost (n * w_obs * dt, within the ordinary tolerance), and every other
 rollout is held to the ordinary tolerance.
 
-Tolerances: u_out max_t |du| / max_t |u_ref| <= 1e-5 per channel and
-|dS| / S <= 1e-5, for both forms (the tensor-core split products carry ~22
-significand bits, so that form is held to the FP32 bound, tighter than the
-2e-3 stated for it).  The damped cases have their own bounds (see there).
+Tolerances: u_out max_t |du| / max_t |u_ref| per channel and |dS| / S, per
+form: 1e-5 for FP32 and for the three-product tensor-core form (its split
+products carry ~22 significand bits, so it is held to the FP32 bound, tighter
+than the 2e-3 stated for the tensor-core form); 2e-3 for the two-product form
+(tc_fp16x2), whose 128 quadratic terms per exponent each carry an fp16
+rounding.  The damped cases have their own bounds (see there).
 """
 import numpy as np
 import pytest
@@ -31,9 +33,9 @@ from paper_1503_00330_b300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-U_TOL = 1e-5
-S_TOL = 1e-5
-FORMS = ["fp32", "tc"]
+FORMS = ["fp32", "tc", "tc_fp16x2"]
+U_TOL = {"fp32": 1e-5, "tc": 1e-5, "tc_fp16x2": 2e-3}
+S_TOL = {"fp32": 1e-5, "tc": 1e-5, "tc_fp16x2": 2e-3}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -98,10 +100,10 @@ def _check_against_oracle(p, form, ref, u, c, steps, label):
           f"indicator flips {int(n_flip.sum())} in {int(flipped.sum())} rollouts "
           f"(residual after the flips' cost {resid[flipped].max() if flipped.any() else 0.0:.3g})")
     assert np.all(np.isfinite(u)) and np.all(np.isfinite(c))
-    assert np.all(err[~flipped] <= S_TOL)
-    assert np.all(resid[flipped] <= S_TOL)
+    assert np.all(err[~flipped] <= S_TOL[form])
+    assert np.all(resid[flipped] <= S_TOL[form])
     assert flipped.sum() <= max(2, p.K // 1000)
-    assert np.all(eu <= U_TOL)
+    assert np.all(eu <= U_TOL[form])
 
 
 # ---------------------------------------------------------------------------
@@ -153,7 +155,12 @@ def _damped_model(L, seed):
 
 
 # cost-to-go error bounds of the damped cases (relative, per rollout)
-DAMPED_S_BOUND = {"fp32": 5e-5, "tc": 2e-4}
+DAMPED_S_BOUND = {"fp32": 5e-5, "tc": 2e-4, "tc_fp16x2": 2e-3}
+# rollouts with indicator flips allowed in the damped cases: the two-product form's
+# exponents carry ~1e-4 relative error per step, which over 600-2000 steps moves a
+# grazing trajectory across a cylinder boundary at a different step (5 of 300
+# rollouts over 2000 steps); their weight in Eq. 2 is bounded by the u_out check
+DAMPED_FLIPS = {"fp32": lambda K: 2, "tc": lambda K: 2, "tc_fp16x2": lambda K: max(2, K // 50)}
 TC_U_BOUND = 2e-3
 
 
@@ -165,14 +172,15 @@ def test_damped_model_conditioning(oracle, form, K, T, L):
     FP32 rounding of an exponent, about q * 2^-24 absolute, is a relative error
     of the same size in its softmax weight (Eq. 1); the variance term of the
     cost inherits it at the wider spread, so the cost-to-go carries relative
-    errors well above 1e-5 (bounded here by DAMPED_S_BOUND; the tensor-core
-    exponents carry ~22 significand bits, so four times the FP32 bound).
+    errors well above 1e-5 (bounded here by DAMPED_S_BOUND; the three-product
+    tensor-core exponents carry ~22 significand bits, so four times the FP32
+    bound; the two-product form is held to its stated 2e-3).
 
     u_out is then held to the first-order propagation of those errors through
     Eq. 2: P_k = softmax(-S_k / lambda) moves by P_k (|dS_k| + max |dS|) / lambda,
     so |du_c| <= 2 max_{k,i} |dS_{k,i}| max_k |eps_{k,c}| / lambda, where
     |dS_{k,i}| <= |dphi_k| + dt sum_j |dq_{k,j}| from the per-step errors.  The
-    tensor-core form is also held to its stated bound, 2e-3 per channel."""
+    tensor-core forms are also held to their stated bound, 2e-3 per channel."""
     model = _damped_model(L, 2000 + K)
     p = W.problem(K, T, L, seed=2000 + K, n_obs=5, model=model)
     ref = _oracle_full(oracle, p)
@@ -193,10 +201,10 @@ def test_damped_model_conditioning(oracle, form, K, T, L):
     print(f"damped K={K} T={T} L={L} ({form}): u_out rel err {np.array2string(eu, precision=3)}, "
           f"first-order bound {np.array2string(bound, precision=3)}; S0 max rel err {eS.max():.3g}; "
           f"max |dS| {dS_max:.3g}; rollouts with indicator flips {flips}")
-    assert flips <= 2
+    assert flips <= DAMPED_FLIPS[form](K)
     assert eS.max() <= DAMPED_S_BOUND[form]
-    assert np.all(eu <= bound + U_TOL)
-    if form == "tc":
+    assert np.all(eu <= bound + U_TOL[form])
+    if form != "fp32":
         assert np.all(eu <= TC_U_BOUND)
 
 
@@ -237,7 +245,7 @@ def test_batched_workload_sampled(batched_ref, form):
         c = c_b[i].cpu().numpy().astype(np.float64)
         err = np.abs(c[ks] - S0) / S0
         print(f"batched ({form}) controller {i} K={p.K} T={p.T} L={p.model.L}: S0 max rel err {err.max():.3g}")
-        assert np.all(err <= S_TOL)
+        assert np.all(err <= S_TOL[form])
         assert np.all(np.isfinite(u_b[i].cpu().numpy()))
     batch.close()
     for c in ctls:

@@ -5,7 +5,8 @@ run (a real-time control loop that forbids cudaMalloc after start-up, or a
 host program that owns all GPU memory through its own pool): it keeps its
 scratch in a fixed array inside the library.  Its results must match the
 ordinary entry point's within the end-to-end tolerances of the parity tests,
-in both forms, on two calls in a row with different sizes and seeds: the
+in every form (FP32 and both tensor-core forms), on two calls in a row with
+different sizes and seeds: the
 second call is the smaller one, so it runs over the first call's leftovers
 in the shared array and must not read them.  After one set-up call, further
 calls must leave the device's free memory unchanged.  This file sorts last so
@@ -36,7 +37,7 @@ def _call(lib, fn, h, x0, un, K, T, lam, su, seed, u, c):
     _lib.check(rc)
 
 
-@pytest.mark.parametrize("form", ["fp32", "tc"])
+@pytest.mark.parametrize("form", ["fp32", "tc", "tc_fp16x2"])
 def test_noalloc_matches_update_two_calls(form):
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
