@@ -2,11 +2,11 @@
 of Eq. 1 limits the accuracy, through the C ABI against the FP64 oracle.
 
 * Realtime update (K=8192, T=100, L=512, 16 obstacles, seed 0), launched as
-  the benchmark launches it, in both forms: u_out element-wise per channel and
+  the benchmark launches it, in every form: u_out element-wise per channel and
   all 8192 costs S_{k,0} (Sec. 3.1, Eq. 2).  The oracle runs every rollout once
-  for both forms.
+  for all forms.
 * Precision shape (L=2048, T=100, cond(D_j) log-uniform in [1, 1e3]) at
-  K=2048 in full, in both forms.
+  K=2048 in full, in every form.
 * 64-controller batch at full size: S_{k,0} of the 32 first and 32 last
   rollouts of four controllers (the two largest L and the two largest K).
 
