@@ -780,11 +780,10 @@ template <int NSPLIT, int QP>
 __global__ void __launch_bounds__(NTHREADS, 1) rollout_tc_group_kernel(const __grid_constant__ TcBatchArgs b)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ TcArgs s_args;
+    // the item's arguments are read from the device table where they are used
+    // (a shared-memory copy kept more values live and spilled)
     const int2 it = b.items[blockIdx.x / NSPLIT];
-    if (threadIdx.x == 0) s_args = b.args[it.x];
-    __syncthreads();
-    tc_cta<false, NSPLIT, QP>(s_args, (long long)it.y * BM, smem);
+    tc_cta<false, NSPLIT, QP>(b.args[it.x], (long long)it.y * BM, smem);
 }
 
 // Persistent batched form (see rollout_fp32_batch_kernel): CTAs claim
