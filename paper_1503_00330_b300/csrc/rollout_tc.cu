@@ -90,7 +90,8 @@ constexpr int OFF_Y = OFF_X + NX * BM * 4;                      // [NY][BM]
 constexpr int OFF_V = OFF_Y + NY * BM * 4;
 constexpr int OFF_YREF = OFF_V + NY * BM * 4;
 constexpr int OFF_Q = OFF_YREF + NY * BM * 4;                   // [BM]
-constexpr int OFF_OBS = OFF_Q + BM * 4;
+constexpr int OFF_N = OFF_Q + BM * 4;                           // [NY + NU][BM] normals of the step
+constexpr int OFF_OBS = OFF_N + (NY + NU) * BM * 4;
 constexpr int OFF_BAR = OFF_OBS + MAX_OBS * 8;
 // barriers: full[NGRP], empty[NGRP], acc_full[2], acc_empty[2],
 //           const_full[4], const_empty[4], phi_ready, xfull, xfree, drain
@@ -200,11 +201,11 @@ __device__ __forceinline__ void split_pair(const float (&zext)[17], uint32_t &hw
 }
 
 // Writes the hi/lo fp16 feature rows of slot r from z (zext[16] == 1), one
-// 16-byte core-matrix row (8 features) at a time.
-template <int K8 = 0>
+// 16-byte core-matrix row (8 features) at a time: rows K8 .. K8END - 1.
+template <int K8 = 0, int K8END = KF / 8>
 __device__ __forceinline__ void build_features(unsigned char *smem, int r, const float (&zext)[17])
 {
-    if constexpr (K8 < KF / 8) {
+    if constexpr (K8 < K8END) {
         uint32_t hw[4], lw[4];
         split_pair<K8 * 8 + 0>(zext, hw[0], lw[0]);
         split_pair<K8 * 8 + 2>(zext, hw[1], lw[1]);
@@ -213,13 +214,13 @@ __device__ __forceinline__ void build_features(unsigned char *smem, int r, const
         const uint32_t off = kmajor_offset(r, K8 * 8, KF);
         *reinterpret_cast<uint4 *>(smem + OFF_PHI_HI + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
         *reinterpret_cast<uint4 *>(smem + OFF_PHI_LO + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
-        build_features<K8 + 1>(smem, r, zext);
+        build_features<K8 + 1, K8END>(smem, r, zext);
     }
 }
 
 struct TcSmem {
     unsigned char *base;
-    float *part, *zbuf, *xbuf, *ybuf, *vbuf, *yrbuf, *qbuf;
+    float *part, *zbuf, *xbuf, *ybuf, *vbuf, *yrbuf, *qbuf, *nbuf;
     float2 *obs_s;
     uint64_t *full, *empty, *acc_full, *acc_empty, *const_full, *const_empty, *phi_ready;
     uint64_t *xfull, *xfree;   // output exchange between the CTAs of a cluster (split form)
@@ -239,6 +240,7 @@ __device__ __forceinline__ TcSmem tc_smem(unsigned char *smem)
     S.vbuf = reinterpret_cast<float *>(smem + OFF_V);
     S.yrbuf = reinterpret_cast<float *>(smem + OFF_YREF);
     S.qbuf = reinterpret_cast<float *>(smem + OFF_Q);
+    S.nbuf = reinterpret_cast<float *>(smem + OFF_N);
     S.obs_s = reinterpret_cast<float2 *>(smem + OFF_OBS);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + OFF_BAR);
     S.full = bars;
@@ -464,7 +466,7 @@ __device__ void tc_epilogue_item(const TcArgs &a, const TcSmem &S, uint32_t tbas
     const int o_begin = (int)rank * n_out;
     unsigned char *smem = S.base;
     float *part = S.part, *zbuf = S.zbuf, *xbuf = S.xbuf, *ybuf = S.ybuf, *vbuf = S.vbuf, *yrbuf = S.yrbuf,
-          *qbuf = S.qbuf;
+          *qbuf = S.qbuf, *nbuf = S.nbuf;
     float2 *obs_s = S.obs_s;
     uint64_t *acc_full = S.acc_full, *acc_empty = S.acc_empty, *const_full = S.const_full,
              *const_empty = S.const_empty, *phi_ready = S.phi_ready;
@@ -517,6 +519,33 @@ __device__ void tc_epilogue_item(const TcArgs &a, const TcSmem &S, uint32_t tbas
     named_bar_sync(1, NE);
 
     for (int t = 0; t < nsteps; ++t) {
+        // The normals of this step (model noise) and of the next (control
+        // perturbation) do not depend on the state: the other column half
+        // draws them while every epilogue warp waits for the step's first
+        // tile, off the serial dynamics step at the end of the step.  The
+        // owners read them there, after barrier 4; the end-of-step barrier 3
+        // orders these writes after the previous step's reads.
+        if (!PREDICT && !owner) {
+            if (a.model_noise) {
+#pragma unroll
+                for (int b = 0; b < 3; ++b) {
+                    const float4 nb =
+                        box_muller4(noise_block(a.seed, (uint32_t)k, (uint32_t)t, (uint32_t)(b + 1), (uint32_t)m));
+                    nbuf[(4 * b + 0) * BM + r] = nb.x;
+                    nbuf[(4 * b + 1) * BM + r] = nb.y;
+                    nbuf[(4 * b + 2) * BM + r] = nb.z;
+                    nbuf[(4 * b + 3) * BM + r] = nb.w;
+                }
+            }
+            if (t + 1 < a.T) {
+                const float4 nn = box_muller4(noise_block(a.seed, (uint32_t)k, (uint32_t)(t + 1), 0u, 0u));
+                nbuf[(NY + 0) * BM + r] = nn.x;
+                nbuf[(NY + 1) * BM + r] = nn.y;
+                nbuf[(NY + 2) * BM + r] = nn.z;
+                nbuf[(NY + 3) * BM + r] = nn.w;
+            }
+            named_bar_arrive(4, NE);
+        }
         // split form: the other CTAs have read this CTA's values of the last
         // step before any of this step's are sent (after each merge below)
         if (!PREDICT && ncl > 1 && owner && t > 0 && !aborted &&
@@ -623,16 +652,10 @@ __device__ void tc_epilogue_item(const TcArgs &a, const TcSmem &S, uint32_t tbas
                 for (int c = 0; c < NX; ++c) x[c] = xbuf[c * BM + r];
                 qbuf[r] = running_cost(a.cost, obs_s, x, var);
                 float n[NY];
+                named_bar_sync(4, NE);   // the other half's normals of this step are in nbuf
                 if (a.model_noise) {
 #pragma unroll
-                    for (int b = 0; b < 3; ++b) {
-                        const float4 nb = box_muller4(
-                            noise_block(a.seed, (uint32_t)k, (uint32_t)t, (uint32_t)(b + 1), (uint32_t)m));
-                        n[4 * b] = nb.x;
-                        n[4 * b + 1] = nb.y;
-                        n[4 * b + 2] = nb.z;
-                        n[4 * b + 3] = nb.w;
-                    }
+                    for (int o = 0; o < NY; ++o) n[o] = nbuf[o * BM + r];
                 } else {
 #pragma unroll
                     for (int o = 0; o < NY; ++o) n[o] = 0.0f;
@@ -652,8 +675,8 @@ __device__ void tc_epilogue_item(const TcArgs &a, const TcSmem &S, uint32_t tbas
                     a.cost_tk[(size_t)t * a.K + k] = qs / (float)M;
                 }
                 if (t + 1 < a.T) {
-                    const float4 nn =
-                        box_muller4(noise_block(a.seed, (uint32_t)k, (uint32_t)(t + 1), 0u, 0u));
+                    const float4 nn = make_float4(nbuf[(NY + 0) * BM + r], nbuf[(NY + 1) * BM + r],
+                                                  nbuf[(NY + 2) * BM + r], nbuf[(NY + 3) * BM + r]);
                     const float eps[4] = {a.sqrt_sigma_u[0] * nn.x, a.sqrt_sigma_u[1] * nn.y,
                                           a.sqrt_sigma_u[2] * nn.z, a.sqrt_sigma_u[3] * nn.w};
 #pragma unroll
@@ -674,7 +697,22 @@ __device__ void tc_epilogue_item(const TcArgs &a, const TcSmem &S, uint32_t tbas
                 }
             }
             zext[16] = 1.0f;
-            if (t + 1 < nsteps) build_features(smem, r, zext);
+            if (PREDICT) {
+                if (t + 1 < nsteps) build_features(smem, r, zext);
+            } else if (t + 1 < nsteps) {
+                // publish z, then each column half builds half of the feature rows
+#pragma unroll
+                for (int c = 0; c < NZ; ++c) zbuf[c * BM + r] = zext[c];
+                named_bar_arrive(5, NE);
+                build_features<0, KF / 16>(smem, r, zext);
+            }
+        } else if (!PREDICT && t + 1 < nsteps) {
+            named_bar_sync(5, NE);
+            float zext[17];
+#pragma unroll
+            for (int c = 0; c < NZ; ++c) zext[c] = zbuf[c * BM + r];
+            zext[16] = 1.0f;
+            build_features<KF / 16, KF / 8>(smem, r, zext);
         }
         const bool any_abort = bar_sync_or(3, NE, aborted || *abort_flag != 0);
         if (any_abort) break;
