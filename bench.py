@@ -15,6 +15,17 @@ copies inside the timed region); ``roofline`` is the rollout kernel's FP32
 rate from per-launch event times; ``cpu_baseline`` is the FP64 oracle timed on
 a bounded sample of the same workload.
 
+At N=1 the default line also carries, beside the FP32 headline:
+  * ``forms``: the realtime loop in the tensor-core forms (three and two split
+    products), each with its roofline, clocks and error against the oracle;
+  * ``precision_workload``: K=65536, T=100, L=2048 (conditioned D) in every form;
+  * ``batched_workload``: 64 uneven controllers in one graph-captured launch,
+    every form;
+  * ``serving_workload``: 256 quadrotors at 50 Hz through the continuous-batching
+    server (throughput, capacity, p50/p99 latency saturated and at half load).
+Each form's error is measured on the workload's seed-0 update against the
+oracle run that the CPU-baseline leg times (so the oracle runs nowhere else).
+
 ``--impl reference`` times the oracle itself (there is no reference
 implementation of the paper's method other than the oracle written from it).
 """
@@ -249,6 +260,38 @@ def form_errors(p, form, ref, dev):
     out["reference"] = (f"FP64 oracle, one update of the first {Ks} rollouts (the CPU-baseline sample); "
                         f"costs also against rollouts 0..{Ks - 1} of the full K={p.K} launch")
     ctl.close()
+    return out
+
+
+def batched_cpu_baseline(probs, pick, n):
+    """FP64 oracle on the first n rollouts of the controllers in `pick` of the batched
+    workload (their seed-0 inputs), timed on all host threads; the results are the
+    reference of the batched errors (rollout k of a controller depends only on its own
+    noise counters)."""
+    from oracle import oracle as O
+    O.build()
+    ref, steps, el = {}, 0, 0.0
+    for i in pick:
+        p = probs[i]
+        t0 = time.perf_counter()
+        r = O.rollouts(p.model, p.cost, p.x0, p.u_nom, n, p.T, p.sigma_u, p.seed, M=p.M, model_noise=p.model_noise)
+        ref[i] = O.cost_to_go(r["cost"], r["phi"], float(p.model.dt))[:, 0]
+        el += time.perf_counter() - t0
+        steps += n * p.T * p.M
+    return ({"value": steps / el, "unit": UNIT, "cores": O.max_threads(), "kind": "oracle",
+             "sample": "the first {} rollouts of controllers {} (K, T, L = {}), {:.2f} s".format(
+                 n, list(pick), [(probs[i].K, probs[i].T, probs[i].model.L) for i in pick], el)}, ref)
+
+
+def batched_errors(probs, costs, ref):
+    """costs_out S_{k,0} of the sampled rollouts of each picked controller, from one batched
+    update of the seed-0 inputs, against the oracle (relative, max over the sample)."""
+    out = {}
+    for i, S0 in ref.items():
+        c = costs[i][:len(S0)]
+        out[f"controller_{i}"] = {"costs_rel_err_max": float(np.max(np.abs(c - S0) / np.abs(S0))),
+                                  "rollouts": int(len(S0)), "K": probs[i].K, "T": probs[i].T, "L": probs[i].model.L}
+    out["costs_rel_err_max"] = max(v["costs_rel_err_max"] for v in out.values())
     return out
 
 
@@ -540,15 +583,85 @@ def time_updates(precision, p, steps, warmup, dev, workload):
             "clocks": clk}
 
 
+BATCHED_SCHEDULE = {"fp32": ("longest_first", 1), "tc": ("longest_first", 1), "tc_fp16x2": ("longest_first", 1)}
+
+
+def batched_forms(probs, sched, order, steps, warmup, dev, pick=()):
+    """Times one batched update of `probs` per form in `order` (schedule per form from
+    `sched`), with CUDA events on the launching stream and L2 flushed between timed
+    updates.  For the controllers in `pick`, also returns each form's costs_out of one
+    update with the controllers' own seeds (the seed-0 inputs) for the error check."""
+    import torch
+    from paper_1503_00330_b300.api import Batch, Controller
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    forms, costs = {}, {}
+    for form in order:
+        ctls = [Controller(p.model, p.cost, M=p.M, model_noise=p.model_noise, precision=form) for p in probs]
+        batch = Batch(ctls, [p.K for p in probs], [p.T for p in probs], precision=form,
+                      x0=[p.x0 for p in probs], u_nom=[p.u_nom for p in probs])
+        batch.set_schedule(sched[form][0])
+        batch.set_tile(sched[form][1])
+        lam = [p.lam for p in probs]
+        su = [p.sigma_u for p in probs]
+        for i in range(warmup):
+            batch.update(lam, su, [p.seed + i for p in probs])
+        batch.sync()
+        ms = []
+        launches0 = batch.launch_count()
+        with ClockSampler(dev.index or 0) as clocks:
+            for i in range(steps):
+                flush.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                batch.update(lam, su, [p.seed + warmup + i for p in probs])
+                b.record(stream)
+                b.synchronize()
+                ms.append(a.elapsed_time(b))
+        batch.sync()
+        launches = batch.launch_count() - launches0
+        if pick:
+            _, c_b = batch.update(lam, su, [p.seed for p in probs])
+            batch.sync()
+            costs[form] = {i: c_b[i].cpu().numpy().astype(np.float64) for i in pick}
+        rs = batch.rollout_steps()
+        useful = sum(p.K * p.T * p.M * 12 * p.model.L for p in probs) * FLOPS_PER_FIELD
+        entry = {"value": rs * steps / (sum(ms) / 1e3), "ms_per_update": statistics.mean(ms), "steps": steps,
+                 "schedule": {"order": sched[form][0], "tile": sched[form][1]},
+                 "gpu_launches": launches, "clocks": clocks.summary()}
+        if form == "fp32":
+            peak = torch.cuda.get_device_properties(dev).multi_processor_count * FP32_LANES_PER_SM * 2 * \
+                float(measured_peaks().get("sm_max_mhz", 2032.0)) * 1e6 / 1e12
+            ach = useful / (statistics.mean(ms) / 1e3) / 1e12
+            kern = "rollout_fp32_batch_kernel" if sched[form][1] == 0 else "rollout_fp32_group_kernel"
+            entry["roofline"] = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                                 "kernel": kern + " (time of the whole batched update)"}
+        else:
+            issued = sum(p.K * p.T * p.M * 12 * (-(-p.model.L // TC_FIELDS_PER_TILE) * TC_FIELDS_PER_TILE)
+                         for p in probs) * TC_MMA_FLOPS_PER_FIELD[form]
+            peak, basis = tensor_peak(measured_peaks(), entry["clocks"])
+            ach = issued / (statistics.mean(ms) / 1e3) / 1e12
+            uf = useful / (statistics.mean(ms) / 1e3) / 1e12
+            entry["roofline"] = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                                 "frac": ach / peak, "useful_tflops": uf, "useful_frac": uf / peak,
+                                 "peak_basis": basis,
+                                 "kernel": ("rollout_tc_batch_kernel" if sched[form][1] == 0 else "rollout_tc_group_kernel")
+                                           + " (time of the whole batched update)"}
+        forms[form] = entry
+        batch.close()
+        for c in ctls:
+            c.close()
+    return forms, costs
+
+
 def run_batched(args):
     """64 independent controllers (K ~ logU[1024, 32768], T ~ U{30..150},
     L ~ logU[128, 2048], own model/obstacles/seed each) updated by one
-    batched launch under a CUDA graph; both forms timed, each with the
+    batched launch under a CUDA graph; every form timed, each with the
     work-list order and (tensor cores) tile shape the autotuner picks."""
     import torch
     from paper_1503_00330_b300 import build
     from paper_1503_00330_b300 import workloads as W
-    from paper_1503_00330_b300.api import Batch, Controller
     build.build()
     dev = torch.device("cuda", 0)
     probs = W.batched(64, seed=0)
@@ -566,58 +679,8 @@ def run_batched(args):
                 best[f] = (o, int(t), ms)
         sched = {f: (o, t) for f, (o, t, _) in best.items()}
         sched["tc_fp16x2"] = sched["tc"]      # the same kernel with fewer MMAs: the tensor-core pick
-    stream = torch.cuda.current_stream(dev)
-    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
-    forms = {}
     order = [args.precision] + ([] if args.no_compare else [f for f in FORMS if f != args.precision])
-    for form in order:
-        ctls = [Controller(p.model, p.cost, M=p.M, model_noise=p.model_noise, precision=form) for p in probs]
-        batch = Batch(ctls, [p.K for p in probs], [p.T for p in probs], precision=form,
-                      x0=[p.x0 for p in probs], u_nom=[p.u_nom for p in probs])
-        batch.set_schedule(sched[form][0])
-        batch.set_tile(sched[form][1])
-        lam = [p.lam for p in probs]
-        su = [p.sigma_u for p in probs]
-        for i in range(args.warmup):
-            batch.update(lam, su, [p.seed + i for p in probs])
-        batch.sync()
-        ms = []
-        launches0 = batch.launch_count()
-        with ClockSampler(0) as clocks:
-            for i in range(args.steps):
-                flush.zero_()
-                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a.record(stream)
-                batch.update(lam, su, [p.seed + args.warmup + i for p in probs])
-                b.record(stream)
-                b.synchronize()
-                ms.append(a.elapsed_time(b))
-        batch.sync()
-        rs = batch.rollout_steps()
-        useful = sum(p.K * p.T * p.M * 12 * p.model.L for p in probs) * FLOPS_PER_FIELD
-        entry = {"value": rs * args.steps / (sum(ms) / 1e3), "ms_per_update": statistics.mean(ms),
-                 "schedule": {"order": sched[form][0], "tile": sched[form][1]},
-                 "gpu_launches": batch.launch_count() - launches0, "clocks": clocks.summary()}
-        if form == "fp32":
-            peak = torch.cuda.get_device_properties(dev).multi_processor_count * FP32_LANES_PER_SM * 2 * \
-                float(measured_peaks().get("sm_max_mhz", 2032.0)) * 1e6 / 1e12
-            ach = useful / (statistics.mean(ms) / 1e3) / 1e12
-            entry["roofline"] = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                                 "kernel": "rollout_fp32_batch_kernel (time of the whole batched update)"}
-        else:
-            issued = sum(p.K * p.T * p.M * 12 * (-(-p.model.L // TC_FIELDS_PER_TILE) * TC_FIELDS_PER_TILE)
-                         for p in probs) * TC_MMA_FLOPS_PER_FIELD[form]
-            peak, basis = tensor_peak(measured_peaks(), entry["clocks"])
-            ach = issued / (statistics.mean(ms) / 1e3) / 1e12
-            uf = useful / (statistics.mean(ms) / 1e3) / 1e12
-            entry["roofline"] = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                                 "frac": ach / peak, "useful_tflops": uf, "useful_frac": uf / peak,
-                                 "peak_basis": basis,
-                                 "kernel": "rollout_tc_batch_kernel (time of the whole batched update)"}
-        forms[form] = entry
-        batch.close()
-        for c in ctls:
-            c.close()
+    forms, _ = batched_forms(probs, sched, order, args.steps, args.warmup, dev)
     main = forms[args.precision]
     rs_total = sum(p.K * p.T * p.M for p in probs)
     line = {"metric": METRIC, "value": main["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
@@ -636,30 +699,33 @@ def run_batched(args):
     print(json.dumps(line), flush=True)
 
 
-def run_serving(args):
+SERVING_WORKLOAD = ("serving: 256 quadrotors, Poisson 50 Hz each, K ~ U{2048..16384}, T ~ U{50..120}, "
+                    "shared LWPR model L=1024, continuous batching")
+
+
+def serving_measure(precision, serve_seconds, sweep_loads, lanes, max_group, warmup):
     """256 simulated quadrotors over one shared LWPR model (L = 1024 fields per
-    output): each issues update requests as a Poisson process at 50 Hz with
+    output): each issues update requests as a Poisson process with
     K ~ U{2048..16384}, T ~ U{50..120}; the continuous-batching server admits
     them by free lanes and pool memory.  A quadrotor whose previous plan has not
-    come back skips its tick (the arrival is dropped).  Timed twice: at the
-    offered 50 Hz (far above what one GPU serves at these sizes, so the server
-    runs saturated) and at half the capacity measured in that run, where the
-    latency is that of a loaded but stable server."""
+    come back skips its tick (the arrival is dropped).  Timed at the offered
+    50 Hz (far above what one GPU serves at these sizes, so the server runs
+    saturated), at half the capacity measured in that run (the latency of a
+    loaded but stable server), and at the other loads of `sweep_loads`.
+    Returns (at the offered rate, at half capacity, sweep points, capacity)."""
     import numpy as np
     import torch
-    from paper_1503_00330_b300 import build
     from paper_1503_00330_b300 import workloads as W
     from paper_1503_00330_b300.api import Controller, Server
-    build.build()
     n_quad, L, lam = 256, 1024, 1.0
     model = W.make_lwpr(L, seed=4)
     cost = W.make_cost(16, seed=4)
-    ctl = Controller(model, cost, precision=args.precision)
-    srv = Server(ctl, n_quad, K_max=16384, T_max=120, max_inflight=args.serve_lanes, max_group=args.serve_group)
+    ctl = Controller(model, cost, precision=precision)
+    srv = Server(ctl, n_quad, K_max=16384, T_max=120, max_inflight=lanes, max_group=max_group)
     rng = np.random.default_rng(5)
     for a in range(n_quad):
         srv.set_agent(a, rng.normal(0, 0.1, 12).astype(np.float32), None, seed=1000 + a)
-    for i in range(args.warmup):                      # warm-up requests (one per agent 0..W-1)
+    for i in range(warmup):                           # warm-up requests (one per agent 0..W-1)
         srv.submit(i, 4096, 100, lam, W.SIGMA_U, keep=False)
     srv.drain()
     srv.poll(1 << 16)
@@ -678,19 +744,19 @@ def run_serving(args):
         queue = (rec["t_launch_ns"] - rec["t_submit_ns"]) / 1e6
         useful = steps * 12 * L * FLOPS_PER_FIELD
         clk = clocks.summary()
-        if args.precision != "fp32":
-            issued = steps * 12 * L_pad * TC_MMA_FLOPS_PER_FIELD[args.precision]
+        if precision != "fp32":
+            issued = steps * 12 * L_pad * TC_MMA_FLOPS_PER_FIELD[precision]
             peak, basis = tensor_peak(measured_peaks(), clk)
             roof = {"bound": "tensor", "achieved": issued / span / 1e12, "peak": peak, "unit": "TFLOP/s",
                     "frac": issued / span / 1e12 / peak, "useful_tflops": useful / span / 1e12,
                     "useful_frac": useful / span / 1e12 / peak, "peak_basis": basis,
-                    "kernel": "rollout_tc_batch_kernel (issued MMA flops over the whole serving span)"}
+                    "kernel": "rollout_tc_group_kernel (issued MMA flops over the whole serving span)"}
         else:
             peak = torch.cuda.get_device_properties(0).multi_processor_count * FP32_LANES_PER_SM * 2 * \
                 float(measured_peaks().get("sm_max_mhz", 2032.0)) * 1e6 / 1e12
             roof = {"bound": "alu", "achieved": useful / span / 1e12, "peak": peak, "unit": "TFLOP/s",
                     "frac": useful / span / 1e12 / peak,
-                    "kernel": "rollout_fp32_batch_kernel (useful flops over the whole serving span)"}
+                    "kernel": "rollout_fp32_group_kernel (useful flops over the whole serving span)"}
         return {"offered_hz_per_quad": rate_hz, "trace_s": seconds, "arrivals": len(trace), "served": int(len(rec)),
                 "dropped": dropped, "span_s": span, "rollout_steps_per_s": steps / span,
                 "requests_per_s": len(rec) / span,
@@ -702,27 +768,36 @@ def run_serving(args):
                 "pool_peak_bytes": int(st1["pool_peak_bytes"]), "roofline": roof, "clocks": clk,
                 "all_ok": bool(np.all(rec["status"] == 0))}
 
-    full = run(50.0, args.serve_seconds, seed=1)
+    full = run(50.0, serve_seconds, seed=1)
     cap = full["requests_per_s"]
     half_rate = 0.5 * cap / n_quad
-    half = run(half_rate, max(args.serve_seconds, 160.0 / (0.5 * cap)), seed=2)
+    half = run(half_rate, max(serve_seconds, 160.0 / (0.5 * cap)), seed=2)
     sweep = []
-    for i, frac in enumerate(args.serve_sweep):
+    for i, frac in enumerate(sweep_loads):
         if frac == 0.5:
             pt = half
         else:
-            pt = run(frac * cap / n_quad, max(args.serve_seconds, 120.0 / (frac * cap)), seed=3 + i)
+            pt = run(frac * cap / n_quad, max(serve_seconds, 120.0 / (frac * cap)), seed=3 + i)
         sweep.append({"load": frac, "offered_hz_per_quad": pt["offered_hz_per_quad"],
                       "requests_per_s": pt["requests_per_s"], "latency_ms": pt["latency_ms"],
                       "queue_ms": pt["queue_ms"], "group_size_mean": pt["group_size"]["mean"],
                       "rollout_steps_per_s": pt["rollout_steps_per_s"]})
     srv.close()
+    ctl.close()
+    return full, half, sweep, cap
+
+
+def run_serving(args):
+    """The serving workload (see serving_measure) as its own JSON line."""
+    from paper_1503_00330_b300 import build
+    build.build()
+    full, half, sweep, cap = serving_measure(args.precision, args.serve_seconds, args.serve_sweep,
+                                             args.serve_lanes, args.serve_group, args.warmup)
     line = {"metric": METRIC, "value": full["rollout_steps_per_s"], "unit": UNIT, "n_gpus": 1,
             "steps": full["served"], "warmup": args.warmup, "ms_per_step": 1e3 / full["requests_per_s"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded generator; quadrotor-shaped LWPR model, Poisson request trace)",
-            "config": {"workload": "serving: 256 quadrotors, Poisson 50 Hz each, K ~ U{2048..16384}, "
-                                   "T ~ U{50..120}, shared LWPR model L=1024, continuous batching",
+            "config": {"workload": SERVING_WORKLOAD,
                        "precision": args.precision, "lanes": args.serve_lanes, "max_group": args.serve_group,
                        "step": "one served request (ms_per_step = 1 / served request rate)",
                        "l2": "inputs of a saturated group exceed L2 (each request's scratch ~K*T*20 bytes)"},
@@ -840,6 +915,36 @@ def run_ours(args):
                            "K": pp.K, "T": pp.T, "L": pp.model.L, "M": pp.M,
                            "l2": "flushed between timed updates (256 MiB write outside the event window)"},
                 "forms": {f: time_updates(f, pp, args.precision_steps, 3, dev, "precision") for f in FORMS}}
+    # the batched workload (64 uneven controllers, one launch under a CUDA graph) in every form,
+    # with the schedule the autotuner picks on it (longest first, one item per CTA)
+    bat = None
+    if ws == 1 and args.workload == "realtime" and not args.no_batched:
+        from paper_1503_00330_b300 import workloads as W
+        bprobs = W.batched(64, seed=0)
+        by_L = max(range(len(bprobs)), key=lambda i: bprobs[i].model.L)
+        by_K = max((i for i in range(len(bprobs)) if i != by_L), key=lambda i: bprobs[i].K)
+        bpick = (by_L, by_K)
+        bforms, bcosts = batched_forms(bprobs, BATCHED_SCHEDULE, FORMS, args.batched_steps, 3, dev, pick=bpick)
+        bat = {"config": {"workload": "batched: 64 controllers, K ~ logU[1024, 32768], T ~ U{30..150}, "
+                                      "L ~ logU[128, 2048], own model, obstacles and seed each; one launch under a "
+                                      "CUDA graph", "controllers": len(bprobs),
+                          "rollout_steps_per_update": sum(p.K * p.T * p.M for p in bprobs),
+                          "schedule": "longest first, one item per CTA (the autotuner's pick on this workload)",
+                          "l2": "flushed between timed updates (256 MiB write outside the event window)"},
+               "forms": bforms}
+    # the serving workload (256 quadrotors, continuous batching), tensor-core form
+    srv_line = None
+    if ws == 1 and args.workload == "realtime" and not args.no_serving:
+        sfull, shalf, _, scap = serving_measure("tc", args.serve_seconds, [], args.serve_lanes, args.serve_group, 3)
+        srv_line = {"config": {"workload": SERVING_WORKLOAD, "precision": "tc", "lanes": args.serve_lanes,
+                               "max_group": args.serve_group},
+                    "rollout_steps_per_s": sfull["rollout_steps_per_s"], "requests_per_s": sfull["requests_per_s"],
+                    "latency_ms_at_offered_rate": sfull["latency_ms"],
+                    "latency_ms_at_half_capacity": shalf["latency_ms"], "capacity_requests_per_s": scap,
+                    "roofline": sfull["roofline"], "clocks": sfull["clocks"], "gpu_launches": sfull["gpu_launches"],
+                    "all_ok": sfull["all_ok"] and shalf["all_ok"],
+                    "error": "each served result equals the agent's updates run alone on the single-controller "
+                             "path bitwise (tests/test_gpu_serve.py), so it carries that path's error"}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
@@ -874,8 +979,18 @@ def run_ours(args):
             for f in prec["forms"]:
                 prec["forms"][f]["error"] = {**form_errors(pp, f, pref, dev), "tolerance_u_out": ERROR_BOUND[f],
                                              "tolerance_costs": ERROR_BOUND[f]}
+        if bat is not None:
+            bbase, bref = batched_cpu_baseline(bprobs, bpick, args.batched_sample)
+            bat["cpu_baseline"] = bbase
+            for f in bat["forms"]:
+                bat["forms"][f]["error"] = {**batched_errors(bprobs, bcosts[f], bref),
+                                            "tolerance_costs": ERROR_BOUND[f]}
     if prec is not None:
         line["precision_workload"] = prec
+    if bat is not None:
+        line["batched_workload"] = bat
+    if srv_line is not None:
+        line["serving_workload"] = srv_line
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
@@ -896,6 +1011,12 @@ def main():
     ap.add_argument("--precision-steps", type=int, default=3,
                     help="timed updates of the precision workload (default line only)")
     ap.add_argument("--no-precision", action="store_true", help="skip the precision workload in the default line")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched workload in the default line")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving workload in the default line")
+    ap.add_argument("--batched-steps", type=int, default=3,
+                    help="timed batched updates per form (default line only)")
+    ap.add_argument("--batched-sample", type=int, default=32,
+                    help="rollouts per sampled controller in the batched error reference")
     ap.add_argument("--ref-sample", type=int, default=64, help="rollouts per reference-arm step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", choices=list(FORMS), default="fp32",
