@@ -89,7 +89,7 @@ def _serve_all(srv, rounds, agents=None):
     return out
 
 
-@pytest.mark.parametrize("form", ["fp32", "tc"])
+@pytest.mark.parametrize("form", ["fp32", "tc", "tc_fp16x2"])
 def test_served_equals_alone_single_controller_path(form):
     ctl = _controller(form)
     srv = _server(ctl, len(AGENTS), max_inflight=3, max_group=4)
@@ -191,7 +191,7 @@ def test_measured_state_and_busy_agent():
     srv.close()
 
 
-@pytest.mark.parametrize("form", ["fp32", "tc"])
+@pytest.mark.parametrize("form", ["fp32", "tc", "tc_fp16x2"])
 def test_served_update_against_oracle(oracle, form):
     from paper_1503_00330_b300.api import update_seed
     ctl = _controller(form)
@@ -206,7 +206,8 @@ def test_served_update_against_oracle(oracle, form):
         scale = np.maximum(np.abs(uref).max(0), np.sqrt(SU.astype(np.float64) / K))
         eu = np.abs(got[(a, 0)][0] - uref).max(0) / scale
         ec = np.max(np.abs(got[(a, 0)][1] - cref) / cref)
-        assert np.all(eu <= 1e-5) and ec <= 1e-5, (a, eu, ec)
+        tol = 2e-3 if form == "tc_fp16x2" else 1e-5     # the two-product form's stated bound
+        assert np.all(eu <= tol) and ec <= tol, (a, eu, ec)
 
 
 def test_trace_replay():
