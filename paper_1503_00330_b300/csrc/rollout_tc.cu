@@ -23,9 +23,9 @@
 // Roles (one CTA per SM, 128 slots, 320 threads):
 //   warp 0:        producer (one elected lane issues) -- 1-D bulk copies
 //                  (TMA) of the pre-packed coefficient chunks (8 KB each,
-//                  11 per tile of 128 fields) in two groups per tile
-//                  (chunks 0-5 and 6-10, one copy and one barrier pair each)
-//                  into a ring that holds one tile, and of the per-field
+//                  11 per tile of 128 fields) in NGRP groups per tile
+//                  (one copy and one barrier pair each) into a ring that
+//                  holds one tile, and of the per-field
 //                  constants (cy, sigma^2) into a 4-deep constant ring;
 //   warp 1:        MMA issuer (the whole warp runs the loop, one elected
 //                  lane issues) -- per tile of 128 fields, 30 MMAs (M=128,
@@ -61,15 +61,19 @@ constexpr int BM = TC_SLOTS;            // rollout slots per CTA (MMA M)
 constexpr int TNF = TC_TILE_FIELDS;     // fields per tile (MMA N)
 constexpr int KF = TC_KF;               // feature columns of phi (S GEMM K)
 constexpr int NCH = TC_CHUNKS_PER_TILE; // chunks per tile
-// The chunk ring holds one tile: copy group A = chunks 0..GA-1 in slots
-// 0..GA-1, group B = the rest; each group is one bulk copy and one full/empty
-// barrier pair, so every slot, descriptor offset and barrier of the MMA
-// issuer's per-tile sequence is a compile-time constant.
+// The chunk ring holds one tile, in NGRP copy groups of consecutive chunks
+// (group x = chunks GRP_BEGIN[x] .. GRP_BEGIN[x + 1] - 1, in the ring slots of
+// the same index); each group is one bulk copy and one full/empty barrier
+// pair, so every slot, descriptor offset and barrier of the MMA issuer's
+// per-tile sequence is a compile-time constant.  A group is refilled for the
+// next tile as soon as this tile's MMAs that read it are done, so the copy
+// has the other groups' MMAs to land in.
 constexpr int NSLOT = NCH;              // chunk slots in the ring (one tile)
-constexpr int GA = 6;                   // chunks of copy group A (the N = 256 pair and K steps 1-4)
-constexpr int GB = NCH - GA;            // chunks of copy group B (K steps 5-9)
+// Two groups, chunks 0-5 and 6-10 (three groups of 4/4/3 and four of 3/3/3/2
+// chunks measured the same: the refill of a group lands in time either way)
 constexpr int NGRP = 2;
-static_assert(GA >= 2 && GB >= 1, "group A holds the N = 256 chunk pair");
+__host__ __device__ constexpr int grp_begin(int x) { return x == 0 ? 0 : x == 1 ? 6 : NCH; }
+static_assert(grp_begin(1) >= 2 && grp_begin(NGRP) == NCH, "group 0 holds the N = 256 chunk pair");
 constexpr int NCONST = 4;
 constexpr int NEPI = 8;                 // epilogue warps
 constexpr int NTHREADS = (2 + NEPI) * 32;
@@ -297,7 +301,8 @@ __device__ __forceinline__ void tc_setup(const TcSmem &S, uint32_t ncl)
 // position and barrier phase: tile g uses constant slot g & 3, chunk groups
 // A and B at phase g & 1, accumulator buffer g & 1.
 struct TcProducer {
-    long long g = 0, na = 0, nb = 0;   // tiles started; A and B groups issued
+    long long g = 0;              // tiles started
+    long long n[NGRP] = {};       // copies of each group issued
 };
 struct TcIssuer {
     long long g = 0, ts = 0;
@@ -307,9 +312,9 @@ struct TcIssuer {
 // Producer (all of warp 0; one elected lane issues the copies) for one work
 // item -- the tiles of outputs o_begin .. o_begin + n_out - 1, every step --;
 // false after a timeout.  Per tile: its constants into the 4-deep constant
-// ring, then copy group A (chunks 0..GA-1, one bulk copy) once the MMAs of the
-// previous tile's group A are done, then group B likewise.  A tile's chunks
-// are contiguous in global memory, so each group is one copy.
+// ring, then each copy group once the MMAs of the previous tile that read the
+// group's slots are done.  A tile's chunks are contiguous in global memory, so
+// each group is one copy.
 template <bool PREDICT>
 __device__ bool tc_producer_item(const TcArgs &a, const TcSmem &S, TcProducer &P, int o_begin, int n_out)
 {
@@ -338,23 +343,20 @@ __device__ bool tc_producer_item(const TcArgs &a, const TcSmem &S, TcProducer &P
             __syncwarp();
             P.g = gt + 1;
             const uint32_t prev = (uint32_t)((gt - 1) & 1);   // phase of the previous tile's groups
-            if (gt >= 1) ok = __all_sync(0xffffffffu, mbar_wait_bounded(&empty[0], prev, abort_flag));
-            if (!ok) break;
-            if (elect_one()) {
-                mbar_arrive_expect_tx(&full[0], (uint32_t)(GA * TC_CHUNK_BYTES));
-                bulk_g2s(smem + OFF_RING, src, (uint32_t)(GA * TC_CHUNK_BYTES), &full[0]);
+#pragma unroll
+            for (int x = 0; x < NGRP; ++x) {
+                if (gt >= 1) ok = __all_sync(0xffffffffu, mbar_wait_bounded(&empty[x], prev, abort_flag));
+                if (!ok) break;
+                const int c0 = grp_begin(x), nc = grp_begin(x + 1) - grp_begin(x);
+                if (elect_one()) {
+                    mbar_arrive_expect_tx(&full[x], (uint32_t)(nc * TC_CHUNK_BYTES));
+                    bulk_g2s(smem + OFF_RING + c0 * TC_CHUNK_BYTES, src + c0 * TC_CHUNK_BYTES,
+                             (uint32_t)(nc * TC_CHUNK_BYTES), &full[x]);
+                }
+                __syncwarp();
+                P.n[x] = gt + 1;
             }
-            __syncwarp();
-            P.na = gt + 1;
-            if (gt >= 1) ok = __all_sync(0xffffffffu, mbar_wait_bounded(&empty[1], prev, abort_flag));
             if (!ok) break;
-            if (elect_one()) {
-                mbar_arrive_expect_tx(&full[1], (uint32_t)(GB * TC_CHUNK_BYTES));
-                bulk_g2s(smem + OFF_RING + GA * TC_CHUNK_BYTES, src + GA * TC_CHUNK_BYTES,
-                         (uint32_t)(GB * TC_CHUNK_BYTES), &full[1]);
-            }
-            __syncwarp();
-            P.nb = gt + 1;
         }
     }
     return ok;
@@ -386,14 +388,31 @@ __device__ __forceinline__ void tc_issue_chunks(uint32_t dS, uint64_t a_hi, uint
     }
 }
 
+// The copy groups of one tile from group X on: wait for the group's chunks,
+// issue their MMAs, release the group's slots (the commit arrives when those
+// MMAs are done); false after a timeout.
+template <int X, int QP>
+__device__ __forceinline__ bool tc_issue_groups(const TcSmem &S, uint32_t dS, uint64_t a_hi, uint64_t a_lo,
+                                                uint64_t b0, uint32_t idesc, uint32_t idesc_wide, uint32_t ph)
+{
+    if constexpr (X < NGRP) {
+        if (!__all_sync(0xffffffffu, mbar_wait_bounded(&S.full[X], ph, S.abort_flag))) return false;
+        tc_fence_after();
+        tc_issue_chunks<grp_begin(X), grp_begin(X + 1), QP>(dS, a_hi, a_lo, b0, idesc, idesc_wide);
+        commit_elect(&S.empty[X]);
+        return tc_issue_groups<X + 1, QP>(S, dS, a_hi, a_lo, b0, idesc, idesc_wide, ph);
+    }
+    return true;
+}
+
 // MMA issuer (all of warp 1) for one work item; false after a timeout.  The
 // whole warp runs the loop, so every counter and descriptor is warp-uniform,
 // and the lane elect.sync picks issues the MMAs and commits.  (The issuing
 // warp shares its scheduler with two epilogue warps, so every instruction of
 // this loop costs issue slots on the critical path: the per-tile sequence
-// below has no per-chunk bookkeeping.)  Per tile: wait for group A, its 18
-// MMAs (the N = 256 triple and K steps 1-4), release A; wait for group B, its
-// 15 MMAs (K steps 5-9), release B; signal the accumulator.
+// below has no per-chunk bookkeeping.)  Per tile: wait for a free accumulator,
+// then for each copy group its MMAs (tc_issue_groups), then signal the
+// accumulator.
 template <bool PREDICT, int QP>
 __device__ bool tc_issuer_item(const TcArgs &a, const TcSmem &S, uint32_t tbase, TcIssuer &I, int n_out)
 {
@@ -423,17 +442,10 @@ __device__ bool tc_issuer_item(const TcArgs &a, const TcSmem &S, uint32_t tbase,
             if (g >= 2)
                 ok = __all_sync(0xffffffffu,
                                 mbar_wait_bounded(&acc_empty[buf], (uint32_t)(((g >> 1) - 1) & 1), abort_flag));
-            if (ok) ok = __all_sync(0xffffffffu, mbar_wait_bounded(&full[0], ph, abort_flag));
             if (!ok) break;
-            tc_fence_after();
             const uint32_t dS = tbase + buf * 256;   // S: columns 0-127, Y: 128-255
-            tc_issue_chunks<1, GA, QP>(dS, a_hi, a_lo, b0, idesc, idesc_wide);
-            commit_elect(&empty[0]);
-            ok = __all_sync(0xffffffffu, mbar_wait_bounded(&full[1], ph, abort_flag));
+            ok = tc_issue_groups<0, QP>(S, dS, a_hi, a_lo, b0, idesc, idesc_wide, ph);
             if (!ok) break;
-            tc_fence_after();
-            tc_issue_chunks<GA, NCH, QP>(dS, a_hi, a_lo, b0, idesc, idesc_wide);
-            commit_elect(&empty[1]);
             commit_elect(&acc_full[buf]);
         }
     }
@@ -731,8 +743,9 @@ __device__ __forceinline__ void tc_drain(const TcArgs &a, const TcSmem &S, const
     if (warp == 0 && lane == 0) {
         // keep the CTA alive until every copy issued has landed: the last
         // phase of each group barrier, and of the last constant slots
-        if (P.na > 0 && !mbar_wait_drain(&S.full[0], (uint32_t)((P.na - 1) & 1))) atomicOr(a.err, DEVERR_TIMEOUT_DRAIN);
-        if (P.nb > 0 && !mbar_wait_drain(&S.full[1], (uint32_t)((P.nb - 1) & 1))) atomicOr(a.err, DEVERR_TIMEOUT_DRAIN);
+        for (int x = 0; x < NGRP; ++x)
+            if (P.n[x] > 0 && !mbar_wait_drain(&S.full[x], (uint32_t)((P.n[x] - 1) & 1)))
+                atomicOr(a.err, DEVERR_TIMEOUT_DRAIN);
         for (long long g = (P.g > NCONST ? P.g - NCONST : 0); g < P.g; ++g)
             if (!mbar_wait_drain(&S.const_full[g & 3], (uint32_t)((g >> 2) & 1))) atomicOr(a.err, DEVERR_TIMEOUT_DRAIN);
     }
