@@ -327,6 +327,9 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# Timed steps enqueued back to back before their stage times are read (at most the
+# context's ring of stage-event sets, 64)
+TIMING_CHUNK = 32
 # Stated accuracy of each form against the FP64 oracle (u_out per channel and costs, relative)
 ERROR_BOUND = {"fp32": 1e-5, "tc": 2e-3, "tc_fp16x2": 2e-3}
 FORMS = ("fp32", "tc", "tc_fp16x2")
@@ -498,22 +501,29 @@ def time_form(precision, p, args, dev):
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
     rollout_ms, step_ms, scan_ms, merge_ms, plant_ms = [], [], [], [], []
-    sampler = ClockSampler(dev.index or 0)
-    for i in range(args.warmup + args.steps):
-        if i == args.warmup:
-            sampler.__enter__()
-        flush.zero_()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        pa, pb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
+    for i in range(args.warmup):
         ctl.update(x0, ua, K, T, p.lam, p.sigma_u, p.seed + i, u_out=ub, costs_out=costs)
-        pa.record(stream)
         ctl.rh_advance(x0, ub, ua)
-        pb.record(stream)
-        b.record(stream)
-        st = ctl.stage_times()
-        b.synchronize()
-        if i >= args.warmup:
+    ctl.sync()
+    sampler = ClockSampler(dev.index or 0)
+    sampler.__enter__()
+    for c0 in range(0, args.steps, TIMING_CHUNK):     # enqueued back to back, as in the headline loop
+        c1 = min(args.steps, c0 + TIMING_CHUNK)
+        evs = []
+        for i in range(c0, c1):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            pa, pb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            ctl.update(x0, ua, K, T, p.lam, p.sigma_u, p.seed + args.warmup + i, u_out=ub, costs_out=costs)
+            pa.record(stream)
+            ctl.rh_advance(x0, ub, ua)
+            pb.record(stream)
+            b.record(stream)
+            evs.append((a, b, pa, pb))
+        for i, (a, b, pa, pb) in zip(range(c0, c1), evs):
+            st = ctl.stage_times(back=c1 - 1 - i)
+            b.synchronize()
             rollout_ms.append(st[0])
             scan_ms.append(st[1])
             merge_ms.append(st[2])
@@ -555,18 +565,23 @@ def time_updates(precision, p, steps, warmup, dev, workload):
     rollout_ms, step_ms, scan_ms, merge_ms = [], [], [], []
     launches0 = ctl.launch_count()
     with ClockSampler(dev.index or 0) as clocks:
-        for i in range(steps):
-            flush.zero_()
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            ctl.update(x0, un, K, T, p.lam, p.sigma_u, p.seed + warmup + i, u_out=u, costs_out=costs)
-            b.record(stream)
-            st = ctl.stage_times()
-            b.synchronize()
-            rollout_ms.append(st[0])
-            scan_ms.append(st[1])
-            merge_ms.append(st[2])
-            step_ms.append(a.elapsed_time(b))
+        for c0 in range(0, steps, TIMING_CHUNK):       # enqueued back to back, as in the headline loop
+            c1 = min(steps, c0 + TIMING_CHUNK)
+            evs = []
+            for i in range(c0, c1):
+                flush.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                ctl.update(x0, un, K, T, p.lam, p.sigma_u, p.seed + warmup + i, u_out=u, costs_out=costs)
+                b.record(stream)
+                evs.append((a, b))
+            for i, (a, b) in zip(range(c0, c1), evs):
+                st = ctl.stage_times(back=c1 - 1 - i)
+                b.synchronize()
+                rollout_ms.append(st[0])
+                scan_ms.append(st[1])
+                merge_ms.append(st[2])
+                step_ms.append(a.elapsed_time(b))
     launches = ctl.launch_count() - launches0
     ctl.sync()
     ctl.close()
@@ -853,15 +868,21 @@ def run_ours(args):
     torch.cuda.synchronize()
     launches0 = ctl.launch_count()
     with ClockSampler(local) as clocks:
-        for i in range(args.steps):
-            flush.zero_()                               # L2 flush, outside the event window
-            ev[i][0].record(stream)
-            rh_step(args.warmup + i, pev[i])
-            ev[i][1].record(stream)
-            st = ctl.stage_times()                      # waits for this update
-            rollout_ms.append(st[0])
-            scan_ms.append(st[1])
-            merge_ms.append(st[2])
+        # the steps of a chunk are enqueued back to back (no host sync between them, so
+        # no host latency inside an event window); the context's ring of stage events
+        # then gives each update's kernel times
+        for c0 in range(0, args.steps, TIMING_CHUNK):
+            c1 = min(args.steps, c0 + TIMING_CHUNK)
+            for i in range(c0, c1):
+                flush.zero_()                           # L2 flush, outside the event window
+                ev[i][0].record(stream)
+                rh_step(args.warmup + i, pev[i])
+                ev[i][1].record(stream)
+            for i in range(c0, c1):
+                st = ctl.stage_times(back=c1 - 1 - i)
+                rollout_ms.append(st[0])
+                scan_ms.append(st[1])
+                merge_ms.append(st[2])
         torch.cuda.synchronize()
     if dist is not None:
         dist.barrier()

@@ -227,11 +227,21 @@ int pi_update_host(pi_ctx *ctx, const float *x0, const float *u_nominal, int K, 
  *                           must not overlap u_out */
 int pi_rh_advance(pi_ctx *ctx, float *x0, const float *u_out, int T, float *u_nom_next);
 
-/* Per-kernel timing of pi_update with CUDA events on the context's stream
- * (off by default).  pi_stage_times waits for the last timed update and writes
- * ms[0] = rollout kernel, ms[1] = cost-to-go/LSE kernel, ms[2] = merge kernel. */
+/* Per-kernel timing of pi_update (and pi_update_noalloc) with CUDA events on
+ * the context's stream (off by default).  The context keeps the events of the
+ * last PI2RH_TIMING_RING timed updates, so a caller can enqueue many updates
+ * back to back and read their times afterwards.
+ *   pi_stage_times     waits for the last timed update and writes ms[0] =
+ *                      rollout kernel, ms[1] = cost-to-go/LSE kernel, ms[2] =
+ *                      merge kernel (milliseconds)
+ *   pi_stage_times_at  the same for the timed update `back` calls before the
+ *                      last (back = 0 is the last); INVALID_ARG unless
+ *                      0 <= back < min(timed updates so far, PI2RH_TIMING_RING)
+ * Host memory ms[3]; both block until that update's kernels have finished. */
+#define PI2RH_TIMING_RING 64
 int pi_set_timing(pi_ctx *ctx, int enable);
 int pi_stage_times(pi_ctx *ctx, float *ms);
+int pi_stage_times_at(pi_ctx *ctx, int back, float *ms);
 
 /* ---------------------------------------------------------------------------
  * Batched form: many independent controllers of uneven size (own model, cost,

@@ -101,6 +101,7 @@ _SIGS = {
     "pi_rh_advance": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _vp]),
     "pi_set_timing": (ctypes.c_int, [_vp, ctypes.c_int]),
     "pi_stage_times": (ctypes.c_int, [_vp, _fp]),
+    "pi_stage_times_at": (ctypes.c_int, [_vp, ctypes.c_int, _fp]),
     "pi_debug_tc_gemm": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _vp]),
     "pi_debug_wait_timeout": (ctypes.c_int, [_vp, ctypes.c_int64]),
     "pi_batch_create": (ctypes.c_int, [ctypes.POINTER(BatchItemC), ctypes.c_int, ctypes.c_int, ctypes.POINTER(_vp)]),

@@ -125,10 +125,11 @@ class Controller:
     def set_timing(self, enable: bool = True):
         check(self._lib.pi_set_timing(self._h, 1 if enable else 0))
 
-    def stage_times(self):
-        """(rollout_ms, scan_ms, merge_ms) of the last timed update."""
+    def stage_times(self, back: int = 0):
+        """(rollout_ms, scan_ms, merge_ms) of the timed update `back` calls before the
+        last (0 = the last; the context keeps the last PI2RH_TIMING_RING = 64)."""
         ms = (ctypes.c_float * 3)()
-        check(self._lib.pi_stage_times(self._h, ms))
+        check(self._lib.pi_stage_times_at(self._h, int(back), ms))
         return tuple(float(v) for v in ms)
 
     def sync(self):

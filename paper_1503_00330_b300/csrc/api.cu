@@ -176,8 +176,10 @@ int launch_rollouts(pi_ctx *c, const float *x0, const float *u_nom, int K, int T
     return PI_OK;
 }
 
+// ev_mid (may be null) is recorded between the scan and the merge launches.
 int launch_reduce(pi_ctx *c, const float *cost, const float *phi, const float4 *eps,
-                  const float *u_nom, int K, int T, float lambda, float *u_out, float *costs_out)
+                  const float *u_nom, int K, int T, float lambda, float *u_out, float *costs_out,
+                  cudaEvent_t ev_mid = nullptr)
 {
     NvtxRange nv("pi2rh cost-to-go + weighted average");
     const double inv_lam_log2e = 1.4426950408889634074 / (double)lambda;
@@ -185,7 +187,7 @@ int launch_reduce(pi_ctx *c, const float *cost, const float *phi, const float4 *
                             c->stream),
             "scan kernel launch");
     c->launches++;
-    if (c->timing) PI_CUDA(cudaEventRecord(c->ev[2], c->stream), "event record");
+    if (ev_mid) PI_CUDA(cudaEventRecord(ev_mid, c->stream), "event record");
     PI_CUDA(launch_lse_merge(c->d_part, scan_blocks(K), T, inv_lam_log2e, u_nom, u_out, c->stream),
             "merge kernel launch");
     c->launches++;
@@ -199,8 +201,9 @@ void free_ctx_memory(pi_ctx *c)
     for (void *p : ptrs)
         if (p) cudaFreeAsync(p, c->stream);
     cudaStreamSynchronize(c->stream);
-    for (cudaEvent_t &e : c->ev)
-        if (e) cudaEventDestroy(e);
+    for (auto &set : c->ev)
+        for (cudaEvent_t &e : set)
+            if (e) cudaEventDestroy(e);
 }
 
 }  // namespace
@@ -489,11 +492,16 @@ int pi_update(pi_ctx *c, const float *x0, const float *u_nom, int K, int T, floa
     DeviceGuard dg(c->device);
     PI_CUDA(dg.err, "cudaSetDevice");
     PI_TRY(ensure_scratch(c, K, T));
-    if (c->timing) PI_CUDA(cudaEventRecord(c->ev[0], c->stream), "event record");
+    cudaEvent_t *ev = timing_slot(c);
+    if (ev) PI_CUDA(cudaEventRecord(ev[0], c->stream), "event record");
     PI_TRY(launch_rollouts(c, x0, u_nom, K, T, sigma_u, seed, c->d_cost, c->d_eps, c->d_phi));
-    if (c->timing) PI_CUDA(cudaEventRecord(c->ev[1], c->stream), "event record");
-    PI_TRY(launch_reduce(c, c->d_cost, c->d_phi, c->d_eps, u_nom, K, T, lambda, u_out, costs_out));
-    if (c->timing) PI_CUDA(cudaEventRecord(c->ev[3], c->stream), "event record");
+    if (ev) PI_CUDA(cudaEventRecord(ev[1], c->stream), "event record");
+    PI_TRY(launch_reduce(c, c->d_cost, c->d_phi, c->d_eps, u_nom, K, T, lambda, u_out, costs_out,
+                         ev ? ev[2] : nullptr));
+    if (ev) {
+        PI_CUDA(cudaEventRecord(ev[3], c->stream), "event record");
+        ++c->n_timed;
+    }
     return PI_OK;
 }
 
@@ -525,24 +533,31 @@ int pi_set_timing(pi_ctx *c, int enable)
     if (!c) return fail(PI_ERR_INVALID_ARG, "ctx is NULL");
     DeviceGuard dg(c->device);
     PI_CUDA(dg.err, "cudaSetDevice");
-    if (enable && !c->ev[0])
-        for (cudaEvent_t &e : c->ev) PI_CUDA(cudaEventCreate(&e), "cudaEventCreate");
+    if (enable && !c->ev[0][0])
+        for (auto &set : c->ev)
+            for (cudaEvent_t &e : set) PI_CUDA(cudaEventCreate(&e), "cudaEventCreate");
     c->timing = enable != 0;
     return PI_OK;
 }
 
-int pi_stage_times(pi_ctx *c, float *ms)
+int pi_stage_times_at(pi_ctx *c, int back, float *ms)
 {
     if (!c || !ms) return fail(PI_ERR_INVALID_ARG, "bad argument");
-    if (!c->ev[0]) return fail(PI_ERR_INVALID_ARG, "timing is not enabled");
+    if (!c->ev[0][0]) return fail(PI_ERR_INVALID_ARG, "timing is not enabled");
+    const uint64_t avail = c->n_timed < (uint64_t)PI2RH_TIMING_RING ? c->n_timed : (uint64_t)PI2RH_TIMING_RING;
+    if (back < 0 || (uint64_t)back >= avail)
+        return fail(PI_ERR_INVALID_ARG, "no timed update %d calls back (%llu kept)", back, (unsigned long long)avail);
+    cudaEvent_t *ev = c->ev[(c->n_timed - 1 - (uint64_t)back) % PI2RH_TIMING_RING];
     DeviceGuard dg(c->device);
     PI_CUDA(dg.err, "cudaSetDevice");
-    PI_CUDA(cudaEventSynchronize(c->ev[3]), "cudaEventSynchronize");
-    PI_CUDA(cudaEventElapsedTime(&ms[0], c->ev[0], c->ev[1]), "cudaEventElapsedTime");
-    PI_CUDA(cudaEventElapsedTime(&ms[1], c->ev[1], c->ev[2]), "cudaEventElapsedTime");
-    PI_CUDA(cudaEventElapsedTime(&ms[2], c->ev[2], c->ev[3]), "cudaEventElapsedTime");
+    PI_CUDA(cudaEventSynchronize(ev[3]), "cudaEventSynchronize");
+    PI_CUDA(cudaEventElapsedTime(&ms[0], ev[0], ev[1]), "cudaEventElapsedTime");
+    PI_CUDA(cudaEventElapsedTime(&ms[1], ev[1], ev[2]), "cudaEventElapsedTime");
+    PI_CUDA(cudaEventElapsedTime(&ms[2], ev[2], ev[3]), "cudaEventElapsedTime");
     return PI_OK;
 }
+
+int pi_stage_times(pi_ctx *c, float *ms) { return pi_stage_times_at(c, 0, ms); }
 
 int pi_sync(pi_ctx *c)
 {

@@ -119,7 +119,8 @@ extern "C" int pi_update_noalloc(pi_ctx *c, const float *x0, const float *u_nom,
         double *part = reinterpret_cast<double *>(base + NA_PART_OFF);
 
         const bool tc = pi2rh_is_tc(c->opts.precision);
-        if (c->timing) rc = na_cuda(cudaEventRecord(c->ev[0], c->stream), "event record");
+        cudaEvent_t *ev = timing_slot(c);
+        if (ev) rc = na_cuda(cudaEventRecord(ev[0], c->stream), "event record");
         if (rc == PI_OK && tc) {
             TcArgs t = ctx_tc_args(c);
             t.K = K;
@@ -145,16 +146,17 @@ extern "C" int pi_update_noalloc(pi_ctx *c, const float *x0, const float *u_nom,
             a.phi = phi;
             rc = na_cuda(launch_rollout_fp32(a, c->stream), "rollout kernel launch");
         }
-        if (rc == PI_OK && c->timing) rc = na_cuda(cudaEventRecord(c->ev[1], c->stream), "event record");
+        if (rc == PI_OK && ev) rc = na_cuda(cudaEventRecord(ev[1], c->stream), "event record");
         const double inv_lam_log2e = 1.4426950408889634074 / (double)lambda;
         if (rc == PI_OK)
             rc = na_cuda(launch_scan_lse(cost, phi, eps, K, T, c->dt, inv_lam_log2e, costs_out, part, c->stream),
                          "scan kernel launch");
-        if (rc == PI_OK && c->timing) rc = na_cuda(cudaEventRecord(c->ev[2], c->stream), "event record");
+        if (rc == PI_OK && ev) rc = na_cuda(cudaEventRecord(ev[2], c->stream), "event record");
         if (rc == PI_OK)
             rc = na_cuda(launch_lse_merge(part, scan_blocks(K), T, inv_lam_log2e, u_nom, u_out, c->stream),
                          "merge kernel launch");
-        if (rc == PI_OK && c->timing) rc = na_cuda(cudaEventRecord(c->ev[3], c->stream), "event record");
+        if (rc == PI_OK && ev) rc = na_cuda(cudaEventRecord(ev[3], c->stream), "event record");
+        if (rc == PI_OK && ev) ++c->n_timed;
         if (rc == PI_OK) c->launches += 3;
     }
     if (prev >= 0 && prev != c->device) cudaSetDevice(prev);

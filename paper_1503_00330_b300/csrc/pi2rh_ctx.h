@@ -34,9 +34,11 @@ struct pi_ctx {
     size_t cap_x0 = 0, cap_unom = 0, cap_uout = 0, cap_costs = 0;
     // receding-horizon advance scratch: z [16], y [12], var [12]
     float *d_rh = nullptr;
-    // per-kernel timing
+    // per-kernel timing: a ring of event sets, timed update n records into set
+    // n % PI2RH_TIMING_RING (start, after the rollout, after the scan, end)
     bool timing = false;
-    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t ev[PI2RH_TIMING_RING][4] = {};
+    uint64_t n_timed = 0;
     uint64_t launches = 0;
 };
 
@@ -57,6 +59,12 @@ inline bool pi2rh_is_tc(int precision)
 
 // Split products on the quadratic-feature K steps of a tensor-core precision.
 inline int pi2rh_tc_qprod(int precision) { return precision == PI_PRECISION_TC_FP16X2 ? 2 : 3; }
+
+// The event set the next timed update records into, or nullptr with timing off.
+inline cudaEvent_t *timing_slot(pi_ctx *c)
+{
+    return c->timing ? c->ev[c->n_timed % PI2RH_TIMING_RING] : nullptr;
+}
 
 // Records msg as the calling thread's last error (pi_last_error) and returns code.
 int pi2rh_fail(int code, const char *msg);

@@ -45,8 +45,11 @@
 // work-list form and a one-wave group form for batches.
 // Every wait is bounded; on expiry the kernel flags the device error word,
 // drains its copies and MMAs, frees its tensor memory and returns.
+#include <array>
 #include <cstdio>
 #include <cstdlib>
+#include <map>
+#include <mutex>
 
 #include <cuda_fp16.h>
 
@@ -976,13 +979,31 @@ double split_cost(long long items, int s, long long resident)
 // cluster so that the SMs fill up; a few waves of blocks use pairs to shorten
 // the last, partly empty wave.  PI2RH_TC_SPLIT = 1..4 forces a value (the
 // results are bitwise the same for every split).
+// Resident CTAs of the single-controller kernel for splits 1-4 on the current
+// device, from the occupancy API on the first launch there and cached (the
+// queries cost tens of microseconds of host time in front of every launch
+// otherwise, with the GPU idle).
+std::array<long long, 5> resident_per_split()
+{
+    static std::mutex m;
+    static std::map<int, std::array<long long, 5>> cache;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lock(m);
+    auto it = cache.find(dev);
+    if (it == cache.end())
+        it = cache.emplace(dev, std::array<long long, 5>{0, resident_ctas<1>(), resident_ctas<2>(), resident_ctas<3>(),
+                                                         resident_ctas<4>()}).first;
+    return it->second;
+}
+
 int choose_split(long long blocks)
 {
     if (const char *e = getenv("PI2RH_TC_SPLIT")) {
         const int v = atoi(e);
         if (v >= 1 && v <= 4) return v;
     }
-    const long long res[5] = {0, resident_ctas<1>(), resident_ctas<2>(), resident_ctas<3>(), resident_ctas<4>()};
+    const std::array<long long, 5> res = resident_per_split();
     int best = 1;
     for (int sp = 2; sp <= 4; ++sp)
         if (split_cost(blocks, sp, res[sp]) < split_cost(blocks, best, res[best])) best = sp;
@@ -1011,22 +1032,41 @@ cudaError_t prepare_group()
     return set_smem_once(done, rollout_tc_group_kernel<NSPLIT, QP>, SMEM_BYTES);
 }
 
+// Clusters of NSPLIT CTAs of the group kernel that can be resident at once on
+// the current device (0 if the shape cannot be launched), queried once per
+// device and cached.
+template <int NSPLIT>
+long long group_resident_clusters()
+{
+    static std::mutex m;
+    static std::map<int, long long> cache;
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lock(m);
+    auto it = cache.find(dev);
+    if (it != cache.end()) return it->second;
+    long long n = 0;
+    if (prepare_group<NSPLIT>() == cudaSuccess) {
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute at[1];
+        split_config(cfg, at, sms, NSPLIT, nullptr);
+        int clusters = 0;
+        if (cudaOccupancyMaxActiveClusters(&clusters, rollout_tc_group_kernel<NSPLIT, 3>, &cfg) == cudaSuccess)
+            n = clusters;
+        else
+            cudaGetLastError();   // the shape cannot be launched: not an error of the caller's
+    } else {
+        cudaGetLastError();
+    }
+    cache.emplace(dev, n);
+    return n;
+}
+
 template <int NSPLIT>
 bool group_clusters_resident(long long items)
 {
-    if (prepare_group<NSPLIT>() != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute at[1];
-    split_config(cfg, at, items, NSPLIT, nullptr);
-    int clusters = 0;
-    if (cudaOccupancyMaxActiveClusters(&clusters, rollout_tc_group_kernel<NSPLIT, 3>, &cfg) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return clusters >= items;
+    return group_resident_clusters<NSPLIT>() >= items;
 }
 
 template <int NSPLIT, int QP>

@@ -439,3 +439,21 @@ def test_end_to_end_long_horizon_and_most_subrollouts(oracle, form, K, T, L, M, 
     print(f"K={K} T={T} L={L} M={M} ({form}): u err {eu} cost err {ec:.3g}")
     assert np.all(eu <= U_TOL)
     assert ec <= S_TOL
+
+
+def test_stage_times_ring():
+    """With timing on, the context keeps the stage events of its last 64 timed
+    updates: updates enqueued back to back can be read afterwards, oldest with the
+    largest `back`; asking past what is kept is an argument error."""
+    from paper_1503_00330_b300._lib import PiError
+    p = W.problem(300, 20, 40, seed=4)
+    ctl = _ctrl(p)
+    ctl.set_timing(True)
+    for i in range(3):
+        ctl.update(p.x0, p.u_nom, p.K, p.T, p.lam, p.sigma_u, p.seed + i)
+    times = [ctl.stage_times(back=b) for b in (2, 1, 0)]
+    assert all(all(v > 0 for v in t) for t in times)
+    assert ctl.stage_times() == times[-1]
+    with pytest.raises(PiError):
+        ctl.stage_times(back=3)
+    ctl.sync()
