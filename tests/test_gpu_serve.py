@@ -287,3 +287,36 @@ def test_cancelled_requests_leave_the_rest_unchanged():
     srv.drain()
     assert int(srv.state_save()["counter"][5]) == 2
     srv.close()
+
+
+@pytest.mark.parametrize("form", ["tc", "tc_fp16x2"])
+def test_served_at_full_size_sampled(oracle, form):
+    """The serving workload's own sizes (one shared L = 1024 model, 16 obstacles,
+    K up to 16384, T up to 120): three requests served in one mix; S_{k,0} of the
+    32 first and 32 last rollouts of each against the oracle (rollout k depends only
+    on its own noise counters, so a range is run alone)."""
+    from paper_1503_00330_b300.api import Controller, Server, update_seed
+    model, cost = W.make_lwpr(1024, seed=4), W.make_cost(16, seed=4)
+    ctl = Controller(model, cost, precision=form)
+    sizes = [(16384, 120), (2048, 50), (9001, 85)]
+    srv = Server(ctl, len(sizes), K_max=16384, T_max=120, want_costs=True)
+    rng = np.random.default_rng(11)
+    x0 = rng.normal(0, 0.1, (len(sizes), 12)).astype(np.float32)
+    warm = rng.normal(0, 0.2, (len(sizes), 120, 4)).astype(np.float32)
+    seeds = [5000 + a for a in range(len(sizes))]
+    for a in range(len(sizes)):
+        srv.set_agent(a, x0[a], warm[a], seeds[a])
+    tickets = {srv.submit(a, K, T, LAM, SU): a for a, (K, T) in enumerate(sizes)}
+    done = srv.wait(tickets)
+    tol = 2e-3 if form == "tc_fp16x2" else 1e-5
+    for t, a in tickets.items():
+        assert done[t]["status"] == 0
+        K, T = sizes[a]
+        _, c = srv.result(t, T, K)
+        for k0 in (0, K - 32):
+            r = oracle.rollouts(model, cost, x0[a], warm[a][:T], 32, T, SU, update_seed(seeds[a], 0), k0=k0)
+            S0 = oracle.cost_to_go(r["cost"], r["phi"], float(model.dt))[:, 0]
+            err = np.abs(c[k0:k0 + 32].astype(np.float64) - S0) / S0
+            print(f"served {form} K={K} T={T} rollouts {k0}..{k0 + 31}: S0 max rel err {err.max():.3g}")
+            assert np.all(err <= tol)
+    srv.close()
