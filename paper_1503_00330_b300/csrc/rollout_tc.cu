@@ -662,10 +662,8 @@ __device__ void tc_epilogue_item(const TcArgs &a, const TcSmem &S, uint32_t tbas
 #pragma unroll
                 for (int c = 0; c < NZ; ++c) zext[c] = zbuf[c * BM + r];
             } else {
-                float x[NX];
-#pragma unroll
-                for (int c = 0; c < NX; ++c) x[c] = xbuf[c * BM + r];
-                qbuf[r] = running_cost(a.cost, obs_s, x, var);
+                // the Euler step first: the next step's features (and with them
+                // the tensor core) wait for it, the running cost does not
                 float n[NY];
                 named_bar_sync(4, NE);   // the other half's normals of this step are in nbuf
                 if (a.model_noise) {
@@ -678,16 +676,7 @@ __device__ void tc_epilogue_item(const TcArgs &a, const TcSmem &S, uint32_t tbas
 #pragma unroll
                 for (int c = 0; c < NX; ++c) {
                     const float xdot = fmaf(sqrtf(var[c]), n[c], y[c]);
-                    x[c] = fmaf(a.dt, xdot, x[c]);
-                    xbuf[c * BM + r] = x[c];
-                    zext[c] = x[c];
-                    yrbuf[c * BM + r] = y[c];
-                }
-                named_bar_sync(2, BM);
-                if (writer) {
-                    float qs = 0.0f;
-                    for (int i = 0; i < M; ++i) qs += qbuf[r + i];
-                    a.cost_tk[(size_t)t * a.K + k] = qs / (float)M;
+                    zext[c] = fmaf(a.dt, xdot, xbuf[c * BM + r]);
                 }
                 if (t + 1 < a.T) {
                     const float4 nn = make_float4(nbuf[(NY + 0) * BM + r], nbuf[(NY + 1) * BM + r],
@@ -701,7 +690,43 @@ __device__ void tc_epilogue_item(const TcArgs &a, const TcSmem &S, uint32_t tbas
                 } else {
 #pragma unroll
                     for (int c = 0; c < NU; ++c) zext[NX + c] = 0.0f;
+                }
+            }
+            zext[16] = 1.0f;
+            if (PREDICT) {
+                if (t + 1 < nsteps) build_features(smem, r, zext);
+            } else {
+                if (t + 1 < nsteps) {
+                    // publish z, build this half of the feature rows, release them to the issuer
+#pragma unroll
+                    for (int c = 0; c < NZ; ++c) zbuf[c * BM + r] = zext[c];
+                    named_bar_arrive(5, NE);
+                    build_features<0, KF / 16>(smem, r, zext);
+                    fence_proxy_async_smem();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(phi_ready);
+                }
+                // off the tensor core's path: the running cost at (x_t, z_t) from the state still
+                // in xbuf, then the new state, this step's means as the next reference, the costs
+                float x[NX];
+#pragma unroll
+                for (int c = 0; c < NX; ++c) x[c] = xbuf[c * BM + r];
+                qbuf[r] = running_cost(a.cost, obs_s, x, var);
+#pragma unroll
+                for (int c = 0; c < NX; ++c) {
+                    xbuf[c * BM + r] = zext[c];
+                    yrbuf[c * BM + r] = y[c];
+                }
+                named_bar_sync(2, BM);
+                if (writer) {
+                    float qs = 0.0f;
+                    for (int i = 0; i < M; ++i) qs += qbuf[r + i];
+                    a.cost_tk[(size_t)t * a.K + k] = qs / (float)M;
+                }
+                if (t + 1 >= a.T) {
                     named_bar_sync(2, BM);
+#pragma unroll
+                    for (int c = 0; c < NX; ++c) x[c] = zext[c];
                     qbuf[r] = terminal_cost(a.cost, x);
                     named_bar_sync(2, BM);
                     if (writer) {
@@ -711,16 +736,6 @@ __device__ void tc_epilogue_item(const TcArgs &a, const TcSmem &S, uint32_t tbas
                     }
                 }
             }
-            zext[16] = 1.0f;
-            if (PREDICT) {
-                if (t + 1 < nsteps) build_features(smem, r, zext);
-            } else if (t + 1 < nsteps) {
-                // publish z, then each column half builds half of the feature rows
-#pragma unroll
-                for (int c = 0; c < NZ; ++c) zbuf[c * BM + r] = zext[c];
-                named_bar_arrive(5, NE);
-                build_features<0, KF / 16>(smem, r, zext);
-            }
         } else if (!PREDICT && t + 1 < nsteps) {
             named_bar_sync(5, NE);
             float zext[17];
@@ -728,10 +743,13 @@ __device__ void tc_epilogue_item(const TcArgs &a, const TcSmem &S, uint32_t tbas
             for (int c = 0; c < NZ; ++c) zext[c] = zbuf[c * BM + r];
             zext[16] = 1.0f;
             build_features<KF / 16, KF / 8>(smem, r, zext);
+            fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(phi_ready);
         }
         const bool any_abort = bar_sync_or(3, NE, aborted || *abort_flag != 0);
         if (any_abort) break;
-        if (t + 1 < nsteps) {
+        if (PREDICT && t + 1 < nsteps) {
             fence_proxy_async_smem();
             __syncwarp();
             if (lane == 0) mbar_arrive(phi_ready);
