@@ -534,12 +534,12 @@ __device__ void tc_epilogue_item(const TcArgs &a, const TcSmem &S, uint32_t tbas
     named_bar_sync(1, NE);
 
     for (int t = 0; t < nsteps; ++t) {
-        // The normals of this step (model noise) and of the next (control
-        // perturbation) do not depend on the state: the other column half
-        // draws them while every epilogue warp waits for the step's first
-        // tile, off the serial dynamics step at the end of the step.  The
-        // owners read them there, after barrier 4; the end-of-step barrier 3
-        // orders these writes after the previous step's reads.
+        // The normals of this step (model noise) and the next step's controls
+        // do not depend on the state: the other column half draws them while
+        // every epilogue warp waits for the step's first tile, off the serial
+        // dynamics step at the end of the step.  The owners read them there,
+        // after barrier 4; the end-of-step barrier 3 orders these writes after
+        // the previous step's reads.
         if (!PREDICT && !owner) {
             if (a.model_noise) {
 #pragma unroll
@@ -553,11 +553,14 @@ __device__ void tc_epilogue_item(const TcArgs &a, const TcSmem &S, uint32_t tbas
                 }
             }
             if (t + 1 < a.T) {
+                // the next step's controls u = u_nom + eps (and eps itself to the output)
                 const float4 nn = box_muller4(noise_block(a.seed, (uint32_t)k, (uint32_t)(t + 1), 0u, 0u));
-                nbuf[(NY + 0) * BM + r] = nn.x;
-                nbuf[(NY + 1) * BM + r] = nn.y;
-                nbuf[(NY + 2) * BM + r] = nn.z;
-                nbuf[(NY + 3) * BM + r] = nn.w;
+                const float eps[4] = {a.sqrt_sigma_u[0] * nn.x, a.sqrt_sigma_u[1] * nn.y, a.sqrt_sigma_u[2] * nn.z,
+                                      a.sqrt_sigma_u[3] * nn.w};
+#pragma unroll
+                for (int c = 0; c < NU; ++c) nbuf[(NY + c) * BM + r] = a.u_nom[(size_t)(t + 1) * NU + c] + eps[c];
+                if (rank == 0 && k < a.K && m == 0)
+                    a.eps_tk[(size_t)(t + 1) * a.K + k] = make_float4(eps[0], eps[1], eps[2], eps[3]);
             }
             named_bar_arrive(4, NE);
         }
@@ -679,14 +682,8 @@ __device__ void tc_epilogue_item(const TcArgs &a, const TcSmem &S, uint32_t tbas
                     zext[c] = fmaf(a.dt, xdot, xbuf[c * BM + r]);
                 }
                 if (t + 1 < a.T) {
-                    const float4 nn = make_float4(nbuf[(NY + 0) * BM + r], nbuf[(NY + 1) * BM + r],
-                                                  nbuf[(NY + 2) * BM + r], nbuf[(NY + 3) * BM + r]);
-                    const float eps[4] = {a.sqrt_sigma_u[0] * nn.x, a.sqrt_sigma_u[1] * nn.y,
-                                          a.sqrt_sigma_u[2] * nn.z, a.sqrt_sigma_u[3] * nn.w};
 #pragma unroll
-                    for (int c = 0; c < NU; ++c) zext[NX + c] = a.u_nom[(size_t)(t + 1) * NU + c] + eps[c];
-                    if (writer)
-                        a.eps_tk[(size_t)(t + 1) * a.K + k] = make_float4(eps[0], eps[1], eps[2], eps[3]);
+                    for (int c = 0; c < NU; ++c) zext[NX + c] = nbuf[(NY + c) * BM + r];
                 } else {
 #pragma unroll
                     for (int c = 0; c < NU; ++c) zext[NX + c] = 0.0f;
