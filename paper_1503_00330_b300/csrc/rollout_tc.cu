@@ -98,7 +98,8 @@ constexpr int OFF_V = OFF_Y + NY * BM * 4;
 constexpr int OFF_YREF = OFF_V + NY * BM * 4;
 constexpr int OFF_Q = OFF_YREF + NY * BM * 4;                   // [BM]
 constexpr int OFF_N = OFF_Q + BM * 4;                           // [NY + NU][BM] normals of the step
-constexpr int OFF_OBS = OFF_N + (NY + NU) * BM * 4;
+constexpr int OFF_SD = OFF_N + (NY + NU) * BM * 4;              // [NY][BM] sqrt of the variances
+constexpr int OFF_OBS = OFF_SD + NY * BM * 4;
 constexpr int OFF_BAR = OFF_OBS + MAX_OBS * 8;
 // barriers: full[NGRP], empty[NGRP], acc_full[2], acc_empty[2],
 //           const_full[4], const_empty[4], phi_ready, xfull, xfree, drain
@@ -107,6 +108,7 @@ constexpr int OFF_TSLOT = OFF_BAR + NBARS * 8;
 constexpr int OFF_ABORT = OFF_TSLOT + 8;
 constexpr int SMEM_BYTES = OFF_ABORT + 16;
 static_assert(OFF_RING % 128 == 0 && OFF_CONST % 16 == 0 && OFF_BAR % 8 == 0, "alignment");
+static_assert(OFF_SD % 16 == 0, "alignment");
 static_assert(SMEM_BYTES <= 232448, "shared memory budget");
 
 constexpr uint32_t TMEM_COLS = 512;     // 2 buffers x (S 128 + Y 128)
@@ -227,7 +229,7 @@ __device__ __forceinline__ void build_features(unsigned char *smem, int r, const
 
 struct TcSmem {
     unsigned char *base;
-    float *part, *zbuf, *xbuf, *ybuf, *vbuf, *yrbuf, *qbuf, *nbuf;
+    float *part, *zbuf, *xbuf, *ybuf, *vbuf, *yrbuf, *qbuf, *nbuf, *sdbuf;
     float2 *obs_s;
     uint64_t *full, *empty, *acc_full, *acc_empty, *const_full, *const_empty, *phi_ready;
     uint64_t *xfull, *xfree;   // output exchange between the CTAs of a cluster (split form)
@@ -248,6 +250,7 @@ __device__ __forceinline__ TcSmem tc_smem(unsigned char *smem)
     S.yrbuf = reinterpret_cast<float *>(smem + OFF_YREF);
     S.qbuf = reinterpret_cast<float *>(smem + OFF_Q);
     S.nbuf = reinterpret_cast<float *>(smem + OFF_N);
+    S.sdbuf = reinterpret_cast<float *>(smem + OFF_SD);
     S.obs_s = reinterpret_cast<float2 *>(smem + OFF_OBS);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + OFF_BAR);
     S.full = bars;
@@ -481,7 +484,7 @@ __device__ void tc_epilogue_item(const TcArgs &a, const TcSmem &S, uint32_t tbas
     const int o_begin = (int)rank * n_out;
     unsigned char *smem = S.base;
     float *part = S.part, *zbuf = S.zbuf, *xbuf = S.xbuf, *ybuf = S.ybuf, *vbuf = S.vbuf, *yrbuf = S.yrbuf,
-          *qbuf = S.qbuf, *nbuf = S.nbuf;
+          *qbuf = S.qbuf, *nbuf = S.nbuf, *sdbuf = S.sdbuf;
     float2 *obs_s = S.obs_s;
     uint64_t *acc_full = S.acc_full, *acc_empty = S.acc_empty, *const_full = S.const_full,
              *const_empty = S.const_empty, *phi_ready = S.phi_ready;
@@ -619,13 +622,17 @@ __device__ void tc_epilogue_item(const TcArgs &a, const TcSmem &S, uint32_t tbas
                 const float inv = 1.0f / st.s0;
                 const float me = st.s1 * inv;
                 const float yo = yref + me, vo = fmaxf(fmaf(-me, me, st.s2 * inv), 0.0f);
+                // the standard deviation of the sampled step, here rather than in the serial step
+                const float so = sqrtf(vo);
                 ybuf[o * BM + r] = yo;
                 vbuf[o * BM + r] = vo;
+                sdbuf[o * BM + r] = so;
                 if (!PREDICT && ncl > 1 && !aborted)   // send now, behind the next output's tiles
                     for (uint32_t pr = 0; pr < ncl; ++pr) {
                         if (pr == rank) continue;
                         st_cluster_f32(mapa_shared(ybuf, pr) + (uint32_t)((o * BM + r) * 4), yo);
                         st_cluster_f32(mapa_shared(vbuf, pr) + (uint32_t)((o * BM + r) * 4), vo);
+                        st_cluster_f32(mapa_shared(sdbuf, pr) + (uint32_t)((o * BM + r) * 4), so);
                     }
             }
         }
@@ -678,7 +685,7 @@ __device__ void tc_epilogue_item(const TcArgs &a, const TcSmem &S, uint32_t tbas
                 }
 #pragma unroll
                 for (int c = 0; c < NX; ++c) {
-                    const float xdot = fmaf(sqrtf(var[c]), n[c], y[c]);
+                    const float xdot = fmaf(sdbuf[c * BM + r], n[c], y[c]);
                     zext[c] = fmaf(a.dt, xdot, xbuf[c * BM + r]);
                 }
                 if (t + 1 < a.T) {
