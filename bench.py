@@ -357,6 +357,20 @@ def tensor_peak(peaks, clocks):
     return float(peaks.get("bf16_tflops", 1788.7)), f"measured dense bf16 burst ({note} in the run's clock record)"
 
 
+def clock_scaled(peaks, clocks, achieved):
+    """The burst tensor peak scaled to the run's median SM clock (the burst GEMM ran at the
+    maximum clock), with the achieved rate's fraction of it.  A run that the power cap held
+    well above the sustained loop's clock can exceed the sustained figure; this view shows
+    how close it came to the tensor core's rate at the clock it actually ran at."""
+    clocks = clocks or {}
+    mhz, mx = clocks.get("sm_mhz"), clocks.get("sm_max_mhz") or peaks.get("sm_max_mhz", 2032.0)
+    if mhz is None or not mx:
+        return None
+    peak = float(peaks.get("bf16_tflops", 1788.7)) * float(mhz) / float(mx)
+    return {"peak": peak, "frac": achieved / peak, "sm_mhz": float(mhz),
+            "basis": "measured dense bf16 burst x median SM clock / max SM clock"}
+
+
 def form_roofline(precision, rollout_ms, K, T, M, L, dev, peaks, workload, clocks=None):
     """Roofline of the rollout kernel from its per-launch CUDA-event times."""
     import torch
@@ -384,6 +398,7 @@ def form_roofline(precision, rollout_ms, K, T, M, L, dev, peaks, workload, clock
                                   f"flops ({per_field} per field, fields padded to 128-field tiles)",
             "useful_tflops": useful / avg_s / 1e12, "useful_frac": useful / avg_s / 1e12 / peak,
             "useful_basis": f"{FLOPS_PER_FIELD} algorithmic flop per field evaluation (the FP32 form's count)",
+            "at_run_clock": clock_scaled(peaks, clocks, achieved),
             "rollout_ms_per_launch": statistics.mean(rollout_ms)}
 
 
@@ -660,6 +675,7 @@ def batched_forms(probs, sched, order, steps, warmup, dev, pick=()):
             entry["roofline"] = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                                  "frac": ach / peak, "useful_tflops": uf, "useful_frac": uf / peak,
                                  "peak_basis": basis,
+                                 "at_run_clock": clock_scaled(measured_peaks(), entry["clocks"], ach),
                                  "kernel": ("rollout_tc_batch_kernel" if sched[form][1] == 0 else "rollout_tc_group_kernel")
                                            + " (time of the whole batched update)"}
         forms[form] = entry
@@ -765,6 +781,7 @@ def serving_measure(precision, serve_seconds, sweep_loads, lanes, max_group, war
             roof = {"bound": "tensor", "achieved": issued / span / 1e12, "peak": peak, "unit": "TFLOP/s",
                     "frac": issued / span / 1e12 / peak, "useful_tflops": useful / span / 1e12,
                     "useful_frac": useful / span / 1e12 / peak, "peak_basis": basis,
+                    "at_run_clock": clock_scaled(measured_peaks(), clk, issued / span / 1e12),
                     "kernel": "rollout_tc_group_kernel (issued MMA flops over the whole serving span)"}
         else:
             peak = torch.cuda.get_device_properties(0).multi_processor_count * FP32_LANES_PER_SM * 2 * \

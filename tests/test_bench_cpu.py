@@ -59,3 +59,14 @@ def test_tensor_peak_follows_the_clock_record():
     flagged = {"reasons": ["sw_power_cap"], "sm_mhz": 2021.0, "sm_max_mhz": 2032.0}
     assert bench.tensor_peak(peaks, flagged)[0] == 1788.7
     assert bench.tensor_peak(peaks, None)[0] == 1788.7
+
+
+def test_clock_scaled_tensor_peak():
+    """The clock-scaled view divides by the burst rate times the run's median clock over
+    the maximum, and is absent without a clock record."""
+    sys.path.insert(0, ROOT)
+    import bench
+    peaks = {"bf16_tflops": 1788.7}
+    v = bench.clock_scaled(peaks, {"sm_mhz": 1016.0, "sm_max_mhz": 2032.0}, 447.175)
+    assert abs(v["peak"] - 894.35) < 1e-9 and abs(v["frac"] - 0.5) < 1e-12
+    assert bench.clock_scaled(peaks, None, 1.0) is None
