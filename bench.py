@@ -1057,8 +1057,9 @@ def main():
                     help="rollouts per sampled controller in the batched error reference")
     ap.add_argument("--ref-sample", type=int, default=64, help="rollouts per reference-arm step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--precision", choices=list(FORMS), default="fp32",
-                    help="form of the headline line (the other form is timed too and reported under 'forms')")
+    ap.add_argument("--precision", choices=list(FORMS), default=None,
+                    help="form of the headline line (the other forms are timed too and reported under 'forms'); "
+                         "default fp32, except the serving workload, whose default is the tensor-core form")
     ap.add_argument("--no-compare", action="store_true", help="skip timing the other form")
     ap.add_argument("--batch-tile", type=int, default=-1,
                     help="batched: tile shape (0 persistent work list, 1 one item per CTA, 2..4 tensor-core "
@@ -1071,6 +1072,8 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
+    if args.precision is None:
+        args.precision = "tc" if args.workload == "serving" else "fp32"
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batched":
