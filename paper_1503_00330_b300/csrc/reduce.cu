@@ -11,14 +11,16 @@
 //     m_c = min_k S,  Z_c = sum_k 2^((m_c - S) log2(e)/lambda),
 //     V_c = sum_k 2^(...) eps_k
 // (exponent in FP64; exponential, the 2-term lane sums and the pairwise warp
-// sums in FP32; partials stored in FP64).  The halves hand chunks over through
+// sums in FP32; each partial row is 6 doubles wide: m_c as a double, then Z_c
+// and V_c as five floats, widened to FP64 by the merge).  The halves hand chunks over through
 // named barriers (full / empty per buffer).  cost and eps are read once,
 // coalesced and vectorised ([T][K] layout, eps as float4).  costs_out[k] = S_{k,0}.
 // B300 runs FP64 at about 2 lanes per clock per SM, 1/64 of FP32, so the
 // kernel keeps FP64 to the suffix sum (convert + FMA) and the exponent
 // (subtract, multiply, convert) -- five FP64-pipe instructions per
 // rollout-step: the exact minimum over the rollouts is taken on integer keys
-// of the doubles (warp redux), and only lane 0 converts the sums it stores.
+// of the doubles (warp redux), and the FP32 sums are stored as they are (a
+// conversion by lane 0 alone still holds the FP64 pipe for a whole warp).
 //
 // lse_merge_kernel: one warp per timestep (one warp per CTA, so that the FP64
 // exponentials spread over T SMs) merges the per-CTA partials in a fixed order
@@ -191,13 +193,16 @@ __device__ __forceinline__ void scan_lse_block(const float *__restrict__ cost_tk
             const float v2 = warp_sum_f(fmaf(wa, xa.z, wb * xb.z));
             const float v3 = warp_sum_f(fmaf(wa, xa.w, wb * xb.w));
             if (lane == 0) {
+                // the minimum as a double, the five FP32 sums as floats (the
+                // merge widens them, exactly): no conversion on the FP64 pipe here
                 double *p = part + ((size_t)blk * T + i) * 6;
+                float *pf = reinterpret_cast<float *>(p + 1);
                 p[0] = mn;
-                p[1] = (double)z;
-                p[2] = (double)v0;
-                p[3] = (double)v1;
-                p[4] = (double)v2;
-                p[5] = (double)v3;
+                pf[0] = z;
+                pf[1] = v0;
+                pf[2] = v1;
+                pf[3] = v2;
+                pf[4] = v3;
             }
         }
         scan_empty_arrive(b);
@@ -234,10 +239,11 @@ __device__ __forceinline__ void lse_merge_warp(const double *__restrict__ part, 
     double z = 0.0, v[4] = {0.0, 0.0, 0.0, 0.0};
     for (int c = lane; c < nblk; c += 32) {
         const double *p = part + ((size_t)c * T + i) * 6;
+        const float *pf = reinterpret_cast<const float *>(p + 1);
         const double sc = exp2((mn - p[0]) * inv_lam_log2e);
-        z = fma(p[1], sc, z);
+        z = fma((double)pf[0], sc, z);
 #pragma unroll
-        for (int a = 0; a < 4; ++a) v[a] = fma(p[2 + a], sc, v[a]);
+        for (int a = 0; a < 4; ++a) v[a] = fma((double)pf[1 + a], sc, v[a]);
     }
     z = warp_sum_d(z);
 #pragma unroll
