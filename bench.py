@@ -333,6 +333,7 @@ TIMING_CHUNK = 32
 # Stated accuracy of each form against the FP64 oracle (u_out per channel and costs, relative)
 ERROR_BOUND = {"fp32": 1e-5, "tc": 2e-3, "tc_fp16x2": 2e-3}
 FORMS = ("fp32", "tc", "tc_fp16x2")
+SPLIT_MODE = ["auto"]   # --split: launch of the FP32 rollout kernel (set in main)
 TC_FIELDS_PER_TILE = 128                      # fields per tensor-core tile (MMA N)
 # Issued MMA flops per field (2 per multiply-add): K step 0 of the exponent GEMM and the K=16
 # prediction GEMM with 3 split products; the 128 quadratic features (K steps 1-8) with 3
@@ -371,8 +372,18 @@ def clock_scaled(peaks, clocks, achieved):
             "basis": "measured dense bf16 burst x median SM clock / max SM clock"}
 
 
-def form_roofline(precision, rollout_ms, K, T, M, L, dev, peaks, workload, clocks=None):
-    """Roofline of the rollout kernel from its per-launch CUDA-event times."""
+def fp32_launch(ctl, K):
+    """(kernel name, ncu summary file stem) of the FP32 rollout launch for K rollouts."""
+    upc, ctas = ctl.split_plan(K)
+    if upc:
+        return (f"rollout_fp32_split_kernel (output-split launch: {ctas} CTAs x {upc} (block, output) units)",
+                "rollout_fp32_split")
+    return f"rollout_fp32_kernel ({ctas} CTAs, one per 64-slot block)", "rollout_fp32"
+
+
+def form_roofline(precision, rollout_ms, K, T, M, L, dev, peaks, workload, clocks=None, launch=None):
+    """Roofline of the rollout kernel from its per-launch CUDA-event times.
+    launch: fp32_launch() of the FP32 form (kernel name, summary stem)."""
     import torch
     props = torch.cuda.get_device_properties(dev)
     avg_s = statistics.mean(rollout_ms) / 1e3
@@ -381,8 +392,9 @@ def form_roofline(precision, rollout_ms, K, T, M, L, dev, peaks, workload, clock
         sm_max_mhz = float(peaks.get("sm_max_mhz", 2032.0))
         peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12
         achieved = useful / avg_s / 1e12
+        kname, stem = launch or ("rollout_fp32_kernel", "rollout_fp32")
         return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": profile_traffic(f"rollout_fp32_{workload}.md"), "kernel": "rollout_fp32_kernel",
+                "traffic": profile_traffic(f"{stem}_{workload}.md"), "kernel": kname,
                 "peak_basis": f"FP32 FMA pipe: {props.multi_processor_count} SMs x {FP32_LANES_PER_SM} lanes x 2 flop "
                               f"x {sm_max_mhz:.0f} MHz (max SM clock)",
                 "rollout_ms_per_launch": statistics.mean(rollout_ms)}
@@ -507,6 +519,10 @@ def time_form(precision, p, args, dev):
     from paper_1503_00330_b300.api import Controller
     K, T, M, L = p.K, p.T, p.M, p.model.L
     ctl = Controller(p.model, p.cost, M=M, model_noise=p.model_noise, device=dev.index, precision=precision)
+    launch = None
+    if precision == "fp32":
+        ctl.set_output_split(SPLIT_MODE[0])
+        launch = fp32_launch(ctl, K)
     ctl.set_timing(True)
     ctl.reserve(K, T)
     x0 = torch.as_tensor(p.x0, device=dev).clone()
@@ -549,7 +565,8 @@ def time_form(precision, p, args, dev):
     ctl.sync()
     ctl.close()
     total_s = sum(step_ms) / 1e3
-    roof = form_roofline(precision, rollout_ms, K, T, M, L, dev, measured_peaks(), args.workload, clocks=clk)
+    roof = form_roofline(precision, rollout_ms, K, T, M, L, dev, measured_peaks(), args.workload, clocks=clk,
+                         launch=launch)
     roof["rollout_share_of_step"] = sum(rollout_ms) / sum(step_ms)
     roof["secondary"] = mufu_check(precision, rollout_ms, K, T, M, L, dev.index or 0)
     return {"value": K * T * M * args.steps / total_s, "ms_per_update": 1e3 * total_s / args.steps,
@@ -566,6 +583,10 @@ def time_updates(precision, p, steps, warmup, dev, workload):
     from paper_1503_00330_b300.api import Controller
     K, T, M, L = p.K, p.T, p.M, p.model.L
     ctl = Controller(p.model, p.cost, M=M, model_noise=p.model_noise, device=dev.index, precision=precision)
+    launch = None
+    if precision == "fp32":
+        ctl.set_output_split(SPLIT_MODE[0])
+        launch = fp32_launch(ctl, K)
     ctl.set_timing(True)
     ctl.reserve(K, T)
     x0 = torch.as_tensor(p.x0, device=dev).clone()
@@ -602,7 +623,8 @@ def time_updates(precision, p, steps, warmup, dev, workload):
     ctl.close()
     clk = clocks.summary()
     total_s = sum(step_ms) / 1e3
-    roof = form_roofline(precision, rollout_ms, K, T, M, L, dev, measured_peaks(), workload, clocks=clk)
+    roof = form_roofline(precision, rollout_ms, K, T, M, L, dev, measured_peaks(), workload, clocks=clk,
+                         launch=launch)
     roof["rollout_share_of_step"] = sum(rollout_ms) / sum(step_ms)
     roof["secondary"] = mufu_check(precision, rollout_ms, K, T, M, L, dev.index or 0)
     return {"value": K * T * M * steps / total_s, "ms_per_update": 1e3 * total_s / steps, "steps": steps,
@@ -855,6 +877,10 @@ def run_ours(args):
     K, T, M, L = p.K, p.T, p.M, p.model.L
 
     ctl = Controller(p.model, p.cost, M=M, model_noise=p.model_noise, device=local, precision=args.precision)
+    launch = None
+    if args.precision == "fp32":
+        ctl.set_output_split(SPLIT_MODE[0])
+        launch = fp32_launch(ctl, K)
     ctl.set_timing(True)
     ctl.reserve(K, T)
     x0 = torch.as_tensor(p.x0, device=dev).clone()
@@ -931,7 +957,8 @@ def run_ours(args):
 
     peaks = measured_peaks()
     clk = clocks.summary()
-    roofline = form_roofline(args.precision, rollout_ms, K, T, M, L, dev, peaks, args.workload, clocks=clk)
+    roofline = form_roofline(args.precision, rollout_ms, K, T, M, L, dev, peaks, args.workload, clocks=clk,
+                             launch=launch)
     rates = pipe_peaks(local)   # measured pipe rates: context beside the unit-count FP32 peak
     roofline["rollout_share_of_step"] = sum(rollout_ms) / sum(step_ms)
     roofline["secondary"] = mufu_check(args.precision, rollout_ms, K, T, M, L, local)
@@ -1061,6 +1088,8 @@ def main():
                     help="form of the headline line (the other forms are timed too and reported under 'forms'); "
                          "default fp32, except the serving workload, whose default is the tensor-core form")
     ap.add_argument("--no-compare", action="store_true", help="skip timing the other form")
+    ap.add_argument("--split", choices=["auto", "off", "always"], default="auto",
+                    help="launch of the FP32 rollout kernel (pi_set_output_split; same results bit for bit)")
     ap.add_argument("--batch-tile", type=int, default=-1,
                     help="batched: tile shape (0 persistent work list, 1 one item per CTA, 2..4 tensor-core "
                          "outputs split over CTAs; -1 = pick order and tile per form with the autotuner)")
@@ -1070,6 +1099,7 @@ def main():
     ap.add_argument("--serve-sweep", type=float, nargs="*", default=[0.25, 0.5, 0.75, 0.9],
                     help="serving: offered loads (fractions of the measured capacity) for the latency sweep")
     args = ap.parse_args()
+    SPLIT_MODE[0] = args.split
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
     if args.precision is None:

@@ -79,6 +79,7 @@ enum {
  * rather than the FP32 one.  Both tensor-core forms share one packed model. */
 enum { PI_PRECISION_FP32 = 0, PI_PRECISION_TC_FP16X3 = 1, PI_PRECISION_TC_FP16X2 = 2 };
 enum { PI_NOISE_MEAN_ONLY = 0, PI_NOISE_SAMPLED = 1 };
+enum { PI_SPLIT_OFF = 0, PI_SPLIT_AUTO = 1, PI_SPLIT_ALWAYS = 2 };
 enum { PI_OBS_INDICATOR = 0, PI_OBS_GAUSSIAN = 1 };
 
 typedef struct pi_ctx pi_ctx;
@@ -226,6 +227,26 @@ int pi_update_host(pi_ctx *ctx, const float *x0, const float *u_nominal, int K, 
  *   u_nom_next[T][4] out    u_out shifted left by one step, last step repeated;
  *                           must not overlap u_out */
 int pi_rh_advance(pi_ctx *ctx, float *x0, const float *u_out, int T, float *u_nom_next);
+
+/* How the FP32 rollout kernel of pi_update (and pi_update_noalloc) is
+ * launched on an FP32 context (no effect on tensor-core contexts).  The plain
+ * launch gives each block of 64 rollout slots (rollout x sub-rollout) one CTA
+ * for all T steps; with fewer blocks than the GPU has SMs some SMs then stay
+ * idle (K = 8192, M = 1: 128 blocks on 148 SMs).  The output-split launch
+ * deals the blocks' (block, output) pairs out to one co-resident CTA per SM
+ * (a cooperative launch), which exchange each step's state through a 1.5 MB
+ * area in device memory allocated by pi_create; every output is still
+ * evaluated by one CTA in the same order, so the results are identical bit
+ * for bit (Sec. 2, Eq. 1: the split changes which SM evaluates which
+ * receptive fields, not the arithmetic).
+ *   PI_SPLIT_OFF     always the plain launch
+ *   PI_SPLIT_AUTO    (default) the split launch where it takes work off the
+ *                    busiest SM: fewer than ~11/12 as many blocks as SMs and
+ *                    (12 - outputs per CTA) * ceil(L / 2) >= 64
+ *   PI_SPLIT_ALWAYS  the split launch whenever it takes work off the busiest SM
+ * A bounded wait of one CTA on another that expires shows as PI_ERR_TIMEOUT
+ * from pi_sync.  Errors: INVALID_ARG (mode). */
+int pi_set_output_split(pi_ctx *ctx, int mode);
 
 /* Per-kernel timing of pi_update (and pi_update_noalloc) with CUDA events on
  * the context's stream (off by default).  The context keeps the events of the
@@ -527,6 +548,21 @@ int pi_debug_reduce(pi_ctx *ctx, const float *cost, const float *phi, const floa
  * PI_ERR_TIMEOUT and the context stays usable.  Asynchronous on the
  * context's stream. */
 int pi_debug_wait_timeout(pi_ctx *ctx, int64_t limit_ns);
+
+/* The launch an FP32 update of K rollouts (with the context's M and split
+ * mode) would use: *units_per_cta = (block, output) units per CTA of the
+ * output-split launch and *ctas its grid, or 0 and the number of 64-slot
+ * blocks for the plain launch.  Host only; INVALID_ARG on a tensor-core
+ * context or K < 1. */
+int pi_debug_split_plan(pi_ctx *ctx, int K, int *units_per_cta, int *ctas);
+
+/* Failure path of the output-split launch's waits between CTAs, exercised
+ * without a fault: with drop = 1 the next split launches leave out their last
+ * CTA, so the flags it would set are never set.  The CTAs that wait on it give
+ * up after the bounded wait (2 s), tell the others through the exchange area,
+ * and all return; pi_sync then reports PI_ERR_TIMEOUT and the context stays
+ * usable.  drop = 0 restores full launches.  Errors: INVALID_ARG (drop). */
+int pi_debug_split_drop_cta(pi_ctx *ctx, int drop);
 
 /* Tensor-core GEMM core of the tensor-core form, checked on its own:
  * D [128][64] f32 = A [128][K] x B [64][K]^T with A, B fp16 (IEEE binary16,

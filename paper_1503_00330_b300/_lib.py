@@ -15,6 +15,7 @@ HEADER = os.path.join(os.path.dirname(PKG), "include", "pi2rh.h")
 
 (PI_OK, PI_ERR_INVALID_ARG, PI_ERR_OOM, PI_ERR_CUDA, PI_ERR_TIMEOUT, PI_ERR_INTERNAL, PI_ERR_UNSUPPORTED,
  PI_ERR_BUSY, PI_ERR_CANCELLED) = range(9)
+PI_SPLIT_OFF, PI_SPLIT_AUTO, PI_SPLIT_ALWAYS = range(3)
 ERR_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "TIMEOUT", 5: "INTERNAL", 6: "UNSUPPORTED",
              7: "BUSY", 8: "CANCELLED"}
 
@@ -100,6 +101,9 @@ _SIGS = {
     "pi_launch_count": (ctypes.c_uint64, [_vp]),
     "pi_rh_advance": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _vp]),
     "pi_set_timing": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "pi_set_output_split": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "pi_debug_split_plan": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    "pi_debug_split_drop_cta": (ctypes.c_int, [_vp, ctypes.c_int]),
     "pi_stage_times": (ctypes.c_int, [_vp, _fp]),
     "pi_stage_times_at": (ctypes.c_int, [_vp, ctypes.c_int, _fp]),
     "pi_debug_tc_gemm": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _vp]),

@@ -125,6 +125,20 @@ class Controller:
     def set_timing(self, enable: bool = True):
         check(self._lib.pi_set_timing(self._h, 1 if enable else 0))
 
+    def set_output_split(self, mode: str = "auto"):
+        """Launch of the FP32 rollout: "off" (one CTA per 64-slot block), "auto"
+        (default: the output-split launch where it uses SMs the plain one leaves
+        idle) or "always".  The results are the same bit for bit."""
+        modes = {"off": _lib.PI_SPLIT_OFF, "auto": _lib.PI_SPLIT_AUTO, "always": _lib.PI_SPLIT_ALWAYS}
+        check(self._lib.pi_set_output_split(self._h, modes[mode]))
+
+    def split_plan(self, K: int):
+        """(units_per_cta, ctas) of the FP32 rollout launch for K rollouts:
+        units_per_cta = 0 for the plain launch (ctas = its 64-slot blocks)."""
+        upc, ctas = ctypes.c_int(), ctypes.c_int()
+        check(self._lib.pi_debug_split_plan(self._h, int(K), ctypes.byref(upc), ctypes.byref(ctas)))
+        return upc.value, ctas.value
+
     def stage_times(self, back: int = 0):
         """(rollout_ms, scan_ms, merge_ms) of the timed update `back` calls before the
         last (0 = the last; the context keeps the last PI2RH_TIMING_RING = 64)."""

@@ -171,6 +171,7 @@ int launch_rollouts(pi_ctx *c, const float *x0, const float *u_nom, int K, int T
     a.cost_tk = cost;
     a.eps_tk = eps;
     a.phi = phi;
+    PI_CUDA(ctx_split_args(c, a), "split exchange area clear");
     PI_CUDA(launch_rollout_fp32(a, c->stream), "rollout kernel launch");
     c->launches++;
     return PI_OK;
@@ -197,7 +198,7 @@ int launch_reduce(pi_ctx *c, const float *cost, const float *phi, const float4 *
 void free_ctx_memory(pi_ctx *c)
 {
     void *ptrs[] = {c->d_rec, c->d_obs, c->d_err, c->d_cost, c->d_eps, c->d_phi, c->d_part,
-                    c->d_x0, c->d_unom, c->d_uout, c->d_costs, c->d_rh, c->d_wtiles, c->d_wconst};
+                    c->d_x0, c->d_unom, c->d_uout, c->d_costs, c->d_rh, c->d_wtiles, c->d_wconst, c->d_split};
     for (void *p : ptrs)
         if (p) cudaFreeAsync(p, c->stream);
     cudaStreamSynchronize(c->stream);
@@ -428,6 +429,21 @@ int pi_create(const pi_lwpr_params *lw, const pi_cost_params *cp, const pi_opts 
         return bail(e, "obstacle copy");
     if ((e = cudaMalloc(&c->d_err, sizeof(int))) != cudaSuccess) return bail(e, "error word alloc");
     if ((e = cudaMemset(c->d_err, 0, sizeof(int))) != cudaSuccess) return bail(e, "error word clear");
+    if (!pi2rh_is_tc(opts.precision)) {
+        // exchange area of the output-split rollout launch: one block per SM at most
+        int nsm = 0;
+        if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, opts.device)) != cudaSuccess)
+            return bail(e, "SM count");
+        int coop = 0;
+        if ((e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, opts.device)) != cudaSuccess)
+            return bail(e, "cooperative-launch attribute");
+        if (coop && nsm > 0) {
+            c->split_max_blocks = nsm;
+            const size_t nb = split_bytes(nsm);
+            if ((e = cudaMalloc(&c->d_split, nb)) != cudaSuccess) return bail(e, "split exchange alloc");
+            if ((e = cudaMemset(c->d_split, 0, nb)) != cudaSuccess) return bail(e, "split exchange clear");
+        }
+    }
     if (pi2rh_is_tc(opts.precision)) {
         std::vector<unsigned char> wt;
         std::vector<float> wc;
@@ -457,6 +473,41 @@ int pi_create(const pi_lwpr_params *lw, const pi_cost_params *cp, const pi_opts 
     C.n_obs = cp->n_obs;
     C.obs = c->d_obs;
     *out = c;
+    return PI_OK;
+}
+
+int pi_set_output_split(pi_ctx *c, int mode)
+{
+    if (!c) return fail(PI_ERR_INVALID_ARG, "ctx is NULL");
+    if (mode != PI_SPLIT_OFF && mode != PI_SPLIT_AUTO && mode != PI_SPLIT_ALWAYS)
+        return fail(PI_ERR_INVALID_ARG, "split mode must be PI_SPLIT_OFF, PI_SPLIT_AUTO or PI_SPLIT_ALWAYS");
+    c->split_mode = mode;
+    return PI_OK;
+}
+
+int pi_debug_split_plan(pi_ctx *c, int K, int *units_per_cta, int *ctas)
+{
+    if (!c || !units_per_cta || !ctas) return fail(PI_ERR_INVALID_ARG, "NULL argument");
+    if (pi2rh_is_tc(c->opts.precision)) return fail(PI_ERR_INVALID_ARG, "the output split is an FP32-form launch");
+    if (K < 1) return fail(PI_ERR_INVALID_ARG, "K must be >= 1");
+    DeviceGuard dg(c->device);
+    PI_CUDA(dg.err, "cudaSetDevice");
+    RolloutArgs a = base_args(c);
+    a.K = K;
+    a.split = c->d_split;
+    a.split_max_blocks = c->split_max_blocks;
+    a.split_mode = c->split_mode;
+    const int upc = fp32_split_upc(a);
+    *units_per_cta = upc;
+    *ctas = upc > 0 ? fp32_split_grid(a, upc) : (int)(((long long)K * a.M + RF_SLOTS - 1) / RF_SLOTS);
+    return PI_OK;
+}
+
+int pi_debug_split_drop_cta(pi_ctx *c, int drop)
+{
+    if (!c) return fail(PI_ERR_INVALID_ARG, "ctx is NULL");
+    if (drop != 0 && drop != 1) return fail(PI_ERR_INVALID_ARG, "drop must be 0 or 1");
+    c->split_drop = drop;
     return PI_OK;
 }
 
@@ -569,7 +620,7 @@ int pi_sync(pi_ctx *c)
     PI_CUDA(cudaMemcpy(&err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost), "error word read");
     if (err) {
         PI_CUDA(cudaMemset(c->d_err, 0, sizeof(int)), "error word clear");
-        if (err & (DEVERR_TIMEOUT_FULL | DEVERR_TIMEOUT_EMPTY | DEVERR_TIMEOUT_DRAIN))
+        if (err & (DEVERR_TIMEOUT_FULL | DEVERR_TIMEOUT_EMPTY | DEVERR_TIMEOUT_DRAIN | DEVERR_TIMEOUT_PEER))
             return fail(PI_ERR_TIMEOUT, "a bounded device-side wait expired (flags 0x%x)", err);
         return fail(PI_ERR_INTERNAL, "device-side check failed (flags 0x%x)", err);
     }

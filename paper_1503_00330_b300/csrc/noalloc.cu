@@ -144,7 +144,8 @@ extern "C" int pi_update_noalloc(pi_ctx *c, const float *x0, const float *u_nom,
             a.cost_tk = cost;
             a.eps_tk = eps;
             a.phi = phi;
-            rc = na_cuda(launch_rollout_fp32(a, c->stream), "rollout kernel launch");
+            rc = na_cuda(ctx_split_args(c, a), "split exchange area clear");
+            if (rc == PI_OK) rc = na_cuda(launch_rollout_fp32(a, c->stream), "rollout kernel launch");
         }
         if (rc == PI_OK && ev) rc = na_cuda(cudaEventRecord(ev[1], c->stream), "event record");
         const double inv_lam_log2e = 1.4426950408889634074 / (double)lambda;

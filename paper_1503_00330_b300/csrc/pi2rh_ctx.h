@@ -40,6 +40,12 @@ struct pi_ctx {
     cudaEvent_t ev[PI2RH_TIMING_RING][4] = {};
     uint64_t n_timed = 0;
     uint64_t launches = 0;
+    // exchange area of the output-split FP32 rollout launch (FP32 contexts)
+    unsigned char *d_split = nullptr;
+    int split_max_blocks = 0;
+    int split_mode = PI_SPLIT_AUTO;
+    uint32_t split_epoch = 0;
+    int split_drop = 0;   // pi_debug_split_drop_cta
 };
 
 // Scoped NVTX range on the calling host thread (shown by profilers that attach
@@ -82,6 +88,25 @@ inline pi2rh::RolloutArgs ctx_rollout_args(const pi_ctx *c)
     a.model_noise = c->opts.model_noise == PI_NOISE_SAMPLED ? 1 : 0;
     a.err = c->d_err;
     return a;
+}
+
+// Output-split fields of the next FP32 rollout launch on the context's own
+// exchange area: a fresh epoch per launch (the area starts zeroed, so epochs
+// start at 1; before the counter wraps, the area is cleared on the stream).
+inline cudaError_t ctx_split_args(pi_ctx *c, pi2rh::RolloutArgs &a)
+{
+    a.split = c->d_split;
+    a.split_max_blocks = c->split_max_blocks;
+    a.split_mode = c->split_mode;
+    a.split_drop = c->split_drop;
+    if (!c->d_split) return cudaSuccess;
+    if (c->split_epoch == 0xffffffffu) {
+        cudaError_t e = cudaMemsetAsync(c->d_split, 0, pi2rh::split_bytes(c->split_max_blocks), c->stream);
+        if (e != cudaSuccess) return e;
+        c->split_epoch = 0;
+    }
+    a.split_epoch = ++c->split_epoch;
+    return cudaSuccess;
 }
 
 inline pi2rh::TcArgs ctx_tc_args(const pi_ctx *c)

@@ -18,6 +18,7 @@ constexpr int DEVERR_TIMEOUT_FULL = 1;   // consumer waited too long for a stage
 constexpr int DEVERR_TIMEOUT_EMPTY = 2;  // producer waited too long for a free slot
 constexpr int DEVERR_TIMEOUT_DRAIN = 4;  // copies still in flight at exit
 constexpr int DEVERR_BAD_CONFIG = 8;     // launch configuration inconsistent
+constexpr int DEVERR_TIMEOUT_PEER = 16;  // a CTA waited too long for another CTA's step (split launch)
 
 // Upper bound on any single device-side wait (nanoseconds of %globaltimer).
 constexpr unsigned long long WAIT_LIMIT_NS = 2000000000ull;

@@ -45,6 +45,15 @@ struct RolloutArgs {
     float *y_out, *var_out;  // prediction: [n_pred][NY]
     int n_pred;
     int *err;                // device error word
+    // Output-split launch of the FP32 rollout (see launch_rollout_fp32):
+    // exchange area of split_bytes(split_max_blocks) bytes (null: never
+    // split), its mode, and a tag that differs between launches on one area.
+    unsigned char *split;
+    int split_max_blocks;
+    int split_mode;          // PI_SPLIT_OFF / _AUTO / _ALWAYS
+    uint32_t split_epoch;    // >= 1, new for every launch on `split`
+    int split_upc;           // set by the launcher: (block, output) units per CTA
+    int split_drop;          // failure-path check: CTAs left out of the split grid (0 normally)
 };
 
 // Rollout slots (rollout x sub-rollout) per CTA of the FP32 rollout kernel.
@@ -64,7 +73,27 @@ struct BatchArgs {
     int *err;
 };
 
+// Exchange area of the output-split FP32 launch: a 128-byte header, then per
+// 64-slot block its flags (z published, outputs done per non-owner CTA) and
+// its z, y and var rows.
+constexpr size_t SPLIT_HDR_BYTES = 128;
+constexpr size_t SPLIT_BLOCK_BYTES = 128 + (size_t)(NZ + 2 * NY) * RF_SLOTS * 4;
+inline size_t split_bytes(int max_blocks) { return SPLIT_HDR_BYTES + (size_t)max_blocks * SPLIT_BLOCK_BYTES; }
+
+// The FP32 rollout.  With a.split set and the mode allowing it, a launch of
+// fewer 64-slot blocks than the GPU has SMs spreads the blocks' (block,
+// output) units over one co-resident CTA per SM (a cooperative launch), so
+// every SM works; the results are those of the one-CTA-per-block launch bit
+// for bit.
 cudaError_t launch_rollout_fp32(const RolloutArgs &a, cudaStream_t s);
+// Units per CTA that the output-split launch would use for these arguments,
+// or 0 when the one-CTA-per-block launch runs.
+int fp32_split_upc(const RolloutArgs &a);
+inline int fp32_split_grid(const RolloutArgs &a, int upc)
+{
+    const long long units = ((long long)a.K * a.M + RF_SLOTS - 1) / RF_SLOTS * NY;
+    return (int)((units + upc - 1) / upc);
+}
 cudaError_t launch_rollout_fp32_batch(const BatchArgs &b, int grid, cudaStream_t s);
 // Plain-launch form of the batch: one item per CTA (b.counter unused).
 cudaError_t launch_rollout_fp32_group(const BatchArgs &b, cudaStream_t s);

@@ -24,6 +24,7 @@
 // so every parameter load feeds four field-slot evaluations on the packed
 // FP32x2 FMA datapath.  Every wait is bounded; on expiry the kernel records a
 // flag in the device error word, drains its copies and returns.
+#include "pi2rh.h"
 #include "pi2rh_kernels.h"
 
 namespace pi2rh {
@@ -210,17 +211,20 @@ __device__ __forceinline__ void fp32_init_barriers(const Fp32Smem &S)
     fence_mbar_init();
 }
 
-// Producer (one lane): streams the field-pair records of all outputs for one
-// work item (T passes over them) through the stage ring.  `g0` is the ring
-// position at the start of the item; returns the position after it, or -1
-// after a timeout (abort flag set).
-__device__ long long fp32_producer(const RolloutArgs &a, const Fp32Smem &S, long long g0, long long &issued)
+// Producer (one lane): streams the field-pair records of one work item (T
+// passes over its outputs) through the stage ring.  Per step it copies the
+// outputs out_of(0), ..., out_of(n_out - 1), each in spo stages.  `g0` is the
+// ring position at the start of the item; returns the position after it, or
+// -1 after a timeout (abort flag set).
+template <typename OutOf>
+__device__ __forceinline__ long long fp32_produce(const RolloutArgs &a, const Fp32Smem &S, long long g0,
+                                                  long long &issued, int n_out, OutOf out_of)
 {
     unsigned char *stage_base = S.stage_base;
     uint64_t *full = S.full, *empty = S.empty;
     volatile int *abort_flag = S.abort_flag;
     const int P = a.P, spo = a.stages_per_out;
-    const int G = NY * spo;
+    const int G = n_out * spo;
     const long long total = g0 + (long long)G * a.T;
         for (long long g = g0; g < total; ++g) {
             const int slot = (int)(g % NSTAGE);
@@ -233,7 +237,7 @@ __device__ long long fp32_producer(const RolloutArgs &a, const Fp32Smem &S, long
                 }
             }
             const int gs = (int)((g - g0) % G);
-            const int o = gs / spo, s = gs % spo;
+            const int o = out_of(gs / spo), s = gs % spo;
             const int p0 = s * RF_PAIRS_PER_STAGE;
             const int np = min(RF_PAIRS_PER_STAGE, P - p0);
             const uint32_t bytes = (uint32_t)np * REC_BYTES;
@@ -245,22 +249,172 @@ __device__ long long fp32_producer(const RolloutArgs &a, const Fp32Smem &S, long
     return total;
 }
 
+// All NY outputs in order (one 64-slot block per CTA).
+__device__ long long fp32_producer(const RolloutArgs &a, const Fp32Smem &S, long long g0, long long &issued)
+{
+    return fp32_produce(a, S, g0, issued, NY, [](int i) { return i; });
+}
+
+// Initial state of one slot (stepper thread tid of its block): x = x0,
+// z = [x0, u_nom[0] + eps_0], y_ref = 0; the writer stores eps_0.
+__device__ __forceinline__ void fp32_init_slot(const RolloutArgs &a, const Fp32Smem &S, int tid, int k, bool writer)
+{
+    float *zbuf = S.zbuf, *xbuf = S.xbuf, *yrbuf = S.yrbuf;
+    float4 n = box_muller4(noise_block(a.seed, (uint32_t)k, 0u, 0u, 0u));
+    float eps[4] = {a.sqrt_sigma_u[0] * n.x, a.sqrt_sigma_u[1] * n.y,
+                    a.sqrt_sigma_u[2] * n.z, a.sqrt_sigma_u[3] * n.w};
+#pragma unroll
+    for (int c = 0; c < NX; ++c) {
+        float xc = a.x0[c];
+        xbuf[c * SLOTS + tid] = xc;
+        zbuf[c * SLOTS + tid] = xc;
+    }
+#pragma unroll
+    for (int c = 0; c < NU; ++c) zbuf[(NX + c) * SLOTS + tid] = a.u_nom[c] + eps[c];
+#pragma unroll
+    for (int o = 0; o < NY; ++o) yrbuf[o * SLOTS + tid] = 0.0f;
+    if (writer) a.eps_tk[k] = make_float4(eps[0], eps[1], eps[2], eps[3]);
+}
+
+// One output's pass over its field-pair records (spo stages of the ring from
+// position g) for the warp's slots A = lane and B = lane + 32, whose inputs
+// are zA, zB and whose negated reference means are ya, yb.  Writes the
+// warp's softmax states into the partial buffer pb.
+__device__ __forceinline__ void fp32_output_pass(const RolloutArgs &a, const Fp32Smem &S, const float2 (&zA)[NZ],
+                                                 const float2 (&zB)[NZ], float ya, float yb, float *pb,
+                                                 long long &g, bool &aborted)
+{
+    unsigned char *stage_base = S.stage_base;
+    uint64_t *full = S.full, *empty = S.empty;
+    volatile int *abort_flag = S.abort_flag;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int P = a.P, spo = a.stages_per_out;
+    const int slotA = lane, slotB = lane + 32;
+    const float2 yrA = make_float2(ya, ya), yrB = make_float2(yb, yb);
+    Soft stA, stB;
+    soft_init(stA);
+    soft_init(stB);
+    for (int s = 0; s < spo; ++s, ++g) {
+        const int slot = (int)(g % NSTAGE);
+        if (!aborted && !mbar_wait_bounded(&full[slot], (uint32_t)((g / NSTAGE) & 1), abort_flag)) {
+            if (lane == 0) {
+                if (!*abort_flag) atomicOr(a.err, DEVERR_TIMEOUT_FULL);
+                *abort_flag = 1;
+            }
+            aborted = true;
+        }
+#pragma unroll 2
+        for (int j = 0; j < RF_PAIRS_PER_STAGE / CW; ++j) {
+            const int pair = s * RF_PAIRS_PER_STAGE + j * CW + warp;
+            if (!aborted && pair < P) {
+                const float4 *r4 = reinterpret_cast<const float4 *>(
+                    stage_base + (size_t)slot * STAGE_BYTES + (size_t)(j * CW + warp) * REC_BYTES);
+                process_pair(r4, zA, zB, yrA, yrB, stA, stB);
+            }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[slot]);
+    }
+    pb[(warp * 5 + 0) * SLOTS + slotA] = stA.m;
+    pb[(warp * 5 + 1) * SLOTS + slotA] = stA.s0;
+    pb[(warp * 5 + 2) * SLOTS + slotA] = stA.s1;
+    pb[(warp * 5 + 3) * SLOTS + slotA] = stA.s2;
+    pb[(warp * 5 + 4) * SLOTS + slotA] = stA.s3;
+    pb[(warp * 5 + 0) * SLOTS + slotB] = stB.m;
+    pb[(warp * 5 + 1) * SLOTS + slotB] = stB.s0;
+    pb[(warp * 5 + 2) * SLOTS + slotB] = stB.s1;
+    pb[(warp * 5 + 3) * SLOTS + slotB] = stB.s2;
+    pb[(warp * 5 + 4) * SLOTS + slotB] = stB.s3;
+}
+
+// The warp's slot inputs, duplicated into both halves of a float2 (the two
+// fields of a record), from the [NZ][SLOTS] buffer zsrc.
+__device__ __forceinline__ void fp32_load_z(const float *zsrc, float2 (&zA)[NZ], float2 (&zB)[NZ])
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int c = 0; c < NZ; ++c) {
+        float va = zsrc[c * SLOTS + lane], vb = zsrc[c * SLOTS + lane + 32];
+        zA[c] = make_float2(va, va);
+        zB[c] = make_float2(vb, vb);
+    }
+}
+
+// End of step t for one slot (stepper thread tid; all 64 stepper threads
+// call it together): with y and var of every output in ybuf / vbuf, the
+// running cost at (x_t, z_t), the sampled Euler step (Sec. 3.2), the next
+// control perturbation, and at the last step the terminal cost.
+__device__ __forceinline__ void fp32_step_slot(const RolloutArgs &a, const Fp32Smem &S, int t, int tid, int k, int m,
+                                               bool writer)
+{
+    float *zbuf = S.zbuf, *xbuf = S.xbuf, *ybuf = S.ybuf, *vbuf = S.vbuf, *yrbuf = S.yrbuf, *qbuf = S.qbuf;
+    const int M = a.M;
+    float y[NY], var[NY];
+#pragma unroll
+    for (int o = 0; o < NY; ++o) {
+        y[o] = ybuf[o * SLOTS + tid];
+        var[o] = vbuf[o * SLOTS + tid];
+    }
+    float x[NX];
+#pragma unroll
+    for (int c = 0; c < NX; ++c) x[c] = xbuf[c * SLOTS + tid];
+    // running cost at (x_t, z_t), averaged over the sub-rollouts of k
+    qbuf[tid] = running_cost(a.cost, S.obs_s, x, var);
+    // sampled Euler step (Sec. 3.2)
+    float n[NY];
+    if (a.model_noise) {
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            float4 nb = box_muller4(noise_block(a.seed, (uint32_t)k, (uint32_t)t, (uint32_t)(b + 1), (uint32_t)m));
+            n[4 * b] = nb.x;
+            n[4 * b + 1] = nb.y;
+            n[4 * b + 2] = nb.z;
+            n[4 * b + 3] = nb.w;
+        }
+    } else {
+#pragma unroll
+        for (int o = 0; o < NY; ++o) n[o] = 0.0f;
+    }
+#pragma unroll
+    for (int c = 0; c < NX; ++c) {
+        float xdot = fmaf(sqrtf(var[c]), n[c], y[c]);
+        x[c] = fmaf(a.dt, xdot, x[c]);
+        xbuf[c * SLOTS + tid] = x[c];
+        zbuf[c * SLOTS + tid] = x[c];
+        yrbuf[c * SLOTS + tid] = y[c];
+    }
+    named_bar_sync(2, SLOTS);
+    if (writer) {
+        float qs = 0.0f;
+        for (int i = 0; i < M; ++i) qs += qbuf[tid + i];
+        a.cost_tk[(size_t)t * a.K + k] = qs / (float)M;
+    }
+    if (t + 1 < a.T) {
+        float4 nn = box_muller4(noise_block(a.seed, (uint32_t)k, (uint32_t)(t + 1), 0u, 0u));
+        float eps[4] = {a.sqrt_sigma_u[0] * nn.x, a.sqrt_sigma_u[1] * nn.y,
+                        a.sqrt_sigma_u[2] * nn.z, a.sqrt_sigma_u[3] * nn.w};
+#pragma unroll
+        for (int c = 0; c < NU; ++c) zbuf[(NX + c) * SLOTS + tid] = a.u_nom[(size_t)(t + 1) * NU + c] + eps[c];
+        if (writer) a.eps_tk[(size_t)(t + 1) * a.K + k] = make_float4(eps[0], eps[1], eps[2], eps[3]);
+    } else {
+        named_bar_sync(2, SLOTS);           // qbuf reads done before reuse
+        qbuf[tid] = terminal_cost(a.cost, x);
+        named_bar_sync(2, SLOTS);
+        if (writer) {
+            float ps = 0.0f;
+            for (int i = 0; i < M; ++i) ps += qbuf[tid + i];
+            a.phi[k] = ps / (float)M;
+        }
+    }
+}
+
 // Consumers (8 warps): evaluate the LWPR model for the 64 slots of one work
 // item starting at slot_base, step the dynamics and write the item's outputs.
 // `g` is the ring position (advanced in step with the producer).
 __device__ void fp32_consumer(const RolloutArgs &a, const Fp32Smem &S, long long slot_base, long long &g, bool &aborted)
 {
-    unsigned char *stage_base = S.stage_base;
-    float *part = S.part, *zbuf = S.zbuf, *xbuf = S.xbuf, *ybuf = S.ybuf, *vbuf = S.vbuf, *yrbuf = S.yrbuf,
-          *qbuf = S.qbuf;
-    float2 *obs_s = S.obs_s;
-    uint64_t *full = S.full, *empty = S.empty;
-    volatile int *abort_flag = S.abort_flag;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int P = a.P, spo = a.stages_per_out;
-    const int nsteps = a.T;
+    const int tid = threadIdx.x;
     const int M = a.M;
-    const int slotA = lane, slotB = lane + 32;
 
     // Step-thread state: thread tid < SLOTS owns slot tid.
     const bool stepper = tid < SLOTS;
@@ -268,147 +422,27 @@ __device__ void fp32_consumer(const RolloutArgs &a, const Fp32Smem &S, long long
     const int k = (int)(gslot / M), m = (int)(gslot % M);
     const bool writer = stepper && k < a.K && m == 0;
 
-    if (stepper) {
-        {
-            float4 n = box_muller4(noise_block(a.seed, (uint32_t)k, 0u, 0u, 0u));
-            float eps[4] = {a.sqrt_sigma_u[0] * n.x, a.sqrt_sigma_u[1] * n.y,
-                            a.sqrt_sigma_u[2] * n.z, a.sqrt_sigma_u[3] * n.w};
-#pragma unroll
-            for (int c = 0; c < NX; ++c) {
-                float xc = a.x0[c];
-                xbuf[c * SLOTS + tid] = xc;
-                zbuf[c * SLOTS + tid] = xc;
-            }
-#pragma unroll
-            for (int c = 0; c < NU; ++c) zbuf[(NX + c) * SLOTS + tid] = a.u_nom[c] + eps[c];
-#pragma unroll
-            for (int o = 0; o < NY; ++o) yrbuf[o * SLOTS + tid] = 0.0f;
-            if (writer) a.eps_tk[k] = make_float4(eps[0], eps[1], eps[2], eps[3]);
-        }
-    }
+    if (stepper) fp32_init_slot(a, S, tid, k, writer);
     named_bar_sync(1, NCONS);
 
-    for (int t = 0; t < nsteps; ++t) {
+    for (int t = 0; t < a.T; ++t) {
         float2 zA[NZ], zB[NZ];
-#pragma unroll
-        for (int c = 0; c < NZ; ++c) {
-            float va = zbuf[c * SLOTS + slotA], vb = zbuf[c * SLOTS + slotB];
-            zA[c] = make_float2(va, va);
-            zB[c] = make_float2(vb, vb);
-        }
+        fp32_load_z(S.zbuf, zA, zB);
         for (int o = 0; o < NY; ++o) {
-            const float ya = -yrbuf[o * SLOTS + slotA], yb = -yrbuf[o * SLOTS + slotB];
-            const float2 yrA = make_float2(ya, ya), yrB = make_float2(yb, yb);
-            Soft stA, stB;
-            soft_init(stA);
-            soft_init(stB);
-            for (int s = 0; s < spo; ++s, ++g) {
-                const int slot = (int)(g % NSTAGE);
-                if (!aborted &&
-                    !mbar_wait_bounded(&full[slot], (uint32_t)((g / NSTAGE) & 1), abort_flag)) {
-                    if (lane == 0) {
-                        if (!*abort_flag) atomicOr(a.err, DEVERR_TIMEOUT_FULL);
-                        *abort_flag = 1;
-                    }
-                    aborted = true;
-                }
-#pragma unroll 2
-                for (int j = 0; j < RF_PAIRS_PER_STAGE / CW; ++j) {
-                    const int pair = s * RF_PAIRS_PER_STAGE + j * CW + warp;
-                    if (!aborted && pair < P) {
-                        const float4 *r4 = reinterpret_cast<const float4 *>(
-                            stage_base + (size_t)slot * STAGE_BYTES + (size_t)(j * CW + warp) * REC_BYTES);
-                        process_pair(r4, zA, zB, yrA, yrB, stA, stB);
-                    }
-                }
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&empty[slot]);
-            }
-            float *pb = part + (o & 1) * PART_BUF;
-            pb[(warp * 5 + 0) * SLOTS + slotA] = stA.m;
-            pb[(warp * 5 + 1) * SLOTS + slotA] = stA.s0;
-            pb[(warp * 5 + 2) * SLOTS + slotA] = stA.s1;
-            pb[(warp * 5 + 3) * SLOTS + slotA] = stA.s2;
-            pb[(warp * 5 + 4) * SLOTS + slotA] = stA.s3;
-            pb[(warp * 5 + 0) * SLOTS + slotB] = stB.m;
-            pb[(warp * 5 + 1) * SLOTS + slotB] = stB.s0;
-            pb[(warp * 5 + 2) * SLOTS + slotB] = stB.s1;
-            pb[(warp * 5 + 3) * SLOTS + slotB] = stB.s2;
-            pb[(warp * 5 + 4) * SLOTS + slotB] = stB.s3;
+            const int lane = tid & 31;
+            float *pb = S.part + (o & 1) * PART_BUF;
+            fp32_output_pass(a, S, zA, zB, -S.yrbuf[o * SLOTS + lane], -S.yrbuf[o * SLOTS + lane + 32], pb, g,
+                             aborted);
             named_bar_sync(1, NCONS);
             if (stepper) {
                 float y, var;
-                merge_partials(pb, tid, yrbuf[o * SLOTS + tid], y, var);
-                ybuf[o * SLOTS + tid] = y;
-                vbuf[o * SLOTS + tid] = var;
+                merge_partials(pb, tid, S.yrbuf[o * SLOTS + tid], y, var);
+                S.ybuf[o * SLOTS + tid] = y;
+                S.vbuf[o * SLOTS + tid] = var;
             }
         }
-
-        if (stepper) {
-            float y[NY], var[NY];
-#pragma unroll
-            for (int o = 0; o < NY; ++o) {
-                y[o] = ybuf[o * SLOTS + tid];
-                var[o] = vbuf[o * SLOTS + tid];
-            }
-            {
-                float x[NX];
-#pragma unroll
-                for (int c = 0; c < NX; ++c) x[c] = xbuf[c * SLOTS + tid];
-                // running cost at (x_t, z_t), averaged over the sub-rollouts of k
-                qbuf[tid] = running_cost(a.cost, obs_s, x, var);
-                // sampled Euler step (Sec. 3.2)
-                float n[NY];
-                if (a.model_noise) {
-#pragma unroll
-                    for (int b = 0; b < 3; ++b) {
-                        float4 nb = box_muller4(noise_block(a.seed, (uint32_t)k, (uint32_t)t,
-                                                            (uint32_t)(b + 1), (uint32_t)m));
-                        n[4 * b] = nb.x;
-                        n[4 * b + 1] = nb.y;
-                        n[4 * b + 2] = nb.z;
-                        n[4 * b + 3] = nb.w;
-                    }
-                } else {
-#pragma unroll
-                    for (int o = 0; o < NY; ++o) n[o] = 0.0f;
-                }
-#pragma unroll
-                for (int c = 0; c < NX; ++c) {
-                    float xdot = fmaf(sqrtf(var[c]), n[c], y[c]);
-                    x[c] = fmaf(a.dt, xdot, x[c]);
-                    xbuf[c * SLOTS + tid] = x[c];
-                    zbuf[c * SLOTS + tid] = x[c];
-                    yrbuf[c * SLOTS + tid] = y[c];
-                }
-                named_bar_sync(2, SLOTS);
-                if (writer) {
-                    float qs = 0.0f;
-                    for (int i = 0; i < M; ++i) qs += qbuf[tid + i];
-                    a.cost_tk[(size_t)t * a.K + k] = qs / (float)M;
-                }
-                if (t + 1 < a.T) {
-                    float4 nn = box_muller4(noise_block(a.seed, (uint32_t)k, (uint32_t)(t + 1), 0u, 0u));
-                    float eps[4] = {a.sqrt_sigma_u[0] * nn.x, a.sqrt_sigma_u[1] * nn.y,
-                                    a.sqrt_sigma_u[2] * nn.z, a.sqrt_sigma_u[3] * nn.w};
-#pragma unroll
-                    for (int c = 0; c < NU; ++c)
-                        zbuf[(NX + c) * SLOTS + tid] = a.u_nom[(size_t)(t + 1) * NU + c] + eps[c];
-                    if (writer)
-                        a.eps_tk[(size_t)(t + 1) * a.K + k] = make_float4(eps[0], eps[1], eps[2], eps[3]);
-                } else {
-                    named_bar_sync(2, SLOTS);           // qbuf reads done before reuse
-                    qbuf[tid] = terminal_cost(a.cost, x);
-                    named_bar_sync(2, SLOTS);
-                    if (writer) {
-                        float ps = 0.0f;
-                        for (int i = 0; i < M; ++i) ps += qbuf[tid + i];
-                        a.phi[k] = ps / (float)M;
-                    }
-                }
-            }
-        }
-        const bool any_abort = bar_sync_or(3, NCONS, aborted || *abort_flag != 0);
+        if (stepper) fp32_step_slot(a, S, t, tid, k, m, writer);
+        const bool any_abort = bar_sync_or(3, NCONS, aborted || *S.abort_flag != 0);
         if (any_abort) break;
     }
 }
@@ -434,6 +468,340 @@ __global__ void __launch_bounds__(NTHREADS, 1) rollout_fp32_kernel(const __grid_
     long long g = 0;
     bool aborted = false;
     fp32_consumer(a, S, (long long)blockIdx.x * SLOTS, g, aborted);
+}
+
+// ---------------------------------------------------------------------------
+// Output-split launch.  With fewer 64-slot blocks than SMs, the one-CTA-per-
+// block launch leaves SMs idle (K = 8192: 128 blocks on 148 SMs).  Here the
+// (block, output) units of all blocks, unit = b * NY + o, are dealt out in
+// runs of `upc` consecutive units to gridDim.x co-resident CTAs (one per SM,
+// a cooperative launch), upc = ceil(blocks * NY / SMs) < NY.  Each CTA's run
+// covers the end of at most one block (its *owned* block, whose slots it
+// steps) and the start or middle of at most one other (a *non-owned*
+// segment).  Every output of a block is evaluated by one CTA with the same
+// warps, records and merge as in rollout_fp32_kernel, and the owner steps
+// the dynamics with the same code, so the results are identical bit for bit.
+//
+// Per step t, through the exchange area in global memory (L2):
+//   - a non-owned segment waits until the owner has published z_t of its
+//     block (ready >= t + 1), evaluates its outputs and writes their y and
+//     var, then raises its done flag to t + 1;
+//   - the owner evaluates its own outputs, waits for the done flags of the
+//     block's other CTAs, reads their y and var, steps the dynamics and
+//     publishes z_{t+1} (ready = t + 2).
+// Each CTA evaluates its non-owned segment first, so the step's waits point
+// only to work that the other CTAs do first in their own step: no wait can
+// close a cycle.  Flags hold (epoch << 32 | count) with a per-launch epoch,
+// so no flag needs clearing between launches.  Every wait is bounded; on
+// expiry the CTA flags DEVERR_TIMEOUT_PEER, stores its epoch into the abort
+// word (the other CTAs' waits then give up at once) and leaves at the end of
+// the step like any aborted CTA.
+// ---------------------------------------------------------------------------
+constexpr int OFF_ZH = (SMEM_BYTES + 15) / 16 * 16;                 // [NZ][SLOTS] z of the non-owned block
+constexpr int OFF_YRH = OFF_ZH + NZ * SLOTS * 4;                     // [NY][SLOTS] its reference means
+constexpr int OFF_SOK = OFF_YRH + NY * SLOTS * 4;                    // stepper decision word
+constexpr int SPLIT_SMEM_BYTES = OFF_SOK + 16;
+static_assert(SPLIT_SMEM_BYTES <= 232448, "shared memory budget");
+constexpr size_t SB_READY = 0, SB_DONE = 8, SB_Z = 128, SB_Y = SB_Z + NZ * SLOTS * 4, SB_V = SB_Y + NY * SLOTS * 4;
+static_assert(SB_V + NY * SLOTS * 4 == SPLIT_BLOCK_BYTES && SB_DONE + NY * 8 <= SB_Z, "exchange block layout");
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p)
+{
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p)
+{
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_u64(unsigned long long *p, unsigned long long v)
+{
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// One CTA's share of the units.  Segments are listed in evaluation order:
+// the non-owned one (if any) first.
+struct SplitPlan {
+    int nseg;
+    int b[2], o0[2], o1[2], part[2];   // block, outputs [o0, o1), index among the block's non-owners
+    bool owned[2];
+    int nparts;                        // owned block: CTAs before this one that hold some of its outputs
+    int own;                           // segment index of the owned block, or -1
+};
+
+__device__ __forceinline__ SplitPlan split_plan(int cta, int upc, int units)
+{
+    SplitPlan p{};
+    const int s = cta * upc, e = min(s + upc, units);
+    const int b1 = s / NY, end1 = (b1 + 1) * NY;
+    const bool own1 = e >= end1;
+    int n = 0;
+    if (e > end1) {   // the start of block b1 + 1, owned by a later CTA
+        p.b[n] = b1 + 1;
+        p.o0[n] = 0;
+        p.o1[n] = e - end1;
+        p.owned[n] = false;
+        p.part[n] = cta - ((b1 + 1) * NY) / upc;
+        ++n;
+    }
+    p.b[n] = b1;
+    p.o0[n] = s - b1 * NY;
+    p.o1[n] = min(e, end1) - b1 * NY;
+    p.owned[n] = own1;
+    p.part[n] = cta - (b1 * NY) / upc;
+    p.own = own1 ? n : -1;
+    p.nparts = own1 ? cta - (b1 * NY) / upc : 0;
+    p.nseg = n + 1;
+    return p;
+}
+
+// Bounded wait until *flag >= target; gives up when the abort word holds this
+// launch's tag or after WAIT_LIMIT_NS.
+__device__ __forceinline__ bool split_wait(const unsigned long long *flag, unsigned long long target, const unsigned long long *abortw,
+                           unsigned long long tag)
+{
+    if (ld_acquire_u64(flag) >= target) return true;
+    const unsigned long long t0 = globaltimer();
+    for (uint32_t it = 1;; ++it) {
+        // a plain spin: the rest of the CTA waits at a barrier meanwhile, so
+        // the poll takes no issue slots from work
+        if (ld_acquire_u64(flag) >= target) return true;
+        if ((it & 63u) == 0u) {
+            if (ld_relaxed_u64(abortw) == tag) return false;
+            if (globaltimer() - t0 > WAIT_LIMIT_NS) return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void split_fail(const RolloutArgs &a, const Fp32Smem &S, unsigned long long *abortw,
+                                           unsigned long long tag)
+{
+    if (ld_relaxed_u64(abortw) != tag) atomicOr(a.err, DEVERR_TIMEOUT_PEER);
+    st_release_u64(abortw, tag);
+    *S.abort_flag = 1;
+}
+
+// Exchange block b of the split area.
+__device__ __forceinline__ unsigned char *split_blk(const RolloutArgs &a, int b)
+{
+    return a.split + SPLIT_HDR_BYTES + (size_t)b * SPLIT_BLOCK_BYTES;
+}
+
+__device__ __forceinline__ unsigned long long split_tag(const RolloutArgs &a)
+{
+    return (unsigned long long)a.split_epoch << 32;
+}
+
+// Per-CTA unit table of the split kernel (shared memory): unit u of a step
+// evaluates output uo[u] of the owned block (UF_OWNED) or of the non-owned
+// one; UF_FIRST / UF_LAST mark the first and last unit of a segment.
+constexpr int UF_OWNED = 1, UF_FIRST = 2, UF_LAST = 4;
+struct SplitUnits {
+    int n;                 // units per step
+    int uo[NY], uf[NY];
+    int bN, partN;         // non-owned segment (bN < 0: none): block, index among its non-owners
+    int o0N, o1N;          // its outputs
+    int bO, o0O, npartsO;  // owned block (bO < 0: none), its first output, CTAs before this one holding its outputs
+};
+
+__device__ __forceinline__ void split_units(const SplitPlan &p, SplitUnits &u)
+{
+    u.n = 0;
+    u.bN = -1;
+    u.partN = 0;
+    u.o0N = u.o1N = 0;
+    u.bO = -1;
+    u.o0O = 0;
+    u.npartsO = 0;
+    for (int si = 0; si < p.nseg; ++si) {
+        for (int o = p.o0[si]; o < p.o1[si]; ++o) {
+            u.uo[u.n] = o;
+            u.uf[u.n] = (p.owned[si] ? UF_OWNED : 0) | (o == p.o0[si] ? UF_FIRST : 0) | (o + 1 == p.o1[si] ? UF_LAST : 0);
+            ++u.n;
+        }
+        if (p.owned[si]) {
+            u.bO = p.b[si];
+            u.o0O = p.o0[si];
+            u.npartsO = p.nparts;
+        } else {
+            u.bN = p.b[si];
+            u.partN = p.part[si];
+            u.o0N = p.o0[si];
+            u.o1N = p.o1[si];
+        }
+    }
+}
+
+// One segment of a split CTA's step: outputs [o0, o1) of the owned block
+// (OWNED; z, reference means, y and var in the CTA's own buffers) or of the
+// non-owned one (z in zH, reference means in yrH, y and var to the exchange
+// block bb).  Each instantiation is the plain kernel's output loop: z loaded
+// once before it, nothing else live across the record loop but the loop
+// bound and the partial-buffer parity.
+__shared__ SplitUnits s_split;   // the split kernel's unit table (static shared memory)
+
+template <bool OWNED>
+__device__ __forceinline__ void fp32_split_segment(const RolloutArgs &a, const Fp32Smem &S, const float *zsrc, float *yrs,
+                                                   int o0, int o1, int &par, long long &g, bool &aborted)
+{
+    const int tid = threadIdx.x, lane = tid & 31;
+    float2 zA[NZ], zB[NZ];
+    fp32_load_z(zsrc, zA, zB);
+    for (int o = o0; o < o1; ++o) {
+        float *pb = S.part + (par & 1) * PART_BUF;
+        ++par;
+        fp32_output_pass(a, S, zA, zB, -yrs[o * SLOTS + lane], -yrs[o * SLOTS + lane + 32], pb, g, aborted);
+        named_bar_sync(1, NCONS);
+        if (tid < SLOTS) {
+            float y, var;
+            merge_partials(pb, tid, yrs[o * SLOTS + tid], y, var);
+            if (OWNED) {
+                S.ybuf[o * SLOTS + tid] = y;
+                S.vbuf[o * SLOTS + tid] = var;
+            } else {
+                // the exchange block is found again here rather than kept in
+                // registers across the record loop
+                unsigned char *bb = split_blk(a, *(volatile int *)&s_split.bN);
+                __stcg(reinterpret_cast<float *>(bb + SB_Y) + o * SLOTS + tid, y);
+                __stcg(reinterpret_cast<float *>(bb + SB_V) + o * SLOTS + tid, var);
+                yrs[o * SLOTS + tid] = y;
+            }
+        }
+    }
+}
+
+// Consumers of the split kernel: per step the non-owned segment (after the
+// owner has published its block's z), then the owned one, then the owned
+// block's dynamics (after the other CTAs' outputs of it have arrived).
+__device__ __forceinline__ void fp32_split_consumer(const RolloutArgs &a, const Fp32Smem &S, const volatile SplitUnits &U,
+                                                    float *zH, float *yrH, volatile int *s_ok)
+{
+    const int tid = threadIdx.x;
+    const bool stepper = tid < SLOTS;
+    unsigned long long *abortw = reinterpret_cast<unsigned long long *>(a.split);
+    long long g = 0;
+    bool aborted = false;
+
+    if (stepper) {
+#pragma unroll
+        for (int o = 0; o < NY; ++o) yrH[o * SLOTS + tid] = 0.0f;
+        if (U.bO >= 0) {
+            const long long gslot = (long long)U.bO * SLOTS + tid;
+            const int k = (int)(gslot / a.M), m = (int)(gslot % a.M);
+            fp32_init_slot(a, S, tid, k, k < a.K && m == 0);
+            unsigned char *ob = split_blk(a, U.bO);
+            float *zg = reinterpret_cast<float *>(ob + SB_Z);
+#pragma unroll
+            for (int c = 0; c < NZ; ++c) __stcg(&zg[c * SLOTS + tid], S.zbuf[c * SLOTS + tid]);
+            named_bar_sync(2, SLOTS);
+            if (tid == 0) st_release_u64(reinterpret_cast<unsigned long long *>(ob + SB_READY), split_tag(a) | 1ull);
+        }
+    }
+    named_bar_sync(1, NCONS);
+
+    int par = 0;   // partial-buffer parity, alternating over the CTA's units
+    for (int t = 0; t < a.T; ++t) {
+        if (U.bN >= 0) {
+            unsigned char *bb = split_blk(a, U.bN);
+            if (stepper) {
+                if (tid == 0 && !aborted &&
+                    !split_wait(reinterpret_cast<const unsigned long long *>(bb + SB_READY),
+                                split_tag(a) | (unsigned long long)(t + 1), abortw, split_tag(a))) {
+                    split_fail(a, S, abortw, split_tag(a));
+                    aborted = true;
+                }
+                named_bar_sync(2, SLOTS);
+                const float *zg = reinterpret_cast<const float *>(bb + SB_Z);
+#pragma unroll
+                for (int c = 0; c < NZ; ++c) zH[c * SLOTS + tid] = __ldcg(&zg[c * SLOTS + tid]);
+            }
+            named_bar_sync(1, NCONS);
+            fp32_split_segment<false>(a, S, zH, yrH, U.o0N, U.o1N, par, g, aborted);
+            if (stepper) {
+                named_bar_sync(2, SLOTS);
+                if (tid == 0)
+                    st_release_u64(reinterpret_cast<unsigned long long *>(split_blk(a, U.bN) + SB_DONE) + U.partN,
+                                   split_tag(a) | (unsigned long long)(t + 1));
+            }
+        }
+        if (U.bO >= 0) {
+            fp32_split_segment<true>(a, S, S.zbuf, S.yrbuf, U.o0O, NY, par, g, aborted);
+            if (stepper) {
+                unsigned char *ob = split_blk(a, U.bO);
+                if (tid == 0) {
+                    bool ok = !aborted && *S.abort_flag == 0;
+                    for (int p = 0; ok && p < U.npartsO; ++p)
+                        ok = split_wait(reinterpret_cast<const unsigned long long *>(ob + SB_DONE) + p,
+                                        split_tag(a) | (unsigned long long)(t + 1), abortw, split_tag(a));
+                    if (!ok && !aborted) {
+                        split_fail(a, S, abortw, split_tag(a));
+                        aborted = true;
+                    }
+                    *s_ok = ok ? 1 : 0;
+                }
+                named_bar_sync(2, SLOTS);
+                if (*s_ok) {
+                    const float *yg = reinterpret_cast<const float *>(ob + SB_Y), *vg = reinterpret_cast<const float *>(ob + SB_V);
+                    for (int o = 0; o < U.o0O; ++o) {
+                        S.ybuf[o * SLOTS + tid] = __ldcg(&yg[o * SLOTS + tid]);
+                        S.vbuf[o * SLOTS + tid] = __ldcg(&vg[o * SLOTS + tid]);
+                    }
+                    const long long gslot = (long long)U.bO * SLOTS + tid;
+                    const int k = (int)(gslot / a.M), m = (int)(gslot % a.M);
+                    fp32_step_slot(a, S, t, tid, k, m, k < a.K && m == 0);
+                    if (t + 1 < a.T) {
+                        float *zg = reinterpret_cast<float *>(ob + SB_Z);
+#pragma unroll
+                        for (int c = 0; c < NZ; ++c) __stcg(&zg[c * SLOTS + tid], S.zbuf[c * SLOTS + tid]);
+                        named_bar_sync(2, SLOTS);
+                        if (tid == 0)
+                            st_release_u64(reinterpret_cast<unsigned long long *>(ob + SB_READY),
+                                           split_tag(a) | (unsigned long long)(t + 2));
+                    }
+                }
+            }
+        }
+        const bool any_abort = bar_sync_or(3, NCONS, aborted || *S.abort_flag != 0);
+        if (any_abort) {
+            if (tid == 0) st_release_u64(abortw, split_tag(a));   // the other CTAs stop waiting for this one
+            break;
+        }
+    }
+}
+
+// Release stores after a CTA barrier: the barrier orders the other stepper
+// threads' stores before thread 0's release, which makes them visible to the
+// CTA that acquires the flag (the acquirer's threads then read after their own
+// barrier, through L2).
+__global__ void __launch_bounds__(NTHREADS, 1) rollout_fp32_split_kernel(const __grid_constant__ RolloutArgs a)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    SplitUnits &s_units = s_split;
+    const Fp32Smem S = fp32_smem(smem);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        const int blocks = (int)(((long long)a.K * a.M + SLOTS - 1) / SLOTS);
+        split_units(split_plan((int)blockIdx.x, a.split_upc, blocks * NY), s_units);
+        fp32_init_barriers(S);
+    }
+    for (int i = tid; i < a.cost.n_obs; i += NTHREADS) S.obs_s[i] = a.cost.obs[i];
+    __syncthreads();
+    const volatile SplitUnits &pl = s_units;
+    if (warp == CW) {
+        if (lane != 0) return;
+        long long issued = 0;
+        fp32_produce(a, S, 0, issued, pl.n, [&](int i) { return pl.uo[i]; });
+        for (long long g = (issued > NSTAGE ? issued - NSTAGE : 0); g < issued; ++g)
+            if (!mbar_wait_drain(&S.full[g % NSTAGE], (uint32_t)((g / NSTAGE) & 1))) atomicOr(a.err, DEVERR_TIMEOUT_DRAIN);
+        return;
+    }
+    fp32_split_consumer(a, S, pl, reinterpret_cast<float *>(smem + OFF_ZH), reinterpret_cast<float *>(smem + OFF_YRH),
+                        reinterpret_cast<volatile int *>(smem + OFF_SOK));
 }
 
 // Persistent batched form: CTAs take (controller, slot block) work items from
@@ -644,10 +1012,50 @@ cudaError_t launch_impl(const RolloutArgs &a, cudaStream_t s, long long slots)
 
 }  // namespace
 
+std::atomic<uint64_t> g_split_attr;
+
+int fp32_split_upc(const RolloutArgs &a)
+{
+    if (!a.split || a.split_mode == PI_SPLIT_OFF || a.K < 1 || a.M < 1) return 0;
+    const long long blocks = ((long long)a.K * a.M + SLOTS - 1) / SLOTS;
+    if (blocks > a.split_max_blocks) return 0;
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0)
+        return 0;
+    const long long upc = (blocks * NY + nsm - 1) / nsm;
+    if (upc >= NY) return 0;
+    // In auto mode, split only where the per-step work it takes off the
+    // busiest CTA (NY - upc outputs of P records) clearly outweighs the two
+    // flag round trips through L2 that it adds to each step.
+    if (a.split_mode == PI_SPLIT_AUTO && (NY - upc) * (long long)a.P < 64) return 0;
+    return (int)upc;
+}
+
 cudaError_t launch_rollout_fp32(const RolloutArgs &a, cudaStream_t s)
 {
     if (a.M < 1 || a.M > SLOTS || (a.M & (a.M - 1)) != 0) return cudaErrorInvalidValue;
-    return launch_impl(a, s, (long long)a.K * a.M);
+    const int upc = fp32_split_upc(a);
+    if (upc <= 0) return launch_impl(a, s, (long long)a.K * a.M);
+    if (a.cost.n_obs > MAX_OBS || a.P <= 0 || a.stages_per_out <= 0 || a.split_epoch == 0)
+        return cudaErrorInvalidValue;
+    cudaError_t e = set_smem_once(g_split_attr, rollout_fp32_split_kernel, SPLIT_SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    RolloutArgs b = a;
+    b.split_upc = upc;
+    const int grid = fp32_split_grid(a, upc) - (a.split_drop > 0 ? 1 : 0);
+    if (grid < 1) return cudaErrorInvalidValue;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(NTHREADS);
+    cfg.dynamicSmemBytes = SPLIT_SMEM_BYTES;
+    cfg.stream = s;
+    at[0].id = cudaLaunchAttributeCooperative;   // every CTA resident at once: they wait on one another
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, rollout_fp32_split_kernel, b);
 }
 
 cudaError_t launch_predict_fp32(const RolloutArgs &a, cudaStream_t s)

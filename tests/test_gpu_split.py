@@ -1,0 +1,128 @@
+"""Output-split launch of the FP32 rollout (pi_set_output_split).
+
+With fewer 64-slot blocks than SMs, the split launch deals the (block, output)
+units out to one co-resident CTA per SM, which exchange each step's state
+through device memory.  Every output is still evaluated by one CTA with the
+same records, order and merge (Sec. 2, Eq. 1), so the update must equal the
+plain launch's bit for bit: u_out, costs, and (through pi_debug_rollout) the
+per-step costs and perturbations.  The cases cover one block, a ragged last
+block, sub-rollouts, mean-only noise, T = 1, blocks spread over up to 12 CTAs
+(one output each) and the realtime shape (128 blocks, 11 units per CTA); the
+oracle parity of the split path is covered by the end-to-end and full-size
+tests, which run it in the default mode.  The failure test leaves the last
+CTA out of the grid: the waits on it must give up, report PI_ERR_TIMEOUT and
+leave the context usable."""
+import numpy as np
+import pytest
+import torch
+
+from paper_1503_00330_b300 import _lib
+from paper_1503_00330_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1503_00330_b300 import build
+    build.build()
+
+
+def _problem(K, T, L, seed, M=1, noise="sampled"):
+    p = W.problem(K, T, L, seed=seed, n_obs=5, M=M)
+    p.model_noise = noise == "sampled"
+    p.u_nom = np.random.default_rng(seed).normal(0, 0.2, (T, 4)).astype(np.float32)
+    p.x0 = np.random.default_rng(seed + 1).normal(0, 0.1, 12).astype(np.float32)
+    return p
+
+
+# (K, T, L, M, noise): plan checked below
+CASES = [
+    (1, 6, 33, 1, "sampled"),          # one block, 12 CTAs of one output each
+    (256, 20, 64, 1, "sampled"),       # 4 blocks, one output per CTA
+    (1000, 15, 33, 1, "sampled"),      # ragged last block (1000 = 15 x 64 + 40)
+    (300, 12, 40, 4, "sampled"),       # sub-rollouts: 1200 slots, 19 blocks
+    (700, 9, 130, 1, "mean_only"),     # deterministic dynamics
+    (129, 1, 17, 1, "sampled"),        # T = 1
+    (8192, 6, 512, 1, "sampled"),      # realtime shape: 128 blocks, 11 units per CTA
+]
+
+
+@pytest.mark.parametrize("K,T,L,M,noise", CASES)
+def test_split_equals_plain_bitwise(K, T, L, M, noise):
+    from paper_1503_00330_b300.api import Controller
+    p = _problem(K, T, L, seed=K + T + L, M=M, noise=noise)
+    ctl = Controller(p.model, p.cost, M=p.M, model_noise=p.model_noise, precision="fp32")
+    ctl.set_output_split("always")
+    upc, ctas = ctl.split_plan(p.K)
+    blocks = -(-p.K * p.M // 64)
+    assert 0 < upc < 12 and ctas == -(-blocks * 12 // upc) and ctas <= torch.cuda.get_device_properties(0).multi_processor_count
+    outs = {}
+    for mode in ("always", "off", "always"):
+        ctl.set_output_split(mode)
+        u, c = ctl.update(p.x0, p.u_nom, p.K, p.T, p.lam, p.sigma_u, p.seed)
+        ctl.sync()
+        outs.setdefault(mode, []).append((u.clone(), c.clone()))
+    (u_s, c_s), (u_s2, c_s2) = outs["always"]
+    u_p, c_p = outs["off"][0]
+    print(f"K={K} T={T} L={L} M={M}: {ctas} CTAs x {upc} units, plain {blocks} blocks")
+    assert torch.equal(u_s, u_p) and torch.equal(c_s, c_p), "split launch differs from the plain launch"
+    assert torch.equal(u_s2, u_s) and torch.equal(c_s2, c_s), "repeated split launch differs"
+    ctl.close()
+
+
+def test_split_rollout_stage_bitwise():
+    """Per-step costs, perturbations and terminal costs of the rollout stage alone."""
+    from paper_1503_00330_b300.api import Controller
+    p = _problem(2000, 11, 96, seed=4, M=2)
+    ctl = Controller(p.model, p.cost, M=p.M, precision="fp32")
+    res = {}
+    for mode in ("always", "off"):
+        ctl.set_output_split(mode)
+        res[mode] = [t.cpu().numpy() for t in ctl.debug_rollout(p.x0, p.u_nom, p.K, p.T, p.sigma_u, p.seed)]
+        ctl.sync()
+    for a, b in zip(res["always"], res["off"]):
+        assert np.array_equal(a, b)
+    ctl.close()
+
+
+def test_auto_mode_plan():
+    """Default mode: the realtime update (128 blocks) is split over all SMs in
+    runs of 11 units; a launch that fills the SMs and a tiny model are not split."""
+    from paper_1503_00330_b300.api import Controller
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    p = _problem(8, 2, 512, seed=1)
+    ctl = Controller(p.model, p.cost, precision="fp32")
+    upc, ctas = ctl.split_plan(8192)
+    assert upc == -(-128 * 12 // nsm) and ctas == -(-128 * 12 // upc)
+    assert ctl.split_plan(64 * nsm) == (0, nsm)
+    ctl.close()
+    q = _problem(8, 2, 5, seed=1)   # 3 field pairs per output: (12 - 1) * 3 < 64
+    ctl = Controller(q.model, q.cost, precision="fp32")
+    assert ctl.split_plan(256) == (0, 4)
+    ctl.set_output_split("always")
+    assert ctl.split_plan(256)[0] == 1
+    ctl.close()
+
+
+def test_split_peer_wait_times_out_and_context_recovers():
+    from paper_1503_00330_b300.api import Controller
+    p = _problem(640, 4, 64, seed=9)
+    ctl = Controller(p.model, p.cost, precision="fp32")
+    ctl.set_output_split("always")
+    u_ref, c_ref = ctl.update(p.x0, p.u_nom, p.K, p.T, p.lam, p.sigma_u, p.seed)
+    ctl.sync()
+    u_ref, c_ref = u_ref.clone(), c_ref.clone()
+    lib = _lib.load()
+    _lib.check(lib.pi_debug_split_drop_cta(ctl.handle, 1))
+    ctl.update(p.x0, p.u_nom, p.K, p.T, p.lam, p.sigma_u, p.seed)
+    with pytest.raises(_lib.PiError) as ei:
+        ctl.sync()
+    assert ei.value.code == _lib.PI_ERR_TIMEOUT
+    _lib.check(lib.pi_debug_split_drop_cta(ctl.handle, 0))
+    u, c = ctl.update(p.x0, p.u_nom, p.K, p.T, p.lam, p.sigma_u, p.seed)
+    ctl.sync()
+    assert torch.equal(u, u_ref) and torch.equal(c, c_ref)
+    ctl.close()
