@@ -194,7 +194,10 @@ int pi_update(pi_ctx *ctx, const float *x0, const float *u_nominal, int K, int T
  * of about 21 MiB inside the library, held by every GPU that loads the library
  * until the process exits.  Limits: K <= PI2RH_NOALLOC_MAX_K,
  * T <= PI2RH_NOALLOC_MAX_T, K*T <= PI2RH_NOALLOC_MAX_KT; larger sizes return
- * PI_ERR_INVALID_ARG with a message and launch nothing.
+ * PI_ERR_INVALID_ARG with a message and launch nothing.  On an FP32 context
+ * the output-split launch of the rollout (pi_set_output_split) exchanges its
+ * per-step state through the context's own 1.5 MB area, which pi_create
+ * allocated, so it too needs no allocation here.
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) and caches it.  Under CUDA's lazy module loading
  * (the default) that lookup is also when the runtime loads the array onto the

@@ -8,9 +8,10 @@
 // allocate behind its back.  Such a caller creates its pi_ctx during set-up
 // and then calls this entry point in its loop.
 //
-// It runs the rollout kernel of the context's form (FP32 or tensor cores), then
-// the same scan and merge kernels as pi_update, so its results are those of
-// pi_update bit for bit.  Instead of the context's growable scratch, this path keeps the per-update
+// It runs the rollout kernel of the context's form (FP32 or tensor cores; an
+// FP32 context's output-split launch uses the exchange area that pi_create
+// allocated), then the same scan and merge kernels as pi_update, so its
+// results are those of pi_update bit for bit.  Instead of the context's growable scratch, this path keeps the per-update
 // scratch (cost [T][K], eps [T][K][4], phi [K], log-sum-exp partials) in one
 // file-scope device array of fixed size, NOALLOC_BYTES (about 21 MiB), which
 // every GPU that loads the library holds until the process exits.  The
