@@ -374,11 +374,14 @@ def clock_scaled(peaks, clocks, achieved):
 
 def fp32_launch(ctl, K):
     """(kernel name, ncu summary file stem) of the FP32 rollout launch for K rollouts."""
-    upc, ctas = ctl.split_plan(K)
-    if upc:
+    plain, upc, ctas = ctl.split_plan(K)
+    if upc and not plain:
         return (f"rollout_fp32_split_kernel (output-split launch: {ctas} CTAs x {upc} (block, output) units)",
                 "rollout_fp32_split")
-    return f"rollout_fp32_kernel ({ctas} CTAs, one per 64-slot block)", "rollout_fp32"
+    if upc:
+        return (f"rollout_fp32_kernel ({plain} CTAs, one per 64-slot block) + rollout_fp32_split_kernel "
+                f"(the last partial wave: {ctas} CTAs x {upc} units)", "rollout_fp32")
+    return f"rollout_fp32_kernel ({plain} CTAs, one per 64-slot block)", "rollout_fp32"
 
 
 def form_roofline(precision, rollout_ms, K, T, M, L, dev, peaks, workload, clocks=None, launch=None):

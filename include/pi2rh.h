@@ -241,12 +241,14 @@ int pi_rh_advance(pi_ctx *ctx, float *x0, const float *u_out, int T, float *u_no
  * area in device memory allocated by pi_create; every output is still
  * evaluated by one CTA in the same order, so the results are identical bit
  * for bit (Sec. 2, Eq. 1: the split changes which SM evaluates which
- * receptive fields, not the arithmetic).
+ * receptive fields, not the arithmetic).  With more blocks than SMs, whole
+ * waves of blocks keep the plain launch and only the blocks of the last,
+ * partial wave are split (two launches).
  *   PI_SPLIT_OFF     always the plain launch
- *   PI_SPLIT_AUTO    (default) the split launch where it takes work off the
- *                    busiest SM: fewer than ~11/12 as many blocks as SMs and
- *                    (12 - outputs per CTA) * ceil(L / 2) >= 64
- *   PI_SPLIT_ALWAYS  the split launch whenever it takes work off the busiest SM
+ *   PI_SPLIT_AUTO    (default) split the partial wave where that takes work
+ *                    off the busiest SM: fewer than ~11/12 as many blocks in
+ *                    it as SMs and (12 - outputs per CTA) * ceil(L / 2) >= 64
+ *   PI_SPLIT_ALWAYS  split it whenever that takes work off the busiest SM
  * A bounded wait of one CTA on another that expires shows as PI_ERR_TIMEOUT
  * from pi_sync.  Errors: INVALID_ARG (mode). */
 int pi_set_output_split(pi_ctx *ctx, int mode);
@@ -553,11 +555,12 @@ int pi_debug_reduce(pi_ctx *ctx, const float *cost, const float *phi, const floa
 int pi_debug_wait_timeout(pi_ctx *ctx, int64_t limit_ns);
 
 /* The launch an FP32 update of K rollouts (with the context's M and split
- * mode) would use: *units_per_cta = (block, output) units per CTA of the
- * output-split launch and *ctas its grid, or 0 and the number of 64-slot
- * blocks for the plain launch.  Host only; INVALID_ARG on a tensor-core
- * context or K < 1. */
-int pi_debug_split_plan(pi_ctx *ctx, int K, int *units_per_cta, int *ctas);
+ * mode) would use: *plain_blocks 64-slot blocks one CTA each, then, if
+ * *units_per_cta > 0, the remaining blocks as the output-split launch of
+ * *ctas CTAs with that many (block, output) units each (*ctas = 0 when there
+ * is no split launch).  Host only; INVALID_ARG on a tensor-core context or
+ * K < 1. */
+int pi_debug_split_plan(pi_ctx *ctx, int K, int *plain_blocks, int *units_per_cta, int *ctas);
 
 /* Failure path of the output-split launch's waits between CTAs, exercised
  * without a fault: with drop = 1 the next split launches leave out their last

@@ -102,7 +102,8 @@ _SIGS = {
     "pi_rh_advance": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _vp]),
     "pi_set_timing": (ctypes.c_int, [_vp, ctypes.c_int]),
     "pi_set_output_split": (ctypes.c_int, [_vp, ctypes.c_int]),
-    "pi_debug_split_plan": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    "pi_debug_split_plan": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                           ctypes.POINTER(ctypes.c_int)]),
     "pi_debug_split_drop_cta": (ctypes.c_int, [_vp, ctypes.c_int]),
     "pi_stage_times": (ctypes.c_int, [_vp, _fp]),
     "pi_stage_times_at": (ctypes.c_int, [_vp, ctypes.c_int, _fp]),

@@ -133,11 +133,12 @@ class Controller:
         check(self._lib.pi_set_output_split(self._h, modes[mode]))
 
     def split_plan(self, K: int):
-        """(units_per_cta, ctas) of the FP32 rollout launch for K rollouts:
-        units_per_cta = 0 for the plain launch (ctas = its 64-slot blocks)."""
-        upc, ctas = ctypes.c_int(), ctypes.c_int()
-        check(self._lib.pi_debug_split_plan(self._h, int(K), ctypes.byref(upc), ctypes.byref(ctas)))
-        return upc.value, ctas.value
+        """(plain_blocks, units_per_cta, ctas) of the FP32 rollout launch for K
+        rollouts: plain_blocks 64-slot blocks one CTA each, then (units_per_cta
+        > 0) the rest as the output-split launch of ctas CTAs."""
+        pb, upc, ctas = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        check(self._lib.pi_debug_split_plan(self._h, int(K), ctypes.byref(pb), ctypes.byref(upc), ctypes.byref(ctas)))
+        return pb.value, upc.value, ctas.value
 
     def stage_times(self, back: int = 0):
         """(rollout_ms, scan_ms, merge_ms) of the timed update `back` calls before the

@@ -172,8 +172,9 @@ int launch_rollouts(pi_ctx *c, const float *x0, const float *u_nom, int K, int T
     a.eps_tk = eps;
     a.phi = phi;
     PI_CUDA(ctx_split_args(c, a), "split exchange area clear");
-    PI_CUDA(launch_rollout_fp32(a, c->stream), "rollout kernel launch");
-    c->launches++;
+    int n = 0;
+    PI_CUDA(launch_rollout_fp32(a, c->stream, &n), "rollout kernel launch");
+    c->launches += (uint64_t)n;
     return PI_OK;
 }
 
@@ -485,9 +486,9 @@ int pi_set_output_split(pi_ctx *c, int mode)
     return PI_OK;
 }
 
-int pi_debug_split_plan(pi_ctx *c, int K, int *units_per_cta, int *ctas)
+int pi_debug_split_plan(pi_ctx *c, int K, int *plain_blocks, int *units_per_cta, int *ctas)
 {
-    if (!c || !units_per_cta || !ctas) return fail(PI_ERR_INVALID_ARG, "NULL argument");
+    if (!c || !plain_blocks || !units_per_cta || !ctas) return fail(PI_ERR_INVALID_ARG, "NULL argument");
     if (pi2rh_is_tc(c->opts.precision)) return fail(PI_ERR_INVALID_ARG, "the output split is an FP32-form launch");
     if (K < 1) return fail(PI_ERR_INVALID_ARG, "K must be >= 1");
     DeviceGuard dg(c->device);
@@ -497,9 +498,10 @@ int pi_debug_split_plan(pi_ctx *c, int K, int *units_per_cta, int *ctas)
     a.split = c->d_split;
     a.split_max_blocks = c->split_max_blocks;
     a.split_mode = c->split_mode;
-    const int upc = fp32_split_upc(a);
-    *units_per_cta = upc;
-    *ctas = upc > 0 ? fp32_split_grid(a, upc) : (int)(((long long)K * a.M + RF_SLOTS - 1) / RF_SLOTS);
+    const Fp32Launch L = fp32_launch_plan(a);
+    *plain_blocks = L.plain_blocks;
+    *units_per_cta = L.upc;
+    *ctas = L.upc > 0 ? L.split_ctas : 0;
     return PI_OK;
 }
 

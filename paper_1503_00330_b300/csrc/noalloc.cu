@@ -146,7 +146,9 @@ extern "C" int pi_update_noalloc(pi_ctx *c, const float *x0, const float *u_nom,
             a.eps_tk = eps;
             a.phi = phi;
             rc = na_cuda(ctx_split_args(c, a), "split exchange area clear");
-            if (rc == PI_OK) rc = na_cuda(launch_rollout_fp32(a, c->stream), "rollout kernel launch");
+            int n = 0;
+            if (rc == PI_OK) rc = na_cuda(launch_rollout_fp32(a, c->stream, &n), "rollout kernel launch");
+            if (rc == PI_OK) c->launches += (uint64_t)(n - 1);   // counted as one below
         }
         if (rc == PI_OK && ev) rc = na_cuda(cudaEventRecord(ev[1], c->stream), "event record");
         const double inv_lam_log2e = 1.4426950408889634074 / (double)lambda;

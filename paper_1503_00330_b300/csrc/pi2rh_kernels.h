@@ -52,7 +52,8 @@ struct RolloutArgs {
     int split_max_blocks;
     int split_mode;          // PI_SPLIT_OFF / _AUTO / _ALWAYS
     uint32_t split_epoch;    // >= 1, new for every launch on `split`
-    int split_upc;           // set by the launcher: (block, output) units per CTA
+    int split_upc;           // set by the launcher: (block, output) units per CTA,
+    int split_b0, split_blocks;  // and the 64-slot blocks [b0, b0 + blocks) the split launch covers
     int split_drop;          // failure-path check: CTAs left out of the split grid (0 normally)
 };
 
@@ -80,20 +81,21 @@ constexpr size_t SPLIT_HDR_BYTES = 128;
 constexpr size_t SPLIT_BLOCK_BYTES = 128 + (size_t)(NZ + 2 * NY) * RF_SLOTS * 4;
 inline size_t split_bytes(int max_blocks) { return SPLIT_HDR_BYTES + (size_t)max_blocks * SPLIT_BLOCK_BYTES; }
 
-// The FP32 rollout.  With a.split set and the mode allowing it, a launch of
-// fewer 64-slot blocks than the GPU has SMs spreads the blocks' (block,
-// output) units over one co-resident CTA per SM (a cooperative launch), so
-// every SM works; the results are those of the one-CTA-per-block launch bit
-// for bit.
-cudaError_t launch_rollout_fp32(const RolloutArgs &a, cudaStream_t s);
-// Units per CTA that the output-split launch would use for these arguments,
-// or 0 when the one-CTA-per-block launch runs.
-int fp32_split_upc(const RolloutArgs &a);
-inline int fp32_split_grid(const RolloutArgs &a, int upc)
-{
-    const long long units = ((long long)a.K * a.M + RF_SLOTS - 1) / RF_SLOTS * NY;
-    return (int)((units + upc - 1) / upc);
-}
+// How an FP32 rollout is launched: plain_blocks 64-slot blocks [0, plain_blocks)
+// one CTA each (whole waves), then, when upc > 0, the remaining split_blocks
+// blocks [split_b0, split_b0 + split_blocks) of a last, partial wave as the
+// output-split launch: their (block, output) units dealt out upc at a time
+// to split_ctas co-resident CTAs (one per SM).
+struct Fp32Launch {
+    int plain_blocks;
+    int split_b0, split_blocks, upc, split_ctas;
+};
+Fp32Launch fp32_launch_plan(const RolloutArgs &a);
+
+// The FP32 rollout (one or two launches, as fp32_launch_plan says; *n_launched
+// = how many).  The results are those of the one-CTA-per-block launch bit for
+// bit whatever the split.
+cudaError_t launch_rollout_fp32(const RolloutArgs &a, cudaStream_t s, int *n_launched = nullptr);
 cudaError_t launch_rollout_fp32_batch(const BatchArgs &b, int grid, cudaStream_t s);
 // Plain-launch form of the batch: one item per CTA (b.counter unused).
 cudaError_t launch_rollout_fp32_group(const BatchArgs &b, cudaStream_t s);

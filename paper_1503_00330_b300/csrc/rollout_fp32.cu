@@ -691,7 +691,7 @@ __device__ __forceinline__ void fp32_split_consumer(const RolloutArgs &a, const 
 #pragma unroll
         for (int o = 0; o < NY; ++o) yrH[o * SLOTS + tid] = 0.0f;
         if (U.bO >= 0) {
-            const long long gslot = (long long)U.bO * SLOTS + tid;
+            const long long gslot = (long long)(a.split_b0 + U.bO) * SLOTS + tid;
             const int k = (int)(gslot / a.M), m = (int)(gslot % a.M);
             fp32_init_slot(a, S, tid, k, k < a.K && m == 0);
             unsigned char *ob = split_blk(a, U.bO);
@@ -751,7 +751,7 @@ __device__ __forceinline__ void fp32_split_consumer(const RolloutArgs &a, const 
                         S.ybuf[o * SLOTS + tid] = __ldcg(&yg[o * SLOTS + tid]);
                         S.vbuf[o * SLOTS + tid] = __ldcg(&vg[o * SLOTS + tid]);
                     }
-                    const long long gslot = (long long)U.bO * SLOTS + tid;
+                    const long long gslot = (long long)(a.split_b0 + U.bO) * SLOTS + tid;
                     const int k = (int)(gslot / a.M), m = (int)(gslot % a.M);
                     fp32_step_slot(a, S, t, tid, k, m, k < a.K && m == 0);
                     if (t + 1 < a.T) {
@@ -785,8 +785,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) rollout_fp32_split_kernel(const _
     const Fp32Smem S = fp32_smem(smem);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid == 0) {
-        const int blocks = (int)(((long long)a.K * a.M + SLOTS - 1) / SLOTS);
-        split_units(split_plan((int)blockIdx.x, a.split_upc, blocks * NY), s_units);
+        split_units(split_plan((int)blockIdx.x, a.split_upc, a.split_blocks * NY), s_units);
         fp32_init_barriers(S);
     }
     for (int i = tid; i < a.cost.n_obs; i += NTHREADS) S.obs_s[i] = a.cost.obs[i];
@@ -1014,36 +1013,58 @@ cudaError_t launch_impl(const RolloutArgs &a, cudaStream_t s, long long slots)
 
 std::atomic<uint64_t> g_split_attr;
 
-int fp32_split_upc(const RolloutArgs &a)
+Fp32Launch fp32_launch_plan(const RolloutArgs &a)
 {
-    if (!a.split || a.split_mode == PI_SPLIT_OFF || a.K < 1 || a.M < 1) return 0;
-    const long long blocks = ((long long)a.K * a.M + SLOTS - 1) / SLOTS;
-    if (blocks > a.split_max_blocks) return 0;
+    Fp32Launch L{};
+    const long long blocks = a.K >= 1 && a.M >= 1 ? ((long long)a.K * a.M + SLOTS - 1) / SLOTS : 0;
+    L.plain_blocks = (int)blocks;
+    if (!a.split || a.split_mode == PI_SPLIT_OFF || blocks <= 0) return L;
     int dev = 0, nsm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0)
-        return 0;
-    const long long upc = (blocks * NY + nsm - 1) / nsm;
-    if (upc >= NY) return 0;
+        return L;
+    // Whole waves of blocks keep the plain launch (every SM busy); only the
+    // blocks of a last, partial wave are split over all SMs.
+    const long long tail = blocks % nsm;
+    if (tail == 0 || tail > a.split_max_blocks) return L;
+    const long long upc = (tail * NY + nsm - 1) / nsm;
+    if (upc >= NY) return L;
     // In auto mode, split only where the per-step work it takes off the
     // busiest CTA (NY - upc outputs of P records) clearly outweighs the two
     // flag round trips through L2 that it adds to each step.
-    if (a.split_mode == PI_SPLIT_AUTO && (NY - upc) * (long long)a.P < 64) return 0;
-    return (int)upc;
+    if (a.split_mode == PI_SPLIT_AUTO && (NY - upc) * (long long)a.P < 64) return L;
+    L.plain_blocks = (int)(blocks - tail);
+    L.split_b0 = (int)(blocks - tail);
+    L.split_blocks = (int)tail;
+    L.upc = (int)upc;
+    L.split_ctas = (int)((tail * NY + upc - 1) / upc);
+    return L;
 }
 
-cudaError_t launch_rollout_fp32(const RolloutArgs &a, cudaStream_t s)
+cudaError_t launch_rollout_fp32(const RolloutArgs &a, cudaStream_t s, int *n_launched)
 {
+    if (n_launched) *n_launched = 0;
     if (a.M < 1 || a.M > SLOTS || (a.M & (a.M - 1)) != 0) return cudaErrorInvalidValue;
-    const int upc = fp32_split_upc(a);
-    if (upc <= 0) return launch_impl(a, s, (long long)a.K * a.M);
+    const Fp32Launch L = fp32_launch_plan(a);
+    if (L.upc <= 0) {
+        cudaError_t e = launch_impl(a, s, (long long)a.K * a.M);
+        if (e == cudaSuccess && n_launched) *n_launched = 1;
+        return e;
+    }
     if (a.cost.n_obs > MAX_OBS || a.P <= 0 || a.stages_per_out <= 0 || a.split_epoch == 0)
         return cudaErrorInvalidValue;
+    if (L.plain_blocks > 0) {   // the whole waves: blocks [0, plain_blocks)
+        cudaError_t e = launch_impl(a, s, (long long)L.plain_blocks * SLOTS);
+        if (e != cudaSuccess) return e;
+        if (n_launched) *n_launched = 1;
+    }
     cudaError_t e = set_smem_once(g_split_attr, rollout_fp32_split_kernel, SPLIT_SMEM_BYTES);
     if (e != cudaSuccess) return e;
     RolloutArgs b = a;
-    b.split_upc = upc;
-    const int grid = fp32_split_grid(a, upc) - (a.split_drop > 0 ? 1 : 0);
+    b.split_upc = L.upc;
+    b.split_b0 = L.split_b0;
+    b.split_blocks = L.split_blocks;
+    const int grid = L.split_ctas - (a.split_drop > 0 ? 1 : 0);
     if (grid < 1) return cudaErrorInvalidValue;
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute at[1];
@@ -1055,7 +1076,9 @@ cudaError_t launch_rollout_fp32(const RolloutArgs &a, cudaStream_t s)
     at[0].val.cooperative = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, rollout_fp32_split_kernel, b);
+    e = cudaLaunchKernelEx(&cfg, rollout_fp32_split_kernel, b);
+    if (e == cudaSuccess && n_launched) *n_launched += 1;
+    return e;
 }
 
 cudaError_t launch_predict_fp32(const RolloutArgs &a, cudaStream_t s)

@@ -2,12 +2,14 @@
 
 With fewer 64-slot blocks than SMs, the split launch deals the (block, output)
 units out to one co-resident CTA per SM, which exchange each step's state
-through device memory.  Every output is still evaluated by one CTA with the
-same records, order and merge (Sec. 2, Eq. 1), so the update must equal the
-plain launch's bit for bit: u_out, costs, and (through pi_debug_rollout) the
-per-step costs and perturbations.  The cases cover one block, a ragged last
-block, sub-rollouts, mean-only noise, T = 1, blocks spread over up to 12 CTAs
-(one output each) and the realtime shape (128 blocks, 11 units per CTA); the
+through device memory; with more blocks than SMs, whole waves keep the plain
+launch and only the last, partial wave is split.  Every output is still
+evaluated by one CTA with the same records, order and merge (Sec. 2, Eq. 1),
+so the update must equal the plain launch's bit for bit: u_out, costs, and
+(through pi_debug_rollout) the per-step costs and perturbations.  The cases
+cover one block, a ragged last block, sub-rollouts, mean-only noise, T = 1,
+blocks spread over up to 12 CTAs (one output each), the realtime shape (128
+blocks, 11 units per CTA) and a partial last wave after a whole one; the
 oracle parity of the split path is covered by the end-to-end and full-size
 tests, which run it in the default mode.  The failure test leaves the last
 CTA out of the grid: the waits on it must give up, report PI_ERR_TIMEOUT and
@@ -47,18 +49,24 @@ CASES = [
     (700, 9, 130, 1, "mean_only"),     # deterministic dynamics
     (129, 1, 17, 1, "sampled"),        # T = 1
     (8192, 6, 512, 1, "sampled"),      # realtime shape: 128 blocks, 11 units per CTA
+    (-640, 5, 96, 1, "sampled"),       # one whole wave of blocks, then a partial wave of 10 (K = 64 SMs + 640)
+    (1024, 4, 64, 32, "sampled"),      # the sub-rollout workload's shape: 512 blocks, 3 whole waves + a split tail
 ]
 
 
 @pytest.mark.parametrize("K,T,L,M,noise", CASES)
 def test_split_equals_plain_bitwise(K, T, L, M, noise):
     from paper_1503_00330_b300.api import Controller
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    if K < 0:
+        K = 64 * nsm - K
     p = _problem(K, T, L, seed=K + T + L, M=M, noise=noise)
     ctl = Controller(p.model, p.cost, M=p.M, model_noise=p.model_noise, precision="fp32")
     ctl.set_output_split("always")
-    upc, ctas = ctl.split_plan(p.K)
+    plain, upc, ctas = ctl.split_plan(p.K)
     blocks = -(-p.K * p.M // 64)
-    assert 0 < upc < 12 and ctas == -(-blocks * 12 // upc) and ctas <= torch.cuda.get_device_properties(0).multi_processor_count
+    tail = blocks % nsm
+    assert plain == blocks - tail and 0 < upc < 12 and ctas == -(-tail * 12 // upc) and ctas <= nsm
     outs = {}
     for mode in ("always", "off", "always"):
         ctl.set_output_split(mode)
@@ -67,7 +75,7 @@ def test_split_equals_plain_bitwise(K, T, L, M, noise):
         outs.setdefault(mode, []).append((u.clone(), c.clone()))
     (u_s, c_s), (u_s2, c_s2) = outs["always"]
     u_p, c_p = outs["off"][0]
-    print(f"K={K} T={T} L={L} M={M}: {ctas} CTAs x {upc} units, plain {blocks} blocks")
+    print(f"K={K} T={T} L={L} M={M}: {plain} plain blocks + {ctas} CTAs x {upc} units")
     assert torch.equal(u_s, u_p) and torch.equal(c_s, c_p), "split launch differs from the plain launch"
     assert torch.equal(u_s2, u_s) and torch.equal(c_s2, c_s), "repeated split launch differs"
     ctl.close()
@@ -95,15 +103,19 @@ def test_auto_mode_plan():
     nsm = torch.cuda.get_device_properties(0).multi_processor_count
     p = _problem(8, 2, 512, seed=1)
     ctl = Controller(p.model, p.cost, precision="fp32")
-    upc, ctas = ctl.split_plan(8192)
-    assert upc == -(-128 * 12 // nsm) and ctas == -(-128 * 12 // upc)
-    assert ctl.split_plan(64 * nsm) == (0, nsm)
+    plain, upc, ctas = ctl.split_plan(8192)
+    assert plain == 0 and upc == -(-128 * 12 // nsm) and ctas == -(-128 * 12 // upc)
+    assert ctl.split_plan(64 * nsm) == (nsm, 0, 0)                  # one whole wave: plain
+    assert ctl.split_plan(64 * (nsm + 1)) == (nsm, 1, 12)           # + one block split 12 ways
+    assert ctl.split_plan(64 * (2 * nsm - 1))[1] == 0                # a nearly full last wave: plain
+    ctl.set_output_split("off")
+    assert ctl.split_plan(8192) == (128, 0, 0)
     ctl.close()
     q = _problem(8, 2, 5, seed=1)   # 3 field pairs per output: (12 - 1) * 3 < 64
     ctl = Controller(q.model, q.cost, precision="fp32")
-    assert ctl.split_plan(256) == (0, 4)
+    assert ctl.split_plan(256) == (4, 0, 0)
     ctl.set_output_split("always")
-    assert ctl.split_plan(256)[0] == 1
+    assert ctl.split_plan(256) == (0, 1, 48)
     ctl.close()
 
 
