@@ -567,7 +567,12 @@ int pi_debug_split_plan(pi_ctx *ctx, int K, int *plain_blocks, int *units_per_ct
  * CTA, so the flags it would set are never set.  The CTAs that wait on it give
  * up after the bounded wait (2 s), tell the others through the exchange area,
  * and all return; pi_sync then reports PI_ERR_TIMEOUT and the context stays
- * usable.  drop = 0 restores full launches.  Errors: INVALID_ARG (drop). */
+ * usable.  With drop = 2 the split launches are treated as refused by the
+ * runtime (cudaErrorCooperativeLaunchTooLarge, which is what a process gets
+ * when fewer SMs are open to it than the device has, under MPS or green
+ * contexts), so the fallback runs: those blocks go to the plain launch, with
+ * the same results.  drop = 0 restores full launches.  Errors: INVALID_ARG
+ * (drop). */
 int pi_debug_split_drop_cta(pi_ctx *ctx, int drop);
 
 /* Tensor-core GEMM core of the tensor-core form, checked on its own:

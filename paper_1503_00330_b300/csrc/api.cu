@@ -508,7 +508,7 @@ int pi_debug_split_plan(pi_ctx *c, int K, int *plain_blocks, int *units_per_cta,
 int pi_debug_split_drop_cta(pi_ctx *c, int drop)
 {
     if (!c) return fail(PI_ERR_INVALID_ARG, "ctx is NULL");
-    if (drop != 0 && drop != 1) return fail(PI_ERR_INVALID_ARG, "drop must be 0 or 1");
+    if (drop < 0 || drop > 2) return fail(PI_ERR_INVALID_ARG, "drop must be 0, 1 or 2");
     c->split_drop = drop;
     return PI_OK;
 }

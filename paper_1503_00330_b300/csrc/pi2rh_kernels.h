@@ -54,7 +54,9 @@ struct RolloutArgs {
     uint32_t split_epoch;    // >= 1, new for every launch on `split`
     int split_upc;           // set by the launcher: (block, output) units per CTA,
     int split_b0, split_blocks;  // and the 64-slot blocks [b0, b0 + blocks) the split launch covers
-    int split_drop;          // failure-path check: CTAs left out of the split grid (0 normally)
+    int split_drop;          // failure-path checks (0 normally): 1 = leave the split grid's last CTA
+                             // out, 2 = treat the split launch as refused by the runtime
+    int block0;              // first 64-slot block of a plain launch (set by the launcher)
 };
 
 // Rollout slots (rollout x sub-rollout) per CTA of the FP32 rollout kernel.

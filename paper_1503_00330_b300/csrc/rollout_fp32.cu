@@ -602,7 +602,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) rollout_fp32_kernel(const __grid_
     }
     long long g = 0;
     bool aborted = false;
-    fp32_consumer(a, S, (long long)blockIdx.x * SLOTS, g, aborted);
+    fp32_consumer(a, S, ((long long)a.block0 + blockIdx.x) * SLOTS, g, aborted);
 }
 
 // ---------------------------------------------------------------------------
@@ -1134,14 +1134,16 @@ __global__ void __launch_bounds__(PR_CTA_THREADS) predict_rows_kernel(const __gr
 
 std::atomic<uint64_t> g_pred_attr;
 
-cudaError_t launch_impl(const RolloutArgs &a, cudaStream_t s, long long slots)
+// One CTA per 64-slot block for blocks [block0, block0 + blocks).
+cudaError_t launch_impl(const RolloutArgs &a, cudaStream_t s, long long block0, long long blocks)
 {
     if (a.cost.n_obs > MAX_OBS || a.P <= 0 || a.stages_per_out <= 0) return cudaErrorInvalidValue;
     cudaError_t e = set_smem_once(g_attr_set, rollout_fp32_kernel, SMEM_BYTES);
     if (e != cudaSuccess) return e;
-    const long long blocks = (slots + SLOTS - 1) / SLOTS;
-    if (blocks <= 0 || blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
-    rollout_fp32_kernel<<<(unsigned)blocks, NTHREADS, SMEM_BYTES, s>>>(a);
+    if (blocks <= 0 || blocks > 0x7fffffffLL || block0 < 0 || block0 > 0x7fffffffLL) return cudaErrorInvalidValue;
+    RolloutArgs b = a;
+    b.block0 = (int)block0;
+    rollout_fp32_kernel<<<(unsigned)blocks, NTHREADS, SMEM_BYTES, s>>>(b);
     return cudaGetLastError();
 }
 
@@ -1183,14 +1185,14 @@ cudaError_t launch_rollout_fp32(const RolloutArgs &a, cudaStream_t s, int *n_lau
     if (a.M < 1 || a.M > SLOTS || (a.M & (a.M - 1)) != 0) return cudaErrorInvalidValue;
     const Fp32Launch L = fp32_launch_plan(a);
     if (L.upc <= 0) {
-        cudaError_t e = launch_impl(a, s, (long long)a.K * a.M);
+        cudaError_t e = launch_impl(a, s, 0, L.plain_blocks);
         if (e == cudaSuccess && n_launched) *n_launched = 1;
         return e;
     }
     if (a.cost.n_obs > MAX_OBS || a.P <= 0 || a.stages_per_out <= 0 || a.split_epoch == 0)
         return cudaErrorInvalidValue;
     if (L.plain_blocks > 0) {   // the whole waves: blocks [0, plain_blocks)
-        cudaError_t e = launch_impl(a, s, (long long)L.plain_blocks * SLOTS);
+        cudaError_t e = launch_impl(a, s, 0, L.plain_blocks);
         if (e != cudaSuccess) return e;
         if (n_launched) *n_launched = 1;
     }
@@ -1212,7 +1214,14 @@ cudaError_t launch_rollout_fp32(const RolloutArgs &a, cudaStream_t s, int *n_lau
     at[0].val.cooperative = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    e = cudaLaunchKernelEx(&cfg, rollout_fp32_split_kernel, b);
+    e = a.split_drop == 2 ? cudaErrorCooperativeLaunchTooLarge : cudaLaunchKernelEx(&cfg, rollout_fp32_split_kernel, b);
+    if (e == cudaErrorCooperativeLaunchTooLarge) {
+        // Fewer SMs than the device has are open to this process (MPS, green
+        // contexts), so the CTAs cannot all be resident: the split blocks run
+        // as plain blocks instead, with the same results.
+        if (a.split_drop != 2) (void)cudaGetLastError();
+        e = launch_impl(a, s, L.split_b0, L.split_blocks);
+    }
     if (e == cudaSuccess && n_launched) *n_launched += 1;
     return e;
 }

@@ -138,3 +138,25 @@ def test_split_peer_wait_times_out_and_context_recovers():
     ctl.sync()
     assert torch.equal(u, u_ref) and torch.equal(c, c_ref)
     ctl.close()
+
+
+def test_refused_split_launch_falls_back_to_plain_blocks():
+    """A cooperative launch the runtime refuses (fewer SMs open to the process
+    than the device has) runs its blocks as plain blocks: same results."""
+    from paper_1503_00330_b300.api import Controller
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    p = _problem(64 * nsm + 640, 4, 64, seed=12)
+    ctl = Controller(p.model, p.cost, precision="fp32")
+    ctl.set_output_split("off")
+    u_ref, c_ref = (t.clone() for t in ctl.update(p.x0, p.u_nom, p.K, p.T, p.lam, p.sigma_u, p.seed))
+    ctl.sync()
+    ctl.set_output_split("always")
+    lib = _lib.load()
+    _lib.check(lib.pi_debug_split_drop_cta(ctl.handle, 2))
+    n0 = ctl.launch_count()
+    u, c = ctl.update(p.x0, p.u_nom, p.K, p.T, p.lam, p.sigma_u, p.seed)
+    ctl.sync()
+    assert ctl.launch_count() - n0 == 4   # plain whole wave + plain tail + scan + merge
+    _lib.check(lib.pi_debug_split_drop_cta(ctl.handle, 0))
+    assert torch.equal(u, u_ref) and torch.equal(c, c_ref)
+    ctl.close()
