@@ -160,3 +160,32 @@ def test_refused_split_launch_falls_back_to_plain_blocks():
     _lib.check(lib.pi_debug_split_drop_cta(ctl.handle, 0))
     assert torch.equal(u, u_ref) and torch.equal(c, c_ref)
     ctl.close()
+
+
+def test_split_equals_plain_on_random_shapes():
+    """Twelve seeded random shapes (K up to 3 waves of blocks, T, L, M, noise on
+    or off): the split launch equals the plain one bit for bit wherever it runs."""
+    from paper_1503_00330_b300.api import Controller
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    rng = np.random.default_rng(2024)
+    ran = 0
+    for i in range(12):
+        M = int(rng.choice([1, 1, 2, 4, 8]))
+        K = int(rng.integers(1, 3 * 64 * nsm // M))
+        T = int(rng.integers(1, 9))
+        L = int(rng.integers(1, 200))
+        p = _problem(K, T, L, seed=100 + i, M=M, noise="sampled" if rng.random() < 0.7 else "mean_only")
+        ctl = Controller(p.model, p.cost, M=p.M, model_noise=p.model_noise, precision="fp32")
+        ctl.set_output_split("always")
+        plan = ctl.split_plan(p.K)
+        res = []
+        for mode in ("always", "off"):
+            ctl.set_output_split(mode)
+            u, c = ctl.update(p.x0, p.u_nom, p.K, p.T, p.lam, p.sigma_u, p.seed)
+            ctl.sync()
+            res.append((u.clone(), c.clone()))
+        print(f"K={K} T={T} L={L} M={M}: plan {plan}")
+        assert torch.equal(res[0][0], res[1][0]) and torch.equal(res[0][1], res[1][1]), f"shape {i} differs"
+        ran += plan[1] > 0
+        ctl.close()
+    assert ran >= 6   # most shapes have a partial wave to split
