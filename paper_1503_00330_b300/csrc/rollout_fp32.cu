@@ -24,6 +24,14 @@
 // so every parameter load feeds four field-slot evaluations on the packed
 // FP32x2 FMA datapath.  Every wait is bounded; on expiry the kernel records a
 // flag in the device error word, drains its copies and returns.
+//
+// Launches (launch_rollout_fp32): one CTA per 64-slot block
+// (rollout_fp32_kernel) for every whole wave of blocks; the blocks of a last,
+// partial wave (all of them when there are fewer blocks than SMs) can instead
+// go to rollout_fp32_split_kernel, which deals their (block, output) units out
+// to one co-resident CTA per SM with the same per-output arithmetic (see the
+// comment above that kernel).  The batched and serving paths use the
+// persistent and one-item-per-CTA forms at the end of the file.
 #include "pi2rh.h"
 #include "pi2rh_kernels.h"
 
