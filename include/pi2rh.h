@@ -249,6 +249,8 @@ int pi_rh_advance(pi_ctx *ctx, float *x0, const float *u_out, int T, float *u_no
  *                    off the busiest SM: fewer than ~11/12 as many blocks in
  *                    it as SMs and (12 - outputs per CTA) * ceil(L / 2) >= 64
  *   PI_SPLIT_ALWAYS  split it whenever that takes work off the busiest SM
+ * An update enqueued on a stream that is capturing a CUDA graph always takes
+ * the plain launch (a replayed split launch would reuse the flags' tag).
  * A bounded wait of one CTA on another that expires shows as PI_ERR_TIMEOUT
  * from pi_sync.  Errors: INVALID_ARG (mode). */
 int pi_set_output_split(pi_ctx *ctx, int mode);

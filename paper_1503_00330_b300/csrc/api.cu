@@ -498,7 +498,7 @@ int pi_debug_split_plan(pi_ctx *c, int K, int *plain_blocks, int *units_per_cta,
     a.split = c->d_split;
     a.split_max_blocks = c->split_max_blocks;
     a.split_mode = c->split_mode;
-    const Fp32Launch L = fp32_launch_plan(a);
+    const Fp32Launch L = fp32_launch_plan(a, c->stream);
     *plain_blocks = L.plain_blocks;
     *units_per_cta = L.upc;
     *ctas = L.upc > 0 ? L.split_ctas : 0;

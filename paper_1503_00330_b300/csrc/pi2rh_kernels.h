@@ -92,7 +92,8 @@ struct Fp32Launch {
     int plain_blocks;
     int split_b0, split_blocks, upc, split_ctas;
 };
-Fp32Launch fp32_launch_plan(const RolloutArgs &a);
+// (A stream that is capturing a CUDA graph always gets the plain launch.)
+Fp32Launch fp32_launch_plan(const RolloutArgs &a, cudaStream_t s);
 
 // The FP32 rollout (one or two launches, as fp32_launch_plan says; *n_launched
 // = how many).  The results are those of the one-CTA-per-block launch bit for

@@ -1159,12 +1159,17 @@ cudaError_t launch_impl(const RolloutArgs &a, cudaStream_t s, long long block0, 
 
 std::atomic<uint64_t> g_split_attr;
 
-Fp32Launch fp32_launch_plan(const RolloutArgs &a)
+Fp32Launch fp32_launch_plan(const RolloutArgs &a, cudaStream_t s)
 {
     Fp32Launch L{};
     const long long blocks = a.K >= 1 && a.M >= 1 ? ((long long)a.K * a.M + SLOTS - 1) / SLOTS : 0;
     L.plain_blocks = (int)blocks;
     if (!a.split || a.split_mode == PI_SPLIT_OFF || blocks <= 0) return L;
+    // A launch captured into a CUDA graph would replay with the epoch of the
+    // capture, and the flags of one replay would satisfy the waits of the
+    // next: captured updates take the plain launch.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) return L;
     int dev = 0, nsm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0)
@@ -1191,7 +1196,7 @@ cudaError_t launch_rollout_fp32(const RolloutArgs &a, cudaStream_t s, int *n_lau
 {
     if (n_launched) *n_launched = 0;
     if (a.M < 1 || a.M > SLOTS || (a.M & (a.M - 1)) != 0) return cudaErrorInvalidValue;
-    const Fp32Launch L = fp32_launch_plan(a);
+    const Fp32Launch L = fp32_launch_plan(a, s);
     if (L.upc <= 0) {
         cudaError_t e = launch_impl(a, s, 0, L.plain_blocks);
         if (e == cudaSuccess && n_launched) *n_launched = 1;

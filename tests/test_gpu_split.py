@@ -189,3 +189,30 @@ def test_split_equals_plain_on_random_shapes():
         ran += plan[1] > 0
         ctl.close()
     assert ran >= 6   # most shapes have a partial wave to split
+
+
+def test_update_captured_in_a_graph_takes_the_plain_launch():
+    """An FP32 update captured into a CUDA graph (here torch's) is launched
+    plainly, so replays stay correct: each replay equals the eager update."""
+    from paper_1503_00330_b300.api import Controller
+    p = _problem(8192, 3, 64, seed=31)
+    ctl = Controller(p.model, p.cost, precision="fp32")
+    ctl.set_output_split("always")
+    u_ref, c_ref = (t.clone() for t in ctl.update(p.x0, p.u_nom, p.K, p.T, p.lam, p.sigma_u, p.seed))
+    ctl.sync()
+    assert ctl.split_plan(p.K)[1] > 0            # eager: split
+    x0 = torch.as_tensor(p.x0, device="cuda")
+    un = torch.as_tensor(p.u_nom, device="cuda")
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        ctl.reserve(p.K, p.T)            # the context moves to s (and its scratch is sized) before the capture
+        with torch.cuda.graph(g, stream=s):
+            u, c = ctl.update(x0, un, p.K, p.T, p.lam, p.sigma_u, p.seed)
+    for _ in range(3):
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(u, u_ref) and torch.equal(c, c_ref)
+    ctl.sync()
+    ctl.close()
