@@ -216,3 +216,34 @@ def test_update_captured_in_a_graph_takes_the_plain_launch():
         assert torch.equal(u, u_ref) and torch.equal(c, c_ref)
     ctl.sync()
     ctl.close()
+
+
+def test_concurrent_split_updates_on_two_streams():
+    """Two contexts' split updates enqueued on two streams at once (each a
+    cooperative grid over most SMs): both complete without a wait expiring and
+    equal the same updates run one after the other."""
+    from paper_1503_00330_b300.api import Controller
+    p = _problem(8192, 12, 256, seed=41)
+    ctls = [Controller(p.model, p.cost, precision="fp32") for _ in range(2)]
+    for c in ctls:
+        c.set_output_split("always")
+    seeds = [p.seed, p.seed + 1]
+    ref = []
+    for c, sd in zip(ctls, seeds):
+        u, cs = c.update(p.x0, p.u_nom, p.K, p.T, p.lam, p.sigma_u, sd)
+        c.sync()
+        ref.append((u.clone(), cs.clone()))
+    streams = [torch.cuda.Stream() for _ in range(2)]
+    for s in streams:
+        s.wait_stream(torch.cuda.current_stream())
+    for rep in range(3):
+        outs = []
+        for c, s, sd in zip(ctls, streams, seeds):
+            with torch.cuda.stream(s):
+                outs.append(c.update(p.x0, p.u_nom, p.K, p.T, p.lam, p.sigma_u, sd))
+        for c in ctls:
+            c.sync()            # raises PI_ERR_TIMEOUT if a wait between CTAs expired
+        for (u, cs), (ur, cr) in zip(outs, ref):
+            assert torch.equal(u, ur) and torch.equal(cs, cr)
+    for c in ctls:
+        c.close()
