@@ -564,6 +564,13 @@ int pi_debug_wait_timeout(pi_ctx *ctx, int64_t limit_ns);
  * K < 1. */
 int pi_debug_split_plan(pi_ctx *ctx, int K, int *plain_blocks, int *units_per_cta, int *ctas);
 
+/* The same plan computed on the host alone, with no context and no GPU: K
+ * rollouts of M sub-rollouts, L fields per output, n_sm SMs, split mode
+ * `mode` (an exchange area of n_sm blocks, as pi_create allocates).  For
+ * checking the planning rules without a device.  Errors: INVALID_ARG. */
+int pi_debug_split_plan_sizes(int K, int M, int L, int n_sm, int mode, int *plain_blocks, int *units_per_cta,
+                              int *ctas);
+
 /* Failure path of the output-split launch's waits between CTAs, exercised
  * without a fault: with drop = 1 the next split launches leave out their last
  * CTA, so the flags it would set are never set.  The CTAs that wait on it give

@@ -505,6 +505,21 @@ int pi_debug_split_plan(pi_ctx *c, int K, int *plain_blocks, int *units_per_cta,
     return PI_OK;
 }
 
+int pi_debug_split_plan_sizes(int K, int M, int L, int n_sm, int mode, int *plain_blocks, int *units_per_cta,
+                              int *ctas)
+{
+    if (!plain_blocks || !units_per_cta || !ctas) return fail(PI_ERR_INVALID_ARG, "NULL argument");
+    if (K < 1 || M < 1 || L < 1 || n_sm < 1) return fail(PI_ERR_INVALID_ARG, "K, M, L and n_sm must be >= 1");
+    if (mode != PI_SPLIT_OFF && mode != PI_SPLIT_AUTO && mode != PI_SPLIT_ALWAYS)
+        return fail(PI_ERR_INVALID_ARG, "unknown split mode");
+    const long long blocks = ((long long)K * M + RF_SLOTS - 1) / RF_SLOTS;
+    const Fp32Launch Lp = fp32_plan_blocks(blocks, n_sm, (L + 1) / 2, mode, n_sm);
+    *plain_blocks = Lp.plain_blocks;
+    *units_per_cta = Lp.upc;
+    *ctas = Lp.upc > 0 ? Lp.split_ctas : 0;
+    return PI_OK;
+}
+
 int pi_debug_split_drop_cta(pi_ctx *c, int drop)
 {
     if (!c) return fail(PI_ERR_INVALID_ARG, "ctx is NULL");

@@ -94,6 +94,9 @@ struct Fp32Launch {
 };
 // (A stream that is capturing a CUDA graph always gets the plain launch.)
 Fp32Launch fp32_launch_plan(const RolloutArgs &a, cudaStream_t s);
+// The plan for `blocks` 64-slot blocks on nsm SMs, P field pairs per output,
+// split mode `mode` and an exchange area of max_blocks blocks (host only).
+Fp32Launch fp32_plan_blocks(long long blocks, int nsm, int P, int mode, int max_blocks);
 
 // The FP32 rollout (one or two launches, as fp32_launch_plan says; *n_launched
 // = how many).  The results are those of the one-CTA-per-block launch bit for

@@ -1159,10 +1159,33 @@ cudaError_t launch_impl(const RolloutArgs &a, cudaStream_t s, long long block0, 
 
 std::atomic<uint64_t> g_split_attr;
 
-Fp32Launch fp32_launch_plan(const RolloutArgs &a, cudaStream_t s)
+Fp32Launch fp32_plan_blocks(long long blocks, int nsm, int P, int mode, int max_blocks)
 {
     Fp32Launch L{};
+    L.plain_blocks = (int)blocks;
+    if (mode == PI_SPLIT_OFF || blocks <= 0 || nsm <= 0) return L;
+    // Whole waves of blocks keep the plain launch (every SM busy); only the
+    // blocks of a last, partial wave are split over all SMs.
+    const long long tail = blocks % nsm;
+    if (tail == 0 || tail > max_blocks) return L;
+    const long long upc = (tail * NY + nsm - 1) / nsm;
+    if (upc >= NY) return L;
+    // In auto mode, split only where the per-step work it takes off the
+    // busiest CTA (NY - upc outputs of P records) clearly outweighs the two
+    // flag round trips through L2 that it adds to each step.
+    if (mode == PI_SPLIT_AUTO && (NY - upc) * (long long)P < 64) return L;
+    L.plain_blocks = (int)(blocks - tail);
+    L.split_b0 = (int)(blocks - tail);
+    L.split_blocks = (int)tail;
+    L.upc = (int)upc;
+    L.split_ctas = (int)((tail * NY + upc - 1) / upc);
+    return L;
+}
+
+Fp32Launch fp32_launch_plan(const RolloutArgs &a, cudaStream_t s)
+{
     const long long blocks = a.K >= 1 && a.M >= 1 ? ((long long)a.K * a.M + SLOTS - 1) / SLOTS : 0;
+    Fp32Launch L{};
     L.plain_blocks = (int)blocks;
     if (!a.split || a.split_mode == PI_SPLIT_OFF || blocks <= 0) return L;
     // A launch captured into a CUDA graph would replay with the epoch of the
@@ -1174,22 +1197,7 @@ Fp32Launch fp32_launch_plan(const RolloutArgs &a, cudaStream_t s)
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0)
         return L;
-    // Whole waves of blocks keep the plain launch (every SM busy); only the
-    // blocks of a last, partial wave are split over all SMs.
-    const long long tail = blocks % nsm;
-    if (tail == 0 || tail > a.split_max_blocks) return L;
-    const long long upc = (tail * NY + nsm - 1) / nsm;
-    if (upc >= NY) return L;
-    // In auto mode, split only where the per-step work it takes off the
-    // busiest CTA (NY - upc outputs of P records) clearly outweighs the two
-    // flag round trips through L2 that it adds to each step.
-    if (a.split_mode == PI_SPLIT_AUTO && (NY - upc) * (long long)a.P < 64) return L;
-    L.plain_blocks = (int)(blocks - tail);
-    L.split_b0 = (int)(blocks - tail);
-    L.split_blocks = (int)tail;
-    L.upc = (int)upc;
-    L.split_ctas = (int)((tail * NY + upc - 1) / upc);
-    return L;
+    return fp32_plan_blocks(blocks, nsm, a.P, a.split_mode, a.split_max_blocks);
 }
 
 cudaError_t launch_rollout_fp32(const RolloutArgs &a, cudaStream_t s, int *n_launched)
