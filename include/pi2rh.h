@@ -571,6 +571,15 @@ int pi_debug_split_plan(pi_ctx *ctx, int K, int *plain_blocks, int *units_per_ct
 int pi_debug_split_plan_sizes(int K, int M, int L, int n_sm, int mode, int *plain_blocks, int *units_per_cta,
                               int *ctas);
 
+/* The work of CTA `cta` of a split launch over `blocks` 64-slot blocks with
+ * units_per_cta (block, output) units per CTA, as the kernel computes it (the
+ * same code, run on the host): *n_seg segments (1 or 2) in evaluation order,
+ * seg[5 i + 0..4] = {block (relative to the split's first), first output,
+ * output past the last, owned (1: this CTA steps the block's dynamics),
+ * owned ? the number of earlier CTAs holding outputs of the block : this CTA's
+ * index among them}.  seg holds 10 ints.  Host only.  Errors: INVALID_ARG. */
+int pi_debug_split_partition(int blocks, int units_per_cta, int cta, int *seg, int *n_seg);
+
 /* Failure path of the output-split launch's waits between CTAs, exercised
  * without a fault: with drop = 1 the next split launches leave out their last
  * CTA, so the flags it would set are never set.  The CTAs that wait on it give

@@ -106,6 +106,7 @@ _SIGS = {
                                            ctypes.POINTER(ctypes.c_int)]),
     "pi_debug_split_drop_cta": (ctypes.c_int, [_vp, ctypes.c_int]),
     "pi_debug_split_plan_sizes": (ctypes.c_int, [ctypes.c_int] * 5 + [ctypes.POINTER(ctypes.c_int)] * 3),
+    "pi_debug_split_partition": (ctypes.c_int, [ctypes.c_int] * 3 + [ctypes.POINTER(ctypes.c_int)] * 2),
     "pi_stage_times": (ctypes.c_int, [_vp, _fp]),
     "pi_stage_times_at": (ctypes.c_int, [_vp, ctypes.c_int, _fp]),
     "pi_debug_tc_gemm": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _vp]),

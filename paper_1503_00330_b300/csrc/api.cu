@@ -520,6 +520,15 @@ int pi_debug_split_plan_sizes(int K, int M, int L, int n_sm, int mode, int *plai
     return PI_OK;
 }
 
+int pi_debug_split_partition(int blocks, int units_per_cta, int cta, int *seg, int *n_seg)
+{
+    if (!seg || !n_seg) return fail(PI_ERR_INVALID_ARG, "NULL argument");
+    const int n = fp32_split_partition(blocks, units_per_cta, cta, seg);
+    if (n == 0) return fail(PI_ERR_INVALID_ARG, "no such CTA in that split (blocks >= 1, 1 <= units < 12)");
+    *n_seg = n;
+    return PI_OK;
+}
+
 int pi_debug_split_drop_cta(pi_ctx *c, int drop)
 {
     if (!c) return fail(PI_ERR_INVALID_ARG, "ctx is NULL");

@@ -97,6 +97,11 @@ Fp32Launch fp32_launch_plan(const RolloutArgs &a, cudaStream_t s);
 // The plan for `blocks` 64-slot blocks on nsm SMs, P field pairs per output,
 // split mode `mode` and an exchange area of max_blocks blocks (host only).
 Fp32Launch fp32_plan_blocks(long long blocks, int nsm, int P, int mode, int max_blocks);
+// The segments the split kernel's CTA `cta` evaluates (the kernel's own
+// partition, run on the host): seg[5 i ..] = {block, first output, end output,
+// owned, owned ? CTAs before it holding the block : its index among them}, in
+// evaluation order; returns the count (0 for an invalid CTA).
+int fp32_split_partition(int blocks, int upc, int cta, int *seg);
 
 // The FP32 rollout (one or two launches, as fp32_launch_plan says; *n_launched
 // = how many).  The results are those of the one-CTA-per-block launch bit for

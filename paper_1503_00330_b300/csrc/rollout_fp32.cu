@@ -677,7 +677,7 @@ struct SplitPlan {
     int own;                           // segment index of the owned block, or -1
 };
 
-__device__ __forceinline__ SplitPlan split_plan(int cta, int upc, int units)
+__host__ __device__ __forceinline__ SplitPlan split_plan(int cta, int upc, int units)
 {
     SplitPlan p{};
     const int s = cta * upc, e = min(s + upc, units);
@@ -1180,6 +1180,20 @@ Fp32Launch fp32_plan_blocks(long long blocks, int nsm, int P, int mode, int max_
     L.upc = (int)upc;
     L.split_ctas = (int)((tail * NY + upc - 1) / upc);
     return L;
+}
+
+int fp32_split_partition(int blocks, int upc, int cta, int *seg)
+{
+    if (blocks < 1 || upc < 1 || upc >= NY || cta < 0 || cta * upc >= blocks * NY) return 0;
+    const SplitPlan p = split_plan(cta, upc, blocks * NY);
+    for (int i = 0; i < p.nseg; ++i) {
+        seg[5 * i + 0] = p.b[i];
+        seg[5 * i + 1] = p.o0[i];
+        seg[5 * i + 2] = p.o1[i];
+        seg[5 * i + 3] = p.owned[i] ? 1 : 0;
+        seg[5 * i + 4] = p.owned[i] ? p.nparts : p.part[i];
+    }
+    return p.nseg;
 }
 
 Fp32Launch fp32_launch_plan(const RolloutArgs &a, cudaStream_t s)

@@ -69,3 +69,88 @@ def test_rejects_bad_sizes(lib):
     out = [ctypes.c_int() for _ in range(3)]
     for args in ((0, 1, 8, 148, AUTO), (8, 0, 8, 148, AUTO), (8, 1, 0, 148, AUTO), (8, 1, 8, 0, AUTO), (8, 1, 8, 148, 7)):
         assert lib.pi_debug_split_plan_sizes(*args, *[ctypes.byref(o) for o in out]) == _lib.PI_ERR_INVALID_ARG
+
+
+def partition(lib, blocks, upc):
+    """Per CTA: list of segments (block, o0, o1, owned, parts_or_index) from the kernel's own plan."""
+    units = blocks * 12
+    ctas = -(-units // upc)
+    out = []
+    seg = (ctypes.c_int * 10)()
+    n = ctypes.c_int()
+    for c in range(ctas):
+        _lib.check(lib.pi_debug_split_partition(blocks, upc, c, seg, ctypes.byref(n)))
+        out.append([tuple(seg[5 * i:5 * i + 5]) for i in range(n.value)])
+    assert lib.pi_debug_split_partition(blocks, upc, ctas, seg, ctypes.byref(n)) == _lib.PI_ERR_INVALID_ARG
+    return out
+
+
+def simulate(parts, blocks, T=3):
+    """Runs the split kernel's flag protocol (publish / wait ready, done / wait
+    done) over T steps under a round-robin schedule; True when every CTA finishes."""
+    ready = {}
+    done = {}
+    progs = []
+    for segs in parts:
+        ev = []
+        own = [s for s in segs if s[3]]
+        if own:
+            ev.append(("pub", own[0][0], 1))
+        for t in range(T):
+            for b, o0, o1, owned, idx in segs:
+                if not owned:
+                    ev += [("wait_ready", b, t + 1), ("done", b, idx, t + 1)]
+            if own:
+                b, _, _, _, nparts = own[0]
+                ev += [("wait_done", b, p, t + 1) for p in range(nparts)]
+                if t + 1 < T:
+                    ev.append(("pub", b, t + 2))
+        progs.append(ev)
+    pc = [0] * len(progs)
+    moved = True
+    while moved:
+        moved = False
+        for c, ev in enumerate(progs):
+            while pc[c] < len(ev):
+                e = ev[pc[c]]
+                if e[0] == "pub":
+                    ready[e[1]] = e[2]
+                elif e[0] == "done":
+                    done[(e[1], e[2])] = e[3]
+                elif e[0] == "wait_ready" and ready.get(e[1], 0) < e[2]:
+                    break
+                elif e[0] == "wait_done" and done.get((e[1], e[2]), 0) < e[3]:
+                    break
+                pc[c] += 1
+                moved = True
+    return all(pc[c] == len(ev) for c, ev in enumerate(progs))
+
+
+@pytest.mark.parametrize("nsm", [2, 7, 20, 148, 160])
+def test_kernel_partition_covers_every_unit_once_and_cannot_deadlock(lib, nsm):
+    for blocks in range(1, nsm + 1):
+        upc = -(-blocks * 12 // nsm)
+        if upc >= 12:
+            continue
+        parts = partition(lib, blocks, upc)
+        seen = {}
+        owners = {}
+        nonowner_idx = {}
+        for c, segs in enumerate(parts):
+            assert 1 <= len(segs) <= 2 and sum(s[3] for s in segs) <= 1
+            assert len(segs) == 1 or not segs[0][3], "the non-owned segment comes first"
+            for b, o0, o1, owned, idx in segs:
+                assert 0 <= b < blocks and 0 <= o0 < o1 <= 12
+                for o in range(o0, o1):
+                    assert (b, o) not in seen
+                    seen[(b, o)] = c
+                if owned:
+                    assert o1 == 12 and o0 > 0
+                    owners[b] = (c, idx)
+                else:
+                    nonowner_idx.setdefault(b, []).append(idx)
+        assert len(seen) == blocks * 12
+        for b in range(blocks):
+            c, nparts = owners[b]
+            assert sorted(nonowner_idx.get(b, [])) == list(range(nparts)) and 1 <= nparts <= 11
+        assert simulate(parts, blocks), f"flag protocol cannot finish for {blocks} blocks on {nsm} SMs"
