@@ -615,10 +615,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) rollout_fp32_kernel(const __grid_
 
 // ---------------------------------------------------------------------------
 // Output-split launch.  With fewer 64-slot blocks than SMs, the one-CTA-per-
-// block launch leaves SMs idle (K = 8192: 128 blocks on 148 SMs).  Here the
-// (block, output) units of all blocks, unit = b * NY + o, are dealt out in
-// runs of `upc` consecutive units to gridDim.x co-resident CTAs (one per SM,
-// a cooperative launch), upc = ceil(blocks * NY / SMs) < NY.  Each CTA's run
+// block launch leaves SMs idle (K = 8192: 128 blocks on 148 SMs), and so does
+// the last, partial wave of a larger launch.  Here the split_blocks blocks
+// from split_b0 on (numbered b = 0, 1, ... below) are evaluated as
+// (block, output) units, unit = b * NY + o, dealt out in runs of `upc`
+// consecutive units to gridDim.x co-resident CTAs (one per SM, a cooperative
+// launch), upc = ceil(split_blocks * NY / SMs) < NY.  Each CTA's run
 // covers the end of at most one block (its *owned* block, whose slots it
 // steps) and the start or middle of at most one other (a *non-owned*
 // segment).  Every output of a block is evaluated by one CTA with the same
