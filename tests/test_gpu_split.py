@@ -247,3 +247,21 @@ def test_concurrent_split_updates_on_two_streams():
             assert torch.equal(u, ur) and torch.equal(cs, cr)
     for c in ctls:
         c.close()
+
+
+def test_split_equals_plain_with_the_papers_cost():
+    """The Sec. 5 cost (Gaussian obstacle bumps, crash term, no variance or
+    terminal term) through the split launch: bitwise the plain launch's."""
+    from paper_1503_00330_b300.api import Controller
+    p = W.problem(3000, 10, 80, seed=8, cost=W.paper_cost(n_obs=5, seed=8))
+    p.u_nom = np.random.default_rng(8).normal(0, 0.2, (p.T, 4)).astype(np.float32)
+    ctl = Controller(p.model, p.cost, precision="fp32")
+    res = []
+    for mode in ("always", "off"):
+        ctl.set_output_split(mode)
+        u, c = ctl.update(p.x0, p.u_nom, p.K, p.T, p.lam, p.sigma_u, p.seed)
+        ctl.sync()
+        res.append((u.clone(), c.clone()))
+    assert ctl.split_plan(p.K)[1] == 0          # "off" now; "always" split it
+    assert torch.equal(res[0][0], res[1][0]) and torch.equal(res[0][1], res[1][1])
+    ctl.close()
