@@ -250,3 +250,32 @@ def test_batched_workload_sampled(batched_ref, form):
     batch.close()
     for c in ctls:
         c.close()
+
+
+# ---------------------------------------------------------------------------
+# FP32 with a split partial wave, sampled
+# ---------------------------------------------------------------------------
+def test_fp32_partial_wave_split_sampled(oracle):
+    """The realtime model with one whole wave of 64-slot blocks plus ten more
+    (K = 64 SMs + 640): the plain launch takes the whole wave, the output-split
+    launch the last ten blocks.  S_{k,0} of 32 rollouts at each end (one side
+    in each launch) against the oracle."""
+    import torch
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    p = W.realtime(0)
+    p.K, p.T = 64 * nsm + 640, 40
+    p.u_nom = p.u_nom[:p.T].copy()
+    ctl = _ctrl(p, "fp32")
+    plain, upc, ctas = ctl.split_plan(p.K)
+    assert plain == nsm and upc == 1 and ctas == 120
+    u, c = ctl.update(p.x0, p.u_nom, p.K, p.T, p.lam, p.sigma_u, p.seed)
+    ctl.sync()
+    c = c.cpu().numpy().astype(np.float64)
+    for k0 in (0, p.K - 32):
+        r = oracle.rollouts(p.model, p.cost, p.x0, p.u_nom, 32, p.T, p.sigma_u, p.seed, k0=k0)
+        S0 = oracle.cost_to_go(r["cost"], r["phi"], float(p.model.dt))[:, 0]
+        err = np.abs(c[k0:k0 + 32] - S0) / S0
+        print(f"fp32 partial-wave split, rollouts {k0}..{k0 + 31}: S0 max rel err {err.max():.3g}")
+        assert np.all(err <= S_TOL["fp32"])
+    assert np.all(np.isfinite(u.cpu().numpy()))
+    ctl.close()
